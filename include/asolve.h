@@ -1,0 +1,193 @@
+/*
+ * asolve.h -- C ABI of a GB300-native (sm_103a) adaptive solver for A X = B.
+ *
+ * The method is the adaptive solver of Sanderson & Curtin, "An Adaptive
+ * Solver for Systems of Linear Equations" (arXiv 2007.11208): a property scan
+ * of A (Sec. 2.1 bandwidths, Sec. 2.2 triangularity, Sec. 2.3 / Fig. 4
+ * likely-sympd), a solver chosen by the detection order of Sec. 2 (banded
+ * LU, triangular substitution, Cholesky with fallback to LU, LU with partial
+ * pivoting), a reciprocal condition estimate (Sec. 2, "each of the solvers
+ * estimates the reciprocal condition number"), and a minimum-norm SVD solve
+ * when a solver fails or rcond < 0.5 eps (Sec. 2.5).  Every step runs in the
+ * library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are FP64, dense, column-major with leading dimension n (the
+ *    paper's storage, Sec. 1 and Sec. 2.1).  B and X are n x nrhs, ld = n.
+ *  - Unless ASOLVE_HOST_BUFFERS is given, every matrix/vector pointer is a
+ *    DEVICE pointer owned by the caller, 16-byte aligned.  A and B are never
+ *    modified (like the paper's solve(A, B), Fig. 3); X may alias nothing.
+ *  - The context owns its CUDA stream (or the stream given in the config),
+ *    its workspaces and its CUDA graphs.  A context is not thread-safe; use
+ *    one context per host thread.
+ *  - Return codes: 0 = OK; > 0 = warning, X holds an answer; < 0 = error.
+ *  - Work is ordered on the context stream.  Calls returning an
+ *    asolve_info through a host pointer synchronise that stream before they
+ *    return; the *_async / batched calls do not unless ASOLVE_SYNC is set.
+ */
+#ifndef ASOLVE_H
+#define ASOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return / status codes ------------------------------------------- */
+#define ASOLVE_OK              0
+#define ASOLVE_W_APPROX        1   /* SVD fallback used (Sec. 2.5): approximate solution */
+#define ASOLVE_W_ILLCOND       2   /* rcond below threshold, SVD disabled: X from the solver */
+#define ASOLVE_PENDING         3   /* asolve_poll: request still in flight */
+#define ASOLVE_E_INVALID      -1   /* bad argument (null pointer, n < 0, nrhs < 1, ...) */
+#define ASOLVE_E_NONFINITE    -2   /* Inf or NaN in A or B */
+#define ASOLVE_E_SINGULAR     -3   /* solver failed and SVD disabled; X zeroed */
+#define ASOLVE_E_NOMEM        -4   /* device allocation failed / over the HBM budget */
+#define ASOLVE_E_CUDA         -5   /* a CUDA call failed */
+#define ASOLVE_E_TIMEOUT      -6   /* a device-side wait gave up */
+#define ASOLVE_E_IR_STALL     -7   /* refinement stalled and FP64 fallback disabled */
+#define ASOLVE_E_UNSUPPORTED  -8   /* size or option outside what this build supports */
+
+/* ---- detected class (Sec. 2 detection order) ------------------------- */
+#define ASOLVE_CLS_NONE     0
+#define ASOLVE_CLS_BANDED   1
+#define ASOLVE_CLS_LOWER    2
+#define ASOLVE_CLS_UPPER    3
+#define ASOLVE_CLS_SYMPD    4
+#define ASOLVE_CLS_GENERAL  5
+
+/* ---- route taken (the primary solver; SVD use is reported by status) -- */
+#define ASOLVE_ROUTE_NONE          0
+#define ASOLVE_ROUTE_BAND_LU       1   /* Sec. 2.1 (xGBTRF/xGBTRS/xGBCON) */
+#define ASOLVE_ROUTE_TRI_LOWER     2   /* Sec. 2.2, Eq. 3 forward substitution */
+#define ASOLVE_ROUTE_TRI_UPPER     3   /* Sec. 2.2 back substitution */
+#define ASOLVE_ROUTE_CHOL          4   /* Sec. 2.3 (xPOTRF/xPOTRS/xPOCON) */
+#define ASOLVE_ROUTE_CHOL_FAIL_LU  5   /* Sec. 2.3: Cholesky failed -> general solver */
+#define ASOLVE_ROUTE_LU            6   /* Sec. 2.4, Eq. 4 (xGETRF/xGETRS/xGECON) */
+#define ASOLVE_ROUTE_SVD           7   /* ASOLVE_FORCE_SVD only */
+
+/* ---- precision of the dense factorisations --------------------------- */
+#define ASOLVE_PREC_FP64    0   /* FP64 factorisations (DMMA tensor path) */
+#define ASOLVE_PREC_MIXED   1   /* FP32 factors + FP64 iterative refinement */
+
+/* ---- flags ----------------------------------------------------------- */
+#define ASOLVE_NO_APPROX     0x01u  /* disable the SVD fallback (Sec. 2.5 option) */
+#define ASOLVE_FORCE_LU      0x02u  /* skip structure-based routing: always LU */
+#define ASOLVE_FORCE_SVD     0x04u  /* go straight to the SVD solver */
+#define ASOLVE_NO_RCOND      0x08u  /* skip the condition estimate (and its SVD test) */
+#define ASOLVE_SYNC          0x10u  /* synchronise the stream before returning */
+#define ASOLVE_HOST_BUFFERS  0x20u  /* A, B, X (and batched arrays) are host memory */
+#define ASOLVE_BERR          0x40u  /* FP64 path: also compute the backward error */
+
+typedef struct asolve_ctx asolve_ctx;
+
+typedef struct {
+  double  rcond_threshold; /* SVD if rcond < this (strict); default 0.5*DBL_EPSILON (Sec. 2.5) */
+  double  sympd_tol;       /* Fig. 4 symmetry tolerance; default 100*DBL_EPSILON */
+  double  band_frac;       /* Sec. 2.1: not banded if band positions > band_frac*n^2; 0.25 */
+  double  svd_trunc_rel;   /* SVD keeps sigma_i > svd_trunc_rel*sigma_max; <= 0 means n*eps */
+  int32_t precision;       /* ASOLVE_PREC_*; default ASOLVE_PREC_MIXED */
+  int32_t ir_max_iter;     /* refinement steps before falling back to FP64; default 10 */
+  double  ir_target_berr;  /* stop refining when berr <= this; default 1e-13 */
+  double  ir_kappa_limit;  /* mixed: rcond < 1/limit from the FP32 factors -> FP64; default 1e6 */
+  size_t  hbm_budget;      /* serving admission budget in bytes; default 120 GB */
+  void*   stream;          /* cudaStream_t to run on; NULL: the context creates one */
+  int32_t device;          /* CUDA device ordinal; < 0: the current device */
+  int32_t reserved;
+} asolve_config;
+
+typedef struct {           /* 64 bytes, one per system */
+  int32_t cls;             /* ASOLVE_CLS_* detected by the scan */
+  int32_t route;           /* ASOLVE_ROUTE_* primary solver taken */
+  int32_t status;          /* ASOLVE_OK / W_* / E_* for this system */
+  int32_t ir_iters;        /* refinement steps taken (mixed precision) */
+  int64_t kl, ku;          /* exact sub/super-diagonal counts (Sec. 2.1) */
+  double  rcond;           /* estimate from the primary solver; NaN if none */
+  double  berr;            /* max over columns of ||b-Ax||inf/(||A||inf||x||inf+||b||inf); NaN if not
+                              computed.  Mixed precision: the backward error verified by the last FP64
+                              residual; the returned X is that iterate plus the correction computed
+                              from the same residual. */
+  int64_t svd_rank;        /* singular values kept by the SVD solve; -1 if not used */
+  int32_t precision;       /* ASOLVE_PREC_* the final answer came from */
+  int32_t detail;          /* bit 0: FP32 factor rejected by the rcond gate,
+                              bit 1: refinement stalled, bit 2: FP32 Cholesky failed */
+} asolve_info;
+
+typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */
+  int64_t kl, ku;
+  int32_t lower, upper, sympd, banded;
+  int32_t nonfinite, cls;
+  double  norm1, norminf;  /* ||A||_1 and ||A||_inf, to 2^-17 relative (FP32 partial sums) */
+} asolve_scan_result;
+
+typedef struct {           /* per-kernel CUDA-event timing, enabled by asolve_set_profiling */
+  int32_t count;           /* number of kernel kinds filled below */
+  int32_t reserved;
+  struct {
+    char     name[40];
+    int64_t  launches;
+    double   total_ms;
+  } k[24];
+} asolve_profile;
+
+/* Version string of this library. */
+const char* asolve_version(void);
+/* Text for a status code. */
+const char* asolve_strerror(int code);
+/* Fill *cfg with the defaults listed above.  Returns ASOLVE_E_INVALID on NULL. */
+int asolve_default_config(asolve_config* cfg);
+
+/* Create a context on cfg->device (NULL cfg: defaults).  On success *out
+ * owns a stream (unless cfg->stream was given), device workspaces that grow
+ * on demand, and graph caches.  Errors: E_INVALID, E_CUDA, E_NOMEM. */
+int asolve_create(asolve_ctx** out, const asolve_config* cfg);
+/* Release everything the context owns (waits for its stream first). */
+int asolve_destroy(asolve_ctx* ctx);
+/* The stream the context runs on (a cudaStream_t). */
+void* asolve_stream(asolve_ctx* ctx);
+
+/* Property scan of one n x n matrix (Sec. 2.1, 2.2, Fig. 4, plus norms);
+ * A is a device pointer; *out is host memory.  Synchronous. */
+int asolve_scan(asolve_ctx* ctx, const double* A, int64_t n, asolve_scan_result* out);
+
+/* The adaptive solve of one system A X = B (Sec. 2, Fig. 2):
+ *   A: n x n, B: n x nrhs, X: n x nrhs (device unless ASOLVE_HOST_BUFFERS);
+ *   info: host pointer (may be NULL).  Synchronous.  n = 0 returns OK.
+ * Returns the system's status (the value also stored in info->status). */
+int asolve_solve(asolve_ctx* ctx, const double* A, const double* B, int64_t n,
+                 int64_t nrhs, uint32_t flags, double* X, asolve_info* info);
+
+/* Same, for a matrix given in band storage (Sec. 2.1 compact format):
+ * AB is ldab x n column-major with A(i,j) at AB[(ku+i-j) + j*ldab],
+ * ldab >= kl+ku+1, for the declared bandwidths kl, ku.  The system always
+ * takes the banded route, with the true bandwidths found inside the band.
+ * The SVD fallback is available for n <= 4096 only (the dense copy); above
+ * that a failure returns E_SINGULAR and a low rcond W_ILLCOND.  Synchronous. */
+int asolve_solve_band(asolve_ctx* ctx, const double* AB, int64_t ldab, int64_t kl,
+                      int64_t ku, const double* B, int64_t n, int64_t nrhs,
+                      uint32_t flags, double* X, asolve_info* info);
+
+/* Batched adaptive solve of `count` independent systems of uneven size,
+ * packed in flat buffers: system s has A_s at A + a_off[s] (n[s] x n[s]),
+ * B_s at B + b_off[s] and X_s at X + b_off[s] (n[s] x nrhs[s]).  Offsets
+ * are in elements and must be even (16-byte alignment).  n[s] <= 1024.
+ * n, nrhs, a_off, b_off and infos are device arrays (host arrays with
+ * ASOLVE_HOST_BUFFERS, which also makes the call synchronous).  Systems
+ * are scanned in one launch, routed by class on the device, and solved by
+ * one persistent launch per class, replayed from a CUDA graph.  Returns
+ * the launch status (per-system status is in infos[s].status). */
+int asolve_solve_batched(asolve_ctx* ctx, int64_t count, const int64_t* n,
+                         const int64_t* nrhs, const int64_t* a_off,
+                         const int64_t* b_off, const double* A, const double* B,
+                         double* X, uint32_t flags, asolve_info* infos);
+
+/* Per-kernel timing with CUDA events on the context stream (off by default). */
+int asolve_set_profiling(asolve_ctx* ctx, int on);
+int asolve_get_profile(asolve_ctx* ctx, asolve_profile* out);
+int asolve_reset_profile(asolve_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ASOLVE_H */

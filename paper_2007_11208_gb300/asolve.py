@@ -1,0 +1,199 @@
+"""Thin ctypes binding of libasolve.so (include/asolve.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (FP64, column-major buffers:
+a matrix A is passed as a tensor whose memory holds A column by column).
+If libasolve.so is missing the import fails loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libasolve.so")
+
+# ---- constants mirrored from include/asolve.h -----------------------------
+OK, W_APPROX, W_ILLCOND, PENDING = 0, 1, 2, 3
+E_INVALID, E_NONFINITE, E_SINGULAR, E_NOMEM, E_CUDA, E_TIMEOUT, E_IR_STALL, E_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
+CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
+(ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
+ ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD) = range(8)
+PREC_FP64, PREC_MIXED = 0, 1
+NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND, SYNC, HOST_BUFFERS, BERR = (
+    0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40)
+
+
+class Config(C.Structure):
+    _fields_ = [("rcond_threshold", C.c_double), ("sympd_tol", C.c_double),
+                ("band_frac", C.c_double), ("svd_trunc_rel", C.c_double),
+                ("precision", C.c_int32), ("ir_max_iter", C.c_int32),
+                ("ir_target_berr", C.c_double), ("ir_kappa_limit", C.c_double),
+                ("hbm_budget", C.c_size_t), ("stream", C.c_void_p), ("device", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Info(C.Structure):
+    _fields_ = [("cls", C.c_int32), ("route", C.c_int32), ("status", C.c_int32),
+                ("ir_iters", C.c_int32), ("kl", C.c_int64), ("ku", C.c_int64),
+                ("rcond", C.c_double), ("berr", C.c_double), ("svd_rank", C.c_int64),
+                ("precision", C.c_int32), ("detail", C.c_int32)]
+
+
+class ScanResult(C.Structure):
+    _fields_ = [("kl", C.c_int64), ("ku", C.c_int64), ("lower", C.c_int32),
+                ("upper", C.c_int32), ("sympd", C.c_int32), ("banded", C.c_int32),
+                ("nonfinite", C.c_int32), ("cls", C.c_int32), ("norm1", C.c_double),
+                ("norminf", C.c_double)]
+
+
+class _ProfEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("count", C.c_int32), ("reserved", C.c_int32), ("k", _ProfEntry * 24)]
+
+
+INFO_BYTES = C.sizeof(Info)
+assert INFO_BYTES == 64
+
+_lib = None
+
+# Every symbol include/asolve.h declares.
+EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve_create",
+           "asolve_destroy", "asolve_stream", "asolve_scan", "asolve_solve",
+           "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
+           "asolve_get_profile", "asolve_reset_profile")
+
+
+def lib():
+    """Load libasolve.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2007_11208_gb300/build.py "
+                          "(no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    P, vp, i64, i32, u32 = C.POINTER, C.c_void_p, C.c_int64, C.c_int, C.c_uint32
+    L.asolve_version.restype = C.c_char_p
+    L.asolve_strerror.argtypes = [i32]
+    L.asolve_strerror.restype = C.c_char_p
+    L.asolve_default_config.argtypes = [P(Config)]
+    L.asolve_create.argtypes = [P(vp), P(Config)]
+    L.asolve_destroy.argtypes = [vp]
+    L.asolve_stream.argtypes = [vp]
+    L.asolve_stream.restype = vp
+    L.asolve_scan.argtypes = [vp, vp, i64, P(ScanResult)]
+    L.asolve_solve.argtypes = [vp, vp, vp, i64, i64, u32, vp, P(Info)]
+    L.asolve_solve_band.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, u32, vp, P(Info)]
+    L.asolve_solve_batched.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, u32, vp]
+    L.asolve_set_profiling.argtypes = [vp, i32]
+    L.asolve_get_profile.argtypes = [vp, P(Profile)]
+    L.asolve_reset_profile.argtypes = [vp]
+    for f in EXPORTS:
+        if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
+            getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return lib().asolve_strerror(code).decode()
+
+
+def default_config(**kw) -> Config:
+    c = Config()
+    lib().asolve_default_config(C.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(t)
+
+
+def info_dict(i: Info) -> dict:
+    return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+def infos_from_tensor(t: torch.Tensor) -> list:
+    """Decode a uint8/byte tensor holding count asolve_info records."""
+    raw = t.detach().cpu().contiguous().numpy().tobytes()
+    n = len(raw) // INFO_BYTES
+    return [info_dict(Info.from_buffer_copy(raw[k * INFO_BYTES:(k + 1) * INFO_BYTES]))
+            for k in range(n)]
+
+
+class Context:
+    """Owns an asolve_ctx (one CUDA stream, workspaces, captured graphs)."""
+
+    def __init__(self, **cfg):
+        self._h = C.c_void_p()
+        c = default_config(**cfg)
+        rc = lib().asolve_create(C.byref(self._h), C.byref(c))
+        if rc != OK:
+            raise RuntimeError(f"asolve_create: {strerror(rc)}")
+
+    def close(self):
+        if self._h:
+            lib().asolve_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream(self) -> int:
+        return lib().asolve_stream(self._h)
+
+    def scan(self, A: torch.Tensor, n: int) -> dict:
+        r = ScanResult()
+        rc = lib().asolve_scan(self._h, _ptr(A), n, C.byref(r))
+        if rc != OK:
+            raise RuntimeError(f"asolve_scan: {strerror(rc)}")
+        return {k: getattr(r, k) for k, _ in ScanResult._fields_}
+
+    def solve(self, A, B, n: int, nrhs: int, X, flags: int = 0):
+        """A, B, X: CUDA tensors (or host pointers with HOST_BUFFERS)."""
+        inf = Info()
+        rc = lib().asolve_solve(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(inf))
+        return rc, info_dict(inf)
+
+    def solve_band(self, AB, ldab: int, kl: int, ku: int, B, n: int, nrhs: int, X, flags: int = 0):
+        inf = Info()
+        rc = lib().asolve_solve_band(self._h, _ptr(AB), ldab, kl, ku, _ptr(B), n, nrhs, flags,
+                                     _ptr(X), C.byref(inf))
+        return rc, info_dict(inf)
+
+    def solve_batched(self, count, n, nrhs, a_off, b_off, A, B, X, infos, flags: int = 0) -> int:
+        return lib().asolve_solve_batched(self._h, count, _ptr(n), _ptr(nrhs), _ptr(a_off),
+                                          _ptr(b_off), _ptr(A), _ptr(B), _ptr(X), flags,
+                                          _ptr(infos))
+
+    def set_profiling(self, on: bool):
+        lib().asolve_set_profiling(self._h, int(on))
+
+    def reset_profile(self):
+        lib().asolve_reset_profile(self._h)
+
+    def profile(self) -> dict:
+        p = Profile()
+        lib().asolve_get_profile(self._h, C.byref(p))
+        return {p.k[i].name.decode(): (p.k[i].launches, p.k[i].total_ms) for i in range(p.count)}

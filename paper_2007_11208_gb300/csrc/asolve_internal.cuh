@@ -1,0 +1,111 @@
+// asolve_internal.cuh -- definitions shared by the library's translation units.
+//
+// Everything here belongs to the GPU library (libasolve.so); none of it is
+// shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "asolve.h"
+
+namespace asv {
+
+constexpr int kWarp = 32;
+constexpr int kBatchNMax = 1024;   // largest n handled by the per-CTA batched path
+constexpr int kBatchRhsMax = 8;    // largest nrhs handled by the per-CTA batched path
+constexpr int kCtaThreads = 256;   // threads of the per-system (class) kernels
+constexpr double kEps = 2.220446049250313080847e-16;  // 2^-52, machine epsilon
+
+// Scan flags (Sec. 2.1, 2.2, Fig. 4).
+enum : int32_t {
+  SF_NONFINITE = 1 << 0,   // Inf/NaN in A
+  SF_SYMPD = 1 << 1,       // likely_sympd (Fig. 4)
+  SF_LOWER = 1 << 2,       // all elements above the diagonal are zero
+  SF_UPPER = 1 << 3,       // all elements below the diagonal are zero
+  SF_BANDED = 1 << 4,      // band positions <= band_frac * n^2
+  SF_NORM_FP64 = 1 << 5,   // norms had to be summed in FP64 (FP32 range exceeded)
+  SF_B_NONFINITE = 1 << 6, // Inf/NaN in B
+};
+
+struct ScanRes {           // 32 bytes, one per system
+  int32_t kl, ku;
+  int32_t flags;
+  int32_t cls;
+  double norm1, norminf;
+};
+
+// Work lists of the class-routed batched pipeline.
+enum : int { L_BAND = 0, L_TRI = 1, L_CHOL = 2, L_LU = 3, L_SVD = 4, L_COUNT = 5 };
+
+// Device-resident description of one batched call.  The host writes it into
+// pinned memory; the captured graph copies it to the device first.
+struct BatchDesc {
+  int64_t count;
+  const int64_t* n;        // [count]
+  const int64_t* nrhs;     // [count]
+  const int64_t* a_off;    // [count]
+  const int64_t* b_off;    // [count]
+  const double* A;
+  const double* B;
+  double* X;
+  asolve_info* info;       // [count]
+  uint32_t flags;
+  int32_t precision;
+  double rcond_threshold, sympd_tol, band_frac, svd_trunc_rel;
+  int32_t ir_max_iter;
+  int32_t pad0;
+  double ir_target_berr, ir_kappa_limit;
+  // pipeline state (context-owned device memory)
+  ScanRes* scan;           // [capacity]
+  int32_t* lists;          // [L_COUNT][capacity]
+  int32_t* list_len;       // [L_COUNT] (zeroed per call)
+  int32_t* work_ctr;       // [16]      (zeroed per call)
+  int64_t capacity;
+  // per-CTA scratch slots of the class kernels
+  char* slot_base;
+  int64_t slot_bytes;
+  int32_t slot_count;
+  int32_t pad1;
+  int32_t* err_flag;       // device-side error (e.g. a scratch slot too small)
+};
+
+// --------------------------------------------------------------------------
+// Small device helpers.
+__device__ __forceinline__ uint64_t dbits(double x) { return (uint64_t)__double_as_longlong(x); }
+__device__ __forceinline__ bool is_nonzero_bits(uint64_t b) { return (b << 1) != 0; }
+__device__ __forceinline__ bool is_nonfinite_bits(uint64_t b) {
+  return ((b >> 52) & 0x7ff) == 0x7ff;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+// Largest value, ties (and the order of NaN-free equal values) resolved to
+// the smallest index: the first-maximum rule of partial pivoting.
+template <typename T>
+__device__ __forceinline__ void warp_argmax_first(T& v, int& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T w = __shfl_xor_sync(0xffffffffu, v, o);
+    int j = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (w > v || (w == v && j < idx)) { v = w; idx = j; }
+  }
+}
+
+__device__ __forceinline__ int64_t ldg_i64(const int64_t* p) { return __ldg(p); }
+
+}  // namespace asv

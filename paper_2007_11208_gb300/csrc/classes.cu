@@ -1,0 +1,928 @@
+// classes.cu -- the class-routed batched pipeline (paper Sec. 2, Fig. 2).
+//
+//   k_route       reads every system's scan result and applies the detection
+//                 order of Sec. 2 (banded, lower, upper, sympd, general),
+//                 writes the per-system info, and builds one work list per
+//                 solver class, largest systems first.
+//   k_band_class  Sec. 2.1: banded LU with partial pivoting in band storage
+//                 (xGBTRF semantics), band solve, 1-norm estimate.  One warp
+//                 per system.
+//   k_tri_class   Sec. 2.2 / Eq. 3: forward or back substitution, estimate.
+//   k_chol_class  Sec. 2.3: Cholesky; failure sends the system to the LU list.
+//   k_lu_class    Sec. 2.4 / Eq. 4: LU with partial pivoting.
+//   k_svd_class   Sec. 2.5: one-sided Jacobi SVD and minimum-norm solve for
+//                 every system whose solver failed or whose rcond < threshold.
+//
+// Mixed precision (ASOLVE_PREC_MIXED): Cholesky and LU factor in FP32, the
+// solution is refined with FP64 residuals until the normwise backward error
+// reaches the target; a factor whose estimated rcond is below 1/kappa_limit,
+// or a refinement that stalls, is redone in FP64.  Every class kernel is a
+// persistent kernel pulling systems from its list; per-CTA scratch slots
+// hold the factors.
+#include "cta_linalg.cuh"
+
+namespace asv {
+
+__device__ __forceinline__ int round4(int x) { return (x + 3) & ~3; }
+
+__device__ __forceinline__ void write_info_init(asolve_info* inf, const ScanRes& sr, int route,
+                                                int status, int precision) {
+  asolve_info i;
+  i.cls = sr.cls;
+  i.route = route;
+  i.status = status;
+  i.ir_iters = 0;
+  i.kl = sr.kl;
+  i.ku = sr.ku;
+  i.rcond = __longlong_as_double(0x7ff8000000000000ll);
+  i.berr = __longlong_as_double(0x7ff8000000000000ll);
+  i.svd_rank = -1;
+  i.precision = precision;
+  i.detail = 0;
+  *inf = i;
+}
+
+// ------------------------------------------------------------------ router
+// One CTA of 1024 threads.  Lists are sorted by n, descending (counting sort).
+__global__ void __launch_bounds__(1024) k_route(const BatchDesc* __restrict__ dp) {
+  const BatchDesc& d = *dp;
+  __shared__ int hist[4][kBatchNMax + 1];
+  for (int e = threadIdx.x; e < 4 * (kBatchNMax + 1); e += blockDim.x) (&hist[0][0])[e] = 0;
+  __syncthreads();
+  const int64_t cap = d.capacity;
+  for (int64_t s = threadIdx.x; s < d.count; s += blockDim.x) {
+    const int64_t n = d.n[s], nr = d.nrhs[s];
+    ScanRes sr = d.scan[s];
+    int list = -1, route = ASOLVE_ROUTE_NONE, status = ASOLVE_OK;
+    if (n < 0 || nr < 1) {
+      status = ASOLVE_E_INVALID;
+      sr = ScanRes{};
+    } else if (n > kBatchNMax || nr > kBatchRhsMax) {
+      status = ASOLVE_E_UNSUPPORTED;
+      sr = ScanRes{};
+    } else if (n == 0) {
+      sr = ScanRes{};
+    } else if (sr.flags & (SF_NONFINITE | SF_B_NONFINITE)) {
+      status = ASOLVE_E_NONFINITE;
+    } else if (d.flags & ASOLVE_FORCE_SVD) {
+      list = L_SVD;
+      route = ASOLVE_ROUTE_SVD;
+    } else if (d.flags & ASOLVE_FORCE_LU) {
+      list = L_LU;
+      route = ASOLVE_ROUTE_LU;
+    } else {
+      switch (sr.cls) {
+        case ASOLVE_CLS_BANDED: list = L_BAND; route = ASOLVE_ROUTE_BAND_LU; break;
+        case ASOLVE_CLS_LOWER: list = L_TRI; route = ASOLVE_ROUTE_TRI_LOWER; break;
+        case ASOLVE_CLS_UPPER: list = L_TRI; route = ASOLVE_ROUTE_TRI_UPPER; break;
+        case ASOLVE_CLS_SYMPD: list = L_CHOL; route = ASOLVE_ROUTE_CHOL; break;
+        default: list = L_LU; route = ASOLVE_ROUTE_LU; break;
+      }
+    }
+    write_info_init(d.info + s, sr, route, status, ASOLVE_PREC_FP64);
+    if (list >= 0 && list < 4) atomicAdd(&hist[list][n], 1);
+    if (list == L_SVD) {
+      int pos = atomicAdd(&d.list_len[L_SVD], 1);
+      d.lists[(int64_t)L_SVD * cap + pos] = (int32_t)s;
+    }
+  }
+  __syncthreads();
+  // exclusive prefix over n descending, per list
+  if (threadIdx.x < 4) {
+    const int l = threadIdx.x;
+    int acc = 0;
+    for (int n = kBatchNMax; n >= 0; --n) {
+      int h = hist[l][n];
+      hist[l][n] = acc;
+      acc += h;
+    }
+    d.list_len[l] = acc;
+  }
+  __syncthreads();
+  for (int64_t s = threadIdx.x; s < d.count; s += blockDim.x) {
+    const int64_t n = d.n[s];
+    const asolve_info& inf = d.info[s];
+    if (inf.status != ASOLVE_OK || n <= 0 || n > kBatchNMax || d.nrhs[s] > kBatchRhsMax) continue;
+    int list;
+    switch (inf.route) {
+      case ASOLVE_ROUTE_BAND_LU: list = L_BAND; break;
+      case ASOLVE_ROUTE_TRI_LOWER:
+      case ASOLVE_ROUTE_TRI_UPPER: list = L_TRI; break;
+      case ASOLVE_ROUTE_CHOL: list = L_CHOL; break;
+      case ASOLVE_ROUTE_LU: list = L_LU; break;
+      default: list = -1;
+    }
+    if (list < 0) continue;
+    int pos = atomicAdd(&hist[list][n], 1);
+    d.lists[(int64_t)list * cap + pos] = (int32_t)s;
+  }
+}
+
+// ------------------------------------------------------------ shared tail
+// Primary solver finished: decide on the SVD fallback (Sec. 2.5).  CTA scope.
+__device__ void finish_primary(const BatchDesc& d, int64_t s, bool failed, double rc, double* X,
+                               int64_t xcount) {
+  asolve_info* inf = d.info + s;
+  const bool no_rcond = (d.flags & ASOLVE_NO_RCOND) != 0;
+  const bool poor = !failed && !no_rcond && !(rc >= d.rcond_threshold);
+  if (threadIdx.x == 0)
+    inf->rcond = (failed || no_rcond) ? __longlong_as_double(0x7ff8000000000000ll) : rc;
+  if (!failed && !poor) {
+    if (threadIdx.x == 0) inf->status = ASOLVE_OK;
+    return;
+  }
+  if (d.flags & ASOLVE_NO_APPROX) {
+    if (failed)
+      for (int64_t i = threadIdx.x; i < xcount; i += blockDim.x) X[i] = 0.0;
+    if (threadIdx.x == 0) inf->status = failed ? ASOLVE_E_SINGULAR : ASOLVE_W_ILLCOND;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    int pos = atomicAdd(&d.list_len[L_SVD], 1);
+    d.lists[(int64_t)L_SVD * d.capacity + pos] = (int32_t)s;
+  }
+}
+
+// Warp-scope variant of finish_primary for warp-per-system kernels.
+__device__ void finish_primary_warp(const BatchDesc& d, int64_t s, bool failed, double rc, double* X,
+                                    int64_t xcount) {
+  asolve_info* inf = d.info + s;
+  const int lane = threadIdx.x & 31;
+  const bool no_rcond = (d.flags & ASOLVE_NO_RCOND) != 0;
+  const bool poor = !failed && !no_rcond && !(rc >= d.rcond_threshold);
+  if (lane == 0) inf->rcond = (failed || no_rcond) ? __longlong_as_double(0x7ff8000000000000ll) : rc;
+  if (!failed && !poor) {
+    if (lane == 0) inf->status = ASOLVE_OK;
+    return;
+  }
+  if (d.flags & ASOLVE_NO_APPROX) {
+    if (failed)
+      for (int64_t i = lane; i < xcount; i += 32) X[i] = 0.0;
+    if (lane == 0) inf->status = failed ? ASOLVE_E_SINGULAR : ASOLVE_W_ILLCOND;
+    return;
+  }
+  if (lane == 0) {
+    int pos = atomicAdd(&d.list_len[L_SVD], 1);
+    d.lists[(int64_t)L_SVD * d.capacity + pos] = (int32_t)s;
+  }
+}
+
+__device__ __forceinline__ int next_item(const BatchDesc& d, int ctr, int* s_item) {
+  if (threadIdx.x == 0) *s_item = atomicAdd(&d.work_ctr[ctr], 1);
+  __syncthreads();
+  int it = *s_item;
+  __syncthreads();
+  return it;
+}
+
+// Dense-class dynamic shared memory: 104 KB.
+constexpr int kDenseSmem = 104 * 1024;
+
+template <typename T>
+__device__ __forceinline__ int pick_nb(int n) {
+  const int budget = 96 * 1024;
+  int nb = 32;
+  while (nb > 4 && (size_t)(n + 64) * nb * sizeof(T) > (size_t)budget) nb >>= 1;
+  return nb;
+}
+
+// Slot layout of the dense classes: [W (8 * ldw * n)] [piv] [R (n*8 doubles)]
+struct DenseSlot {
+  void* W;
+  int* piv;
+  double* R;
+};
+__device__ __forceinline__ DenseSlot dense_slot(const BatchDesc& d, int n) {
+  char* base = d.slot_base + (size_t)blockIdx.x * d.slot_bytes;
+  DenseSlot s;
+  const size_t wbytes = ((size_t)8 * round4(n) * n + 255) & ~(size_t)255;
+  s.W = base;
+  s.piv = reinterpret_cast<int*>(base + wbytes);
+  s.R = reinterpret_cast<double*>(base + wbytes + 4096 * 2);
+  return s;
+}
+
+template <typename T>
+__device__ void copy_to_work(const double* __restrict__ A, int n, T* W, int ldw) {
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    W[(size_t)c * ldw + r] = (T)__ldg(A + e);
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------- mixed refinement
+// Solve with FP32 factors, refine with FP64 residuals (Sec. 2.4 / 2.3 solve
+// steps, used as the correction solver).  xd, xs: smem.  Returns true when
+// every column reached berr <= target; *berr_out = max column berr.
+template <typename ApplyF>
+__device__ bool refine(const BatchDesc& d, const double* __restrict__ A, const double* __restrict__ B,
+                       int n, int nrhs, double norminf, double* xd, float* xs, double* R,
+                       ApplyF apply32, double& berr_out, int& iters, CtaRed& red) {
+  __shared__ double s_scale[8], s_rmax[8];
+  // x0 = inv(A32) b, with each column scaled to unit max-norm first
+  for (int c = 0; c < nrhs; ++c) {
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(B[(size_t)c * n + i]));
+    m = cta_max(m, red);
+    if (threadIdx.x == 0) s_scale[c] = m > 0.0 ? m : 1.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+    int c = e / n;
+    xs[e] = (float)(B[e] / s_scale[c]);
+  }
+  apply32(xs);
+  for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = (double)xs[e] * s_scale[e / n];
+  __syncthreads();
+  double berr_prev = INFINITY;
+  iters = 0;
+  bool ok = false;
+  for (int it = 0;; ++it) {
+    cta_residual(A, n, n, B, xd, nrhs, R, s_rmax, red);
+    double berr = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      double xm = 0.0, bm = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        xm = fmax(xm, fabs(xd[(size_t)c * n + i]));
+        bm = fmax(bm, fabs(B[(size_t)c * n + i]));
+      }
+      xm = cta_max(xm, red);
+      bm = cta_max(bm, red);
+      double den = norminf * xm + bm;
+      double be = den > 0.0 ? s_rmax[c] / den : (s_rmax[c] > 0.0 ? INFINITY : 0.0);
+      if (!(be <= berr)) berr = be;  // NaN propagates as "not converged"
+    }
+    berr_out = berr;
+    const bool conv = berr <= d.ir_target_berr;
+    if (!conv && (it >= d.ir_max_iter || !(berr < 0.5 * berr_prev))) break;  // stalled
+    berr_prev = berr;
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+      int c = e / n;
+      double sc = s_rmax[c] > 0.0 ? s_rmax[c] : 1.0;
+      xs[e] = (float)(R[e] / sc);
+    }
+    apply32(xs);
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
+      int c = e / n;
+      double sc = s_rmax[c] > 0.0 ? s_rmax[c] : 1.0;
+      xd[e] += (double)xs[e] * sc;
+    }
+    __syncthreads();
+    ++iters;
+    // converged: the correction just applied used the verified residual,
+    // so it only removes the remaining O(kappa u32) part of the error
+    if (conv) { ok = true; break; }
+  }
+  __syncthreads();
+  return ok;
+}
+
+// FP64 backward error of the solution in xd (smem), max over columns.
+__device__ double berr_fp64(const double* __restrict__ A, const double* __restrict__ B, int n, int nrhs,
+                            double norminf, const double* xd, double* R, CtaRed& red) {
+  __shared__ double s_rmax[8];
+  cta_residual(A, n, n, B, xd, nrhs, R, s_rmax, red);
+  double berr = 0.0;
+  for (int c = 0; c < nrhs; ++c) {
+    double xm = 0.0, bm = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      xm = fmax(xm, fabs(xd[(size_t)c * n + i]));
+      bm = fmax(bm, fabs(B[(size_t)c * n + i]));
+    }
+    xm = cta_max(xm, red);
+    bm = cta_max(bm, red);
+    double den = norminf * xm + bm;
+    double be = den > 0.0 ? s_rmax[c] / den : (s_rmax[c] > 0.0 ? INFINITY : 0.0);
+    if (!(be <= berr)) berr = be;
+  }
+  return berr;
+}
+
+// --------------------------------------------------------------- LU / Chol
+// kind 0: LU, kind 1: Cholesky.  Returns for Cholesky whether the FP64
+// factorisation failed (the caller then moves the system to the LU list).
+template <int KIND>
+__device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem, CtaRed& red) {
+  const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
+  const double* A = d.A + d.a_off[s];
+  const double* B = d.B + d.b_off[s];
+  double* X = d.X + d.b_off[s];
+  const ScanRes sr = d.scan[s];
+  asolve_info* inf = d.info + s;
+  DenseSlot sl = dense_slot(d, n);
+  const int ldw = round4(n);
+  const bool no_rcond = (d.flags & ASOLVE_NO_RCOND) != 0;
+  int detail = 0;
+  // ---- mixed precision attempt
+  if (d.precision == ASOLVE_PREC_MIXED) {
+    float* W = reinterpret_cast<float*>(sl.W);
+    copy_to_work<float>(A, n, W, ldw);
+    const int nb = pick_nb<float>(n);
+    int f = KIND == 0 ? cta_lu_factor<float>(W, ldw, n, sl.piv, reinterpret_cast<float*>(smem), nb, red)
+                      : cta_chol_factor<float>(W, ldw, n, reinterpret_cast<float*>(smem), nb, red);
+    if (f == 0) {
+      float* v = reinterpret_cast<float*>(smem);
+      float* xi = v + n;
+      auto apply_est = [&](float* x, bool tr) {
+        if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.piv, x, n, 1, tr);
+        else cta_chol_apply<float, float>(W, ldw, n, x, n, 1);
+      };
+      double rc = __longlong_as_double(0x7ff8000000000000ll);
+      bool gate_ok = true;
+      if (!no_rcond) {
+        double est = cta_est_inv_norm1<float>(n, v, xi, apply_est, red);
+        rc = rcond_from(sr.norm1, est);
+        gate_ok = rc >= 1.0 / d.ir_kappa_limit;
+      }
+      if (gate_ok) {
+        double* xd = reinterpret_cast<double*>(smem);
+        float* xs = reinterpret_cast<float*>(xd + (size_t)n * nrhs);
+        auto apply32 = [&](float* x) {
+          if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.piv, x, n, nrhs, false);
+          else cta_chol_apply<float, float>(W, ldw, n, x, n, nrhs);
+        };
+        double berr;
+        int iters;
+        bool ok = refine(d, A, B, n, nrhs, sr.norminf, xd, xs, sl.R, apply32, berr, iters, red);
+        if (ok) {
+          for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
+          if (threadIdx.x == 0) {
+            inf->rcond = rc;
+            inf->berr = berr;
+            inf->ir_iters = iters;
+            inf->precision = ASOLVE_PREC_MIXED;
+            inf->status = ASOLVE_OK;
+            inf->detail |= detail;
+          }
+          __syncthreads();
+          return false;
+        }
+        detail |= 2;
+      } else {
+        detail |= 1;
+      }
+    } else if (KIND == 1) {
+      detail |= 4;
+    }
+  }
+  // ---- FP64 path
+  double* W = reinterpret_cast<double*>(sl.W);
+  copy_to_work<double>(A, n, W, ldw);
+  const int nb = pick_nb<double>(n);
+  int f = KIND == 0 ? cta_lu_factor<double>(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), nb, red)
+                    : cta_chol_factor<double>(W, ldw, n, reinterpret_cast<double*>(smem), nb, red);
+  if (threadIdx.x == 0) {
+    inf->detail |= detail;
+    inf->precision = ASOLVE_PREC_FP64;
+  }
+  if (KIND == 1 && f != 0) {
+    __syncthreads();
+    return true;  // not sympd after all (Sec. 2.3): general solver
+  }
+  const bool failed = f != 0;
+  double rc = __longlong_as_double(0x7ff8000000000000ll);
+  if (!failed) {
+    double* xd = reinterpret_cast<double*>(smem);
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = B[e];
+    if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.piv, xd, n, nrhs, false);
+    else cta_chol_apply<double, double>(W, ldw, n, xd, n, nrhs);
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
+    __syncthreads();
+    if (d.flags & ASOLVE_BERR) {
+      double be = berr_fp64(A, B, n, nrhs, sr.norminf, xd, sl.R, red);
+      if (threadIdx.x == 0) inf->berr = be;
+    }
+    if (!no_rcond) {
+      double* v = reinterpret_cast<double*>(smem);
+      double* xi = v + n;
+      auto apply_est = [&](double* x, bool tr) {
+        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.piv, x, n, 1, tr);
+        else cta_chol_apply<double, double>(W, ldw, n, x, n, 1);
+      };
+      double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
+      rc = rcond_from(sr.norm1, est);
+    }
+  }
+  __syncthreads();
+  finish_primary(d, s, failed, rc, X, (int64_t)n * nrhs);
+  __syncthreads();
+  return false;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_chol_class(const BatchDesc* __restrict__ dp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtaRed red;
+  __shared__ int s_item;
+  const BatchDesc& d = *dp;
+  const int len = d.list_len[L_CHOL];
+  for (;;) {
+    int it = next_item(d, 8 + L_CHOL, &s_item);
+    if (it >= len) break;
+    int64_t s = d.lists[(int64_t)L_CHOL * d.capacity + it];
+    bool to_lu = dense_system<1>(d, s, smem, red);
+    if (to_lu && threadIdx.x == 0) {
+      d.info[s].route = ASOLVE_ROUTE_CHOL_FAIL_LU;
+      int pos = atomicAdd(&d.list_len[L_LU], 1);
+      d.lists[(int64_t)L_LU * d.capacity + pos] = (int32_t)s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_lu_class(const BatchDesc* __restrict__ dp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtaRed red;
+  __shared__ int s_item;
+  const BatchDesc& d = *dp;
+  const int len = d.list_len[L_LU];
+  for (;;) {
+    int it = next_item(d, 8 + L_LU, &s_item);
+    if (it >= len) break;
+    int64_t s = d.lists[(int64_t)L_LU * d.capacity + it];
+    dense_system<0>(d, s, smem, red);
+  }
+}
+
+// ------------------------------------------------------------- triangular
+__global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __restrict__ dp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ CtaRed red;
+  __shared__ int s_item;
+  const BatchDesc& d = *dp;
+  const int len = d.list_len[L_TRI];
+  for (;;) {
+    int it = next_item(d, 8 + L_TRI, &s_item);
+    if (it >= len) break;
+    const int64_t s = d.lists[(int64_t)L_TRI * d.capacity + it];
+    const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
+    const double* A = d.A + d.a_off[s];
+    const double* B = d.B + d.b_off[s];
+    double* X = d.X + d.b_off[s];
+    const ScanRes sr = d.scan[s];
+    const bool lower = d.info[s].route == ASOLVE_ROUTE_TRI_LOWER;
+    DenseSlot sl = dense_slot(d, n);
+    bool zero = false;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (A[(size_t)i * n + i] == 0.0) zero = true;
+    const bool failed = __syncthreads_or(zero) != 0;
+    double rc = __longlong_as_double(0x7ff8000000000000ll);
+    if (!failed) {
+      double* xd = reinterpret_cast<double*>(smem);
+      for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = B[e];
+      cta_tri_solve<double, double>(A, n, n, lower, false, false, xd, n, nrhs);
+      for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
+      __syncthreads();
+      if (d.flags & ASOLVE_BERR) {
+        double be = berr_fp64(A, B, n, nrhs, sr.norminf, xd, sl.R, red);
+        if (threadIdx.x == 0) d.info[s].berr = be;
+      }
+      if (!(d.flags & ASOLVE_NO_RCOND)) {
+        double* v = reinterpret_cast<double*>(smem);
+        double* xi = v + n;
+        auto apply_est = [&](double* x, bool tr) {
+          cta_tri_solve<double, double>(A, n, n, lower, tr, false, x, n, 1);
+        };
+        double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
+        rc = rcond_from(sr.norm1, est);
+      }
+    }
+    __syncthreads();
+    finish_primary(d, s, failed, rc, X, (int64_t)n * nrhs);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ banded
+// Band factor storage (xGBTRF layout): element (i,j) at F[(kv+i-j) + j*ldf],
+// ldf = 2kl+ku+1, kv = kl+ku; rows 0..kl-1 are fill room for U.
+struct WarpBand {
+  double* F;
+  int* piv;
+  int n, kl, ku, kv, ldf;
+  __device__ double& at(int i, int j) const { return F[(size_t)(kv + i - j) + (size_t)j * ldf]; }
+};
+
+// Warp-scope GBTRF-equivalent.  Returns 0 or j+1 at an exact zero pivot.
+__device__ int warp_band_lu(WarpBand& b) {
+  const int lane = threadIdx.x & 31;
+  int ju = 0;
+  for (int j = 0; j < b.n; ++j) {
+    const int km = min(b.kl, b.n - 1 - j);
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int t = lane; t <= km; t += 32) {
+      double v = fabs(b.at(j + t, j));
+      if (v > best) { best = v; bi = t; }
+    }
+    warp_argmax_first(best, bi);
+    const int jp = bi;
+    if (lane == 0) b.piv[j] = j + jp;
+    const double pv = b.at(j + jp, j);
+    if (pv == 0.0) return j + 1;
+    ju = max(ju, min(j + b.ku + jp, b.n - 1));
+    __syncwarp();
+    if (jp != 0)
+      for (int c = j + lane; c <= ju; c += 32) {
+        double t0 = b.at(j, c);
+        b.at(j, c) = b.at(j + jp, c);
+        b.at(j + jp, c) = t0;
+      }
+    __syncwarp();
+    const double inv = 1.0 / b.at(j, j);
+    for (int t = 1 + lane; t <= km; t += 32) b.at(j + t, j) *= inv;
+    __syncwarp();
+    // rank-1 update of rows j+1..j+km, columns j+1..ju
+    const int ncol = ju - j;
+    if (km > 0)
+      for (int e = lane; e < km * ncol; e += 32) {
+      const int t = 1 + e % km, c = j + 1 + e / km;
+      b.at(j + t, c) -= b.at(j + t, j) * b.at(j, c);
+    }
+    __syncwarp();
+  }
+  return 0;
+}
+
+// x <- inv(A) x (trans: inv(A)^T x) with the band factors, one vector.
+__device__ void warp_band_apply(const WarpBand& b, double* x, bool trans) {
+  const int lane = threadIdx.x & 31;
+  const int n = b.n;
+  if (!trans) {
+    for (int j = 0; j < n; ++j) {
+      const int km = min(b.kl, n - 1 - j);
+      const int p = b.piv[j];
+      __syncwarp();
+      double xj;
+      if (p != j) {
+        double a = x[j], c = x[p];
+        __syncwarp();
+        if (lane == 0) { x[j] = c; x[p] = a; }
+        xj = c;
+      } else {
+        xj = x[j];
+      }
+      __syncwarp();
+      for (int t = 1 + lane; t <= km; t += 32) x[j + t] -= b.at(j + t, j) * xj;
+    }
+    __syncwarp();
+    for (int i = n - 1; i >= 0; --i) {  // U x = y, column-oriented
+      __syncwarp();
+      const double xi = x[i] / b.at(i, i);
+      __syncwarp();
+      if (lane == 0) x[i] = xi;
+      const int lo = max(0, i - b.kv);
+      for (int r = lo + lane; r < i; r += 32) x[r] -= b.at(r, i) * xi;
+    }
+    __syncwarp();
+  } else {
+    for (int i = 0; i < n; ++i) {  // U^T z = b
+      const int lo = max(0, i - b.kv);
+      double sacc = 0.0;
+      for (int r = lo + lane; r < i; r += 32) sacc += b.at(r, i) * x[r];
+      sacc = warp_sum(sacc);
+      __syncwarp();
+      if (lane == 0) x[i] = (x[i] - sacc) / b.at(i, i);
+      __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {  // L_j^T then P_j, in reverse
+      const int km = min(b.kl, n - 1 - j);
+      double sacc = 0.0;
+      for (int t = 1 + lane; t <= km; t += 32) sacc += b.at(j + t, j) * x[j + t];
+      sacc = warp_sum(sacc);
+      __syncwarp();
+      if (lane == 0) {
+        double v = x[j] - sacc;
+        const int p = b.piv[j];
+        x[j] = x[p];
+        x[p] = v;
+        if (p == j) x[j] = v;
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+}
+
+// Warp-scope estimator (same iteration as cta_est_inv_norm1).
+__device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
+  const int lane = threadIdx.x & 31;
+  const int n = b.n;
+  for (int i = lane; i < n; i += 32) v[i] = 1.0 / (double)n;
+  __syncwarp();
+  warp_band_apply(b, v, false);
+  if (n == 1) return fabs(v[0]);
+  auto sum_abs = [&]() {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += fabs(v[i]);
+    return warp_sum(s);
+  };
+  auto argmax = [&]() {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      double a = fabs(v[i]);
+      if (a > best) { best = a; bi = i; }
+    }
+    warp_argmax_first(best, bi);
+    return bi;
+  };
+  double est = sum_abs();
+  for (int i = lane; i < n; i += 32) {
+    double sg = v[i] >= 0.0 ? 1.0 : -1.0;
+    xi[i] = sg;
+    v[i] = sg;
+  }
+  __syncwarp();
+  warp_band_apply(b, v, true);
+  int k = 2;
+  for (;;) {
+    const int j = argmax();
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) v[i] = (i == j) ? 1.0 : 0.0;
+    __syncwarp();
+    warp_band_apply(b, v, false);
+    const double estold = est;
+    est = sum_abs();
+    bool same = true;
+    for (int i = lane; i < n; i += 32)
+      if ((v[i] >= 0.0 ? 1.0 : -1.0) != xi[i]) same = false;
+    same = __all_sync(0xffffffffu, same);
+    if (same || est <= estold) break;
+    for (int i = lane; i < n; i += 32) {
+      double sg = v[i] >= 0.0 ? 1.0 : -1.0;
+      xi[i] = sg;
+      v[i] = sg;
+    }
+    __syncwarp();
+    warp_band_apply(b, v, true);
+    const int jn = argmax();
+    ++k;
+    const double vj = v[j], vjn = fabs(v[jn]);
+    __syncwarp();
+    if (vj == vjn || k > 5) break;
+  }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32) v[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
+  __syncwarp();
+  warp_band_apply(b, v, false);
+  double temp = 2.0 * sum_abs() / (double)(3 * n);
+  return temp > est ? temp : est;
+}
+
+// One warp per banded system.  Each warp owns 1/8 of its CTA's slot; a
+// system whose band storage does not fit there is left for the second
+// phase, where warp 0 of a CTA uses the whole slot.
+__global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __restrict__ dp) {
+  const BatchDesc& d = *dp;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int len = d.list_len[L_BAND];
+  const size_t sub = (size_t)d.slot_bytes / kWarps;
+  for (int phase = 0; phase < 2; ++phase) {
+    if (phase == 1) {
+      __syncthreads();
+      if (w != 0) return;
+    }
+    char* base = d.slot_base + (size_t)blockIdx.x * d.slot_bytes + (phase == 0 ? w * sub : 0);
+    const size_t avail = phase == 0 ? sub : (size_t)d.slot_bytes;
+    for (;;) {
+      int it = 0;
+      if (lane == 0) it = atomicAdd(&d.work_ctr[8 + L_BAND + (phase ? 8 : 0)], 1);
+      it = __shfl_sync(0xffffffffu, it, 0);
+      if (it >= len) break;
+      const int64_t s = d.lists[(int64_t)L_BAND * d.capacity + it];
+      const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
+      const ScanRes sr = d.scan[s];
+      WarpBand b;
+      b.n = n; b.kl = sr.kl; b.ku = sr.ku; b.kv = sr.kl + sr.ku; b.ldf = 2 * sr.kl + sr.ku + 1;
+      const size_t fbytes = ((size_t)b.ldf * n * 8 + 255) & ~(size_t)255;
+      const size_t need = fbytes + (size_t)n * 4 + 3 * (size_t)n * 8 + 1024;
+      const bool fits = need <= sub;
+      if (phase == 0 ? !fits : (fits || need > avail)) {
+        if (phase == 1 && !fits && need > avail && lane == 0) {
+          d.info[s].status = ASOLVE_E_UNSUPPORTED;  // cannot happen for n <= 1024
+        }
+        continue;
+      }
+      b.F = reinterpret_cast<double*>(base);
+      b.piv = reinterpret_cast<int*>(base + fbytes);
+      double* v = reinterpret_cast<double*>(base + fbytes + (((size_t)n * 4 + 255) & ~(size_t)255));
+      double* xi = v + n;
+      double* xv = xi + n;
+      const double* A = d.A + d.a_off[s];
+      const double* B = d.B + d.b_off[s];
+      double* X = d.X + d.b_off[s];
+      // pack (Sec. 2.1 compact storage) with zeroed fill rows
+      for (int64_t e = lane; e < (int64_t)b.ldf * n; e += 32) b.F[e] = 0.0;
+      __syncwarp();
+      for (int j = 0; j < n; ++j) {
+        const int lo = max(0, j - b.ku), hi = min(n - 1, j + b.kl);
+        for (int i = lo + lane; i <= hi; i += 32) b.at(i, j) = A[(size_t)j * n + i];
+      }
+      __syncwarp();
+      const int f = warp_band_lu(b);
+      const bool failed = f != 0;
+      double rc = __longlong_as_double(0x7ff8000000000000ll);
+      if (!failed) {
+        for (int c = 0; c < nrhs; ++c) {
+          for (int i = lane; i < n; i += 32) xv[i] = B[(size_t)c * n + i];
+          __syncwarp();
+          warp_band_apply(b, xv, false);
+          for (int i = lane; i < n; i += 32) X[(size_t)c * n + i] = xv[i];
+          __syncwarp();
+        }
+        if (!(d.flags & ASOLVE_NO_RCOND)) rc = rcond_from(sr.norm1, warp_est_inv_norm1(b, v, xi));
+      }
+      finish_primary_warp(d, s, failed, rc, X, (int64_t)n * nrhs);
+      __syncwarp();
+    }
+  }
+}
+
+// ------------------------------------------------------------------- SVD
+// One-sided Jacobi (Hestenes) with the round-robin parallel ordering; a pair
+// (p < q) is rotated when |g_p.g_q| > n eps ||g_p|| ||g_q||; sweeps end after
+// one without rotation (at most 30).  Then x = sum_{sigma_i > tau} v_i
+// (u_i^T b) / sigma_i with u_i = g_i / sigma_i (Sec. 2.5).
+__device__ int cta_jacobi_svd(double* G, double* V, int n, double* sigma, int* s_rot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    int r = (int)(e % n), c = (int)(e / n);
+    V[e] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int np = (n + 1) & ~1;  // players; index n (odd n) is a dummy
+  const double tol = (double)n * kEps;
+  int sweep = 0;
+  for (; sweep < 30; ++sweep) {
+    if (threadIdx.x == 0) *s_rot = 0;
+    __syncthreads();
+    bool rotated = false;
+    for (int r = 0; r < np - 1; ++r) {
+      for (int pi = w; pi < np / 2; pi += kWarps) {
+        int a, b;
+        auto pos = [&](int k) { return 1 + (k + r) % (np - 1); };
+        if (pi == 0) { a = 0; b = pos(0); }
+        else { a = pos(pi); b = pos(np - 1 - pi); }
+        int p = min(a, b), q = max(a, b);
+        if (q >= n) continue;
+        double* gp = G + (size_t)p * n;
+        double* gq = G + (size_t)q * n;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int k = lane; k < n; k += 32) {
+          double x = gp[k], y = gq[k];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        double* vp = V + (size_t)p * n;
+        double* vq = V + (size_t)q * n;
+        for (int k = lane; k < n; k += 32) {
+          double x = gp[k], y = gq[k];
+          gp[k] = c * x - sn * y;
+          gq[k] = sn * x + c * y;
+          double u = vp[k], z = vq[k];
+          vp[k] = c * u - sn * z;
+          vq[k] = sn * u + c * z;
+        }
+        rotated = true;
+      }
+      __syncthreads();
+    }
+    if (rotated) *s_rot = 1;
+    __syncthreads();
+    const int any = *s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  for (int j = w; j < n; j += kWarps) {
+    double sacc = 0.0;
+    const double* g = G + (size_t)j * n;
+    for (int k = lane; k < n; k += 32) sacc = fma(g[k], g[k], sacc);
+    sacc = warp_sum(sacc);
+    if (lane == 0) sigma[j] = sqrt(sacc);
+  }
+  __syncthreads();
+  return sweep;
+}
+
+__device__ int64_t cta_svd_solve(const double* __restrict__ A, const double* __restrict__ B, int n,
+                                 int nrhs, double trunc_rel, double* X, double* G, double* V,
+                                 double* sigma, double* wv, int* s_rot, CtaRed& red) {
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) G[e] = A[e];
+  __syncthreads();
+  cta_jacobi_svd(G, V, n, sigma, s_rot);
+  double smax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) smax = fmax(smax, sigma[i]);
+  smax = cta_max(smax, red);
+  const double tau = (trunc_rel > 0.0 ? trunc_rel : (double)n * kEps) * smax;
+  int64_t rank = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rank += sigma[i] > tau ? 1 : 0;
+  rank = (int64_t)cta_sum((double)rank, red);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < nrhs; ++c) {
+    const double* b = B + (size_t)c * n;
+    __syncthreads();
+    for (int i = w; i < n; i += kWarps) {
+      const double si = sigma[i];
+      double wi = 0.0;
+      if (si > tau) {
+        const double* g = G + (size_t)i * n;
+        double dsum = 0.0;
+        for (int k = lane; k < n; k += 32) dsum += (g[k] / si) * b[k];
+        dsum = warp_sum(dsum);
+        wi = dsum / si;
+      }
+      if (lane == 0) wv[i] = wi;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      double x = 0.0;
+      for (int i = 0; i < n; ++i) x += V[(size_t)i * n + r] * wv[i];
+      X[(size_t)c * n + r] = x;
+    }
+  }
+  __syncthreads();
+  return rank;
+}
+
+__global__ void __launch_bounds__(kThreads) k_svd_class(const BatchDesc* __restrict__ dp) {
+  __shared__ CtaRed red;
+  __shared__ int s_item, s_rot;
+  const BatchDesc& d = *dp;
+  const int len = *(volatile int*)&d.list_len[L_SVD];
+  for (;;) {
+    int it = next_item(d, 8 + L_SVD, &s_item);
+    if (it >= len) break;
+    const int64_t s = d.lists[(int64_t)L_SVD * d.capacity + it];
+    const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
+    char* base = d.slot_base + (size_t)blockIdx.x * d.slot_bytes;
+    double* G = reinterpret_cast<double*>(base);
+    double* V = G + (size_t)n * n;
+    double* sigma = V + (size_t)n * n;
+    double* wv = sigma + n;
+    int64_t rank = cta_svd_solve(d.A + d.a_off[s], d.B + d.b_off[s], n, nrhs, d.svd_trunc_rel,
+                                 d.X + d.b_off[s], G, V, sigma, wv, &s_rot, red);
+    if (threadIdx.x == 0) {
+      d.info[s].svd_rank = rank;
+      d.info[s].status = ASOLVE_W_APPROX;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------- launchers
+size_t dense_slot_bytes(int nmax) {
+  size_t w = ((size_t)8 * ((nmax + 3) & ~3) * nmax + 255) & ~(size_t)255;
+  size_t svd = 2 * (size_t)8 * nmax * nmax + 2 * (size_t)8 * nmax + 1024;
+  size_t dense = w + 4096 * 2 + (size_t)8 * 8 * nmax + 1024;
+  return ((svd > dense ? svd : dense) + 4095) & ~(size_t)4095;
+}
+
+cudaError_t set_class_attrs() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_chol_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lu_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_tri_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+  if (e != cudaSuccess) return e;
+  done = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_route(const BatchDesc* d, cudaStream_t st) {
+  k_route<<<1, 1024, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_band(const BatchDesc* d, int grid, cudaStream_t st) {
+  k_band_class<<<grid, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_tri(const BatchDesc* d, int grid, cudaStream_t st) {
+  k_tri_class<<<grid, kThreads, kDenseSmem, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_chol(const BatchDesc* d, int grid, cudaStream_t st) {
+  k_chol_class<<<grid, kThreads, kDenseSmem, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_lu(const BatchDesc* d, int grid, cudaStream_t st) {
+  k_lu_class<<<grid, kThreads, kDenseSmem, st>>>(d);
+  return cudaGetLastError();
+}
+cudaError_t launch_svd(const BatchDesc* d, int grid, cudaStream_t st) {
+  k_svd_class<<<grid, kThreads, 0, st>>>(d);
+  return cudaGetLastError();
+}
+
+}  // namespace asv

@@ -1,0 +1,186 @@
+"""GPU parity of the single-system adaptive solve against the oracle.
+
+Bar (stated by the task's numerical contract):
+  - class, kl, ku and route identical to the oracle;
+  - X within the forward-error bound 2^-52 * n * kappa_inf(A) of the
+    oracle's X (both sides' own rounding is inside that bound);
+  - normwise backward error of the returned X <= 1e-13 (checked with the
+    oracle's compensated residual);
+  - rcond: within 1e-5 relative of the oracle for the FP64 route, within a
+    factor 3 for the FP32-factor estimate of the mixed route (both are
+    lower-bound estimates of ||inv(A)||_1, i.e. rcond >= true rcond);
+  - SVD solutions within 1e-10 relative under the same truncation.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import EPS, fwd_err, kappa_inf, solve_gpu
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 5, 31, 32, 33, 100, 200, 257, 512, 777, 1024]
+
+
+@pytest.fixture(scope="module", params=["fp64", "mixed"])
+def ctx(request):
+    from paper_2007_11208_gb300 import asolve, build
+    build.build()
+    prec = asolve.PREC_FP64 if request.param == "fp64" else asolve.PREC_MIXED
+    c = asolve.Context(precision=prec)
+    c.prec = request.param
+    yield c
+    c.close()
+
+
+def make(kind, n, rng):
+    if kind == "general":
+        return rng.standard_normal((n, n)) + 2 * np.sqrt(n) * np.eye(n)
+    if kind == "general_raw":
+        return rng.standard_normal((n, n))
+    if kind == "spd":
+        G = rng.standard_normal((n, n))
+        S = G.T @ G / n + np.eye(n)
+        return np.tril(S) + np.tril(S, -1).T
+    if kind == "lower":
+        A = np.tril(rng.standard_normal((n, n)), -1)
+        return A + np.diag(1 + np.abs(rng.standard_normal(n)) + np.abs(A).sum(1))
+    if kind == "upper":
+        A = np.triu(rng.standard_normal((n, n)), 1)
+        return A + np.diag(1 + np.abs(rng.standard_normal(n)) + np.abs(A).sum(1))
+    if kind == "tridiag":
+        return (np.diag(4 + np.abs(rng.standard_normal(n))) +
+                np.diag(rng.standard_normal(n - 1), 1) + np.diag(rng.standard_normal(n - 1), -1))
+    if kind == "band":
+        kl, ku = max(1, n // 40), max(1, n // 50)
+        A = np.zeros((n, n))
+        for d in range(-kl, ku + 1):
+            A += np.diag(rng.standard_normal(n - abs(d)), d)
+        return A
+    raise ValueError(kind)
+
+
+def check_against_oracle(orc, A, B, rc, info, X, mixed):
+    Xo, io = orc.solve(A, B)
+    assert info["cls"] == io["cls"] and info["kl"] == io["kl"] and info["ku"] == io["ku"], (info, io)
+    assert info["route"] == io["route"], (info, io)
+    assert rc == io["status"] and info["status"] == io["status"], (rc, info, io)
+    if io["status"] == 0:
+        n = A.shape[0]
+        k = kappa_inf(A)
+        assert fwd_err(X, Xo) <= 2.0 ** -52 * n * k, (fwd_err(X, Xo), n, k, info)
+        _, berr = orc.residual_dot2(A, X, B)
+        assert berr.max() <= 1e-13, (berr, info)
+        if not mixed or info["precision"] == 0:
+            assert abs(info["rcond"] - io["rcond"]) <= 1e-5 * io["rcond"] or \
+                (io["rcond"] / 3 <= info["rcond"] <= io["rcond"] * 3), (info["rcond"], io["rcond"])
+        else:
+            assert io["rcond"] / 3 <= info["rcond"] <= io["rcond"] * 3, (info["rcond"], io["rcond"])
+
+
+@pytest.mark.parametrize("kind", ["general", "general_raw", "spd", "lower", "upper", "tridiag", "band"])
+def test_routes_sizes(ctx, orc, kind):
+    rng = np.random.default_rng(abs(hash(kind)) % 1000)
+    for n in SIZES:
+        if kind in ("tridiag", "band") and n < 3:
+            continue
+        A = make(kind, n, rng)
+        nrhs = 1 + (n % 3)
+        B = rng.standard_normal((n, nrhs))
+        rc, info, X = solve_gpu(ctx, A, B)
+        check_against_oracle(orc, A, B, rc, info, X, ctx.prec == "mixed")
+
+
+def test_fig1_examples(ctx, orc):
+    for A in ([[1, 9, 0, 0, 0], [6, 2, 8, 0, 0], [0, 7, 3, 7, 0], [0, 0, 8, 4, 6], [0, 0, 0, 9, 5]],
+              [[1, 0, 0, 0, 0], [2, 6, 0, 0, 0], [3, 7, 1, 0, 0], [4, 8, 2, 4, 0], [5, 9, 3, 5, 6]],
+              [[9, 1, 2, 3, 4], [1, 8, 1, 2, 3], [2, 1, 7, 1, 2], [3, 2, 1, 6, 1], [4, 3, 2, 1, 5]]):
+        A = np.array(A, dtype=np.float64)
+        B = np.arange(1.0, 6.0)
+        rc, info, X = solve_gpu(ctx, A, B)
+        check_against_oracle(orc, A, B.reshape(5, 1), rc, info, X, ctx.prec == "mixed")
+
+
+def test_chol_fail_to_lu(ctx, orc):
+    A = np.array([[1, .9, .9], [.9, 1, -.9], [.9, -.9, 1]])
+    B = np.ones(3)
+    rc, info, X = solve_gpu(ctx, A, B)
+    assert info["cls"] == 4 and info["route"] == 5 and rc == 0
+    assert np.abs(A @ X[:, 0] - 1).max() < 1e-13
+
+
+def test_svd_fallbacks(ctx, orc):
+    rng = np.random.default_rng(5)
+    # exact zero pivot -> SVD (zero column)
+    A = rng.standard_normal((60, 60))
+    A[:, 11] = 0.0
+    B = rng.standard_normal(60)
+    rc, info, X = solve_gpu(ctx, A, B)
+    Xo, io = orc.solve(A, B)
+    assert rc == 1 and info["svd_rank"] == io["svd_rank"] == 59 and info["route"] == io["route"]
+    assert fwd_err(X, Xo) <= 1e-10
+    # zero matrix, banded route -> SVD, X = 0
+    rc, info, X = solve_gpu(ctx, np.zeros((8, 8)), np.ones(8))
+    assert rc == 1 and info["route"] == 1 and info["svd_rank"] == 0 and np.all(X == 0)
+    # Hilbert 12: rcond far below 0.5 eps -> SVD
+    H = np.array([[1.0 / (i + j + 1) for j in range(12)] for i in range(12)])
+    rc, info, X = solve_gpu(ctx, H, np.ones(12))
+    Xo, io = orc.solve(H, np.ones(12))
+    assert rc == io["status"] == 1 and info["route"] == io["route"]
+    # gapped rank-deficient matrix: x within 1e-10 of the oracle's SVD solve
+    n, k = 80, 5
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = (U * np.concatenate([np.logspace(0, -3, n - k), np.zeros(k)])) @ V.T
+    B = rng.standard_normal((n, 2))
+    rc, info, X = solve_gpu(ctx, A, B)
+    Xo, io = orc.solve(A, B)
+    assert rc == io["status"] == 1 and info["svd_rank"] == io["svd_rank"] == n - k
+    assert fwd_err(X, Xo) <= 1e-10
+
+
+def test_force_svd_and_force_lu(ctx, orc):
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((40, 40)) + 8 * np.eye(40)
+    B = rng.standard_normal(40)
+    rc, info, X = solve_gpu(ctx, A, B, asolve.FORCE_SVD)
+    Xo, io = orc.solve(A, B, flags=orc.FORCE_SVD)
+    assert rc == 1 and info["route"] == 7 and fwd_err(X, Xo) <= 1e-10
+    T = np.tril(rng.standard_normal((40, 40))) + 10 * np.eye(40)
+    rc, info, X = solve_gpu(ctx, T, B, asolve.FORCE_LU)
+    Xo, io = orc.solve(T, B, flags=orc.FORCE_LU)
+    assert rc == 0 and info["route"] == 6 and info["cls"] == 2
+    assert fwd_err(X, Xo) <= 2.0 ** -52 * 40 * kappa_inf(T)
+
+
+def test_no_approx_and_errors(ctx, orc):
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((30, 30))
+    A[:, 3] = 0.0
+    rc, info, X = solve_gpu(ctx, A, np.ones(30), asolve.NO_APPROX)
+    assert rc == asolve.E_SINGULAR and np.all(X == 0)
+    A = np.eye(10)
+    A[2, 3] = np.nan
+    rc, info, X = solve_gpu(ctx, A, np.ones(10))
+    assert rc == asolve.E_NONFINITE
+    rc, info, X = solve_gpu(ctx, np.eye(10), np.full(10, np.inf))
+    assert rc == asolve.E_NONFINITE
+
+
+def test_threshold_config(orc):
+    """Graded system U diag(logspace(0,-14)) V^T at n = 200 (Haar U, V): with
+    the paper's threshold it is solved by LU; with rcond_threshold = 1e-13 it
+    goes to the SVD, on both sides."""
+    from paper_2007_11208_gb300 import asolve, synth
+    import torch
+    g = synth.gen(0)
+    M = synth.ill(200, g, k=14.0).numpy().T
+    B = np.random.default_rng(0).standard_normal(200)
+    for thr, svd in ((0.5 * EPS, False), (1e-13, True)):
+        c = asolve.Context(precision=asolve.PREC_FP64, rcond_threshold=thr)
+        rc, info, X = solve_gpu(c, M, B)
+        Xo, io = orc.solve(M, B, cfg=orc.config(rcond_threshold=thr))
+        assert info["route"] == io["route"] == 6
+        assert (rc == 1) == svd and (io["status"] == 1) == svd
+        c.close()
