@@ -175,22 +175,29 @@ __device__ __forceinline__ int next_item(const BatchDesc& d, int ctr, int* s_ite
   return it;
 }
 
-// Dense-class dynamic shared memory: 104 KB.
-constexpr int kDenseSmem = 104 * 1024;
+// Dense-class dynamic shared memory: 110 KB (two blocks per SM).
+constexpr int kDenseSmem = 110 * 1024;
 
+// Panel width: the n x nb panel plus the 32 x 33 inverse and two 32 x 64
+// tiles must fit in kDenseSmem.
 template <typename T>
 __device__ __forceinline__ int pick_nb(int n) {
-  const int budget = 96 * 1024;
+  const size_t extra = (32 * 33 + 8 + 32 * 65 + 8 + 32 * 64) * sizeof(T) + 64;
   int nb = 32;
-  while (nb > 4 && (size_t)(n + 64) * nb * sizeof(T) > (size_t)budget) nb >>= 1;
+  while (nb > 4 && (size_t)n * nb * sizeof(T) + extra > (size_t)kDenseSmem) nb >>= 1;
   return nb;
 }
 
-// Slot layout of the dense classes: [W (8 * ldw * n)] [piv] [R (n*8 doubles)]
+// Slot layout of the dense classes: [W (8 * ldw * n)] [piv | perm] [R] [tmp]
+// [Linv] [Uinv]; R and tmp hold n x 8 doubles, Linv/Uinv 32 x 32 blocks.
 struct DenseSlot {
   void* W;
   int* piv;
+  int* perm;
   double* R;
+  double* tmp;
+  void* Linv;
+  void* Uinv;
 };
 __device__ __forceinline__ DenseSlot dense_slot(const BatchDesc& d, int n) {
   char* base = d.slot_base + (size_t)blockIdx.x * d.slot_bytes;
@@ -198,16 +205,17 @@ __device__ __forceinline__ DenseSlot dense_slot(const BatchDesc& d, int n) {
   const size_t wbytes = ((size_t)8 * round4(n) * n + 255) & ~(size_t)255;
   s.W = base;
   s.piv = reinterpret_cast<int*>(base + wbytes);
-  s.R = reinterpret_cast<double*>(base + wbytes + 4096 * 2);
+  s.perm = s.piv + 1024;
+  s.R = reinterpret_cast<double*>(base + wbytes + 8192);
+  s.tmp = s.R + (size_t)8 * 1024;
+  s.Linv = reinterpret_cast<void*>(s.tmp + (size_t)8 * 1024);
+  s.Uinv = reinterpret_cast<char*>(s.Linv) + (size_t)8 * 32 * 1024;
   return s;
 }
 
 template <typename T>
 __device__ void copy_to_work(const double* __restrict__ A, int n, T* W, int ldw) {
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    W[(size_t)c * ldw + r] = (T)__ldg(A + e);
-  }
+  cta_copy_block<T, double>(W, ldw, A, n, n, n);
   __syncthreads();
 }
 
@@ -314,19 +322,26 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   const int ldw = round4(n);
   const bool no_rcond = (d.flags & ASOLVE_NO_RCOND) != 0;
   int detail = 0;
-  // ---- mixed precision attempt
-  if (d.precision == ASOLVE_PREC_MIXED) {
+  // ---- mixed precision attempt (not when magnitudes leave the FP32 range)
+  if (d.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
     float* W = reinterpret_cast<float*>(sl.W);
     copy_to_work<float>(A, n, W, ldw);
     const int nb = pick_nb<float>(n);
-    int f = KIND == 0 ? cta_lu_factor<float>(W, ldw, n, sl.piv, reinterpret_cast<float*>(smem), nb, red)
-                      : cta_chol_factor<float>(W, ldw, n, reinterpret_cast<float*>(smem), nb, red);
+    int f = KIND == 0 ? cta_lu_factor<float>(W, ldw, n, sl.piv, reinterpret_cast<float*>(smem), nb)
+                      : cta_chol_factor<float>(W, ldw, n, reinterpret_cast<float*>(smem), nb);
+    if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);
     if (f == 0) {
+      float* Li = reinterpret_cast<float*>(sl.Linv);
+      float* Ui = reinterpret_cast<float*>(sl.Uinv);
+      float* tmp = reinterpret_cast<float*>(sl.tmp);
+      cta_block_inverses<float>(W, ldw, n, true, KIND == 0, Li);
+      if (KIND == 0) cta_block_inverses<float>(W, ldw, n, false, false, Ui);
       float* v = reinterpret_cast<float*>(smem);
       float* xi = v + n;
+      float* stage = reinterpret_cast<float*>(smem + 8192 * 2 + 64);  // after v, xi (n <= 1024)
       auto apply_est = [&](float* x, bool tr) {
-        if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.piv, x, n, 1, tr);
-        else cta_chol_apply<float, float>(W, ldw, n, x, n, 1);
+        if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.perm, x, n, 1, tr, tmp, Li, Ui, stage);
+        else cta_chol_apply<float, float>(W, ldw, n, x, n, 1, Li, stage);
       };
       double rc = __longlong_as_double(0x7ff8000000000000ll);
       bool gate_ok = true;
@@ -336,17 +351,18 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
         gate_ok = rc >= 1.0 / d.ir_kappa_limit;
       }
       if (gate_ok) {
-        double* xd = reinterpret_cast<double*>(smem);
-        float* xs = reinterpret_cast<float*>(xd + (size_t)n * nrhs);
+        // FP64 iterate lives in X (global); FP32 correction and the
+        // transposed-update stage in shared memory
+        float* xs = reinterpret_cast<float*>(smem);
+        float* stage = reinterpret_cast<float*>(smem + (size_t)4 * 1024 * 8 + 64);
         auto apply32 = [&](float* x) {
-          if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.piv, x, n, nrhs, false);
-          else cta_chol_apply<float, float>(W, ldw, n, x, n, nrhs);
+          if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.perm, x, n, nrhs, false, tmp, Li, Ui, stage);
+          else cta_chol_apply<float, float>(W, ldw, n, x, n, nrhs, Li, stage);
         };
         double berr;
         int iters;
-        bool ok = refine(d, A, B, n, nrhs, sr.norminf, xd, xs, sl.R, apply32, berr, iters, red);
+        bool ok = refine(d, A, B, n, nrhs, sr.norminf, X, xs, sl.R, apply32, berr, iters, red);
         if (ok) {
-          for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
           if (threadIdx.x == 0) {
             inf->rcond = rc;
             inf->berr = berr;
@@ -370,8 +386,9 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   double* W = reinterpret_cast<double*>(sl.W);
   copy_to_work<double>(A, n, W, ldw);
   const int nb = pick_nb<double>(n);
-  int f = KIND == 0 ? cta_lu_factor<double>(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), nb, red)
-                    : cta_chol_factor<double>(W, ldw, n, reinterpret_cast<double*>(smem), nb, red);
+  int f = KIND == 0 ? cta_lu_factor<double>(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), nb)
+                    : cta_chol_factor<double>(W, ldw, n, reinterpret_cast<double*>(smem), nb);
+  if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);
   if (threadIdx.x == 0) {
     inf->detail |= detail;
     inf->precision = ASOLVE_PREC_FP64;
@@ -385,7 +402,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   if (!failed) {
     double* xd = reinterpret_cast<double*>(smem);
     for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = B[e];
-    if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.piv, xd, n, nrhs, false);
+    if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, xd, n, nrhs, false, sl.tmp);
     else cta_chol_apply<double, double>(W, ldw, n, xd, n, nrhs);
     for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
     __syncthreads();
@@ -394,10 +411,12 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
       if (threadIdx.x == 0) inf->berr = be;
     }
     if (!no_rcond) {
+      // FP64 estimate by substitution: on an ill-conditioned factor a
+      // product with explicit block inverses would corrupt the estimate
       double* v = reinterpret_cast<double*>(smem);
       double* xi = v + n;
       auto apply_est = [&](double* x, bool tr) {
-        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.piv, x, n, 1, tr);
+        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, x, n, 1, tr, sl.tmp);
         else cta_chol_apply<double, double>(W, ldw, n, x, n, 1);
       };
       double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
@@ -517,9 +536,10 @@ __device__ int warp_band_lu(WarpBand& b) {
     }
     warp_argmax_first(best, bi);
     const int jp = bi;
+    if (jp < 0 || jp > km) return j + 1;  // only NaN candidates
     if (lane == 0) b.piv[j] = j + jp;
     const double pv = b.at(j + jp, j);
-    if (pv == 0.0) return j + 1;
+    if (pv == 0.0 || pv != pv) return j + 1;
     ju = max(ju, min(j + b.ku + jp, b.n - 1));
     __syncwarp();
     if (jp != 0)
@@ -638,6 +658,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
   int k = 2;
   for (;;) {
     const int j = argmax();
+    if (j < 0 || j >= n) return __longlong_as_double(0x7ff8000000000000ll);
     __syncwarp();
     for (int i = lane; i < n; i += 32) v[i] = (i == j) ? 1.0 : 0.0;
     __syncwarp();
@@ -658,6 +679,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
     warp_band_apply(b, v, true);
     const int jn = argmax();
     ++k;
+    if (jn < 0 || jn >= n) return __longlong_as_double(0x7ff8000000000000ll);
     const double vj = v[j], vjn = fabs(v[jn]);
     __syncwarp();
     if (vj == vjn || k > 5) break;
@@ -732,6 +754,30 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
           __syncwarp();
         }
         if (!(d.flags & ASOLVE_NO_RCOND)) rc = rcond_from(sr.norm1, warp_est_inv_norm1(b, v, xi));
+        if (d.flags & ASOLVE_BERR) {
+          // FP64 backward error over the band: r = b - A x, A read in band form
+          double berr = 0.0;
+          for (int c = 0; c < nrhs; ++c) {
+            const double* xc = X + (size_t)c * n;
+            const double* bc = B + (size_t)c * n;
+            double rm = 0.0, xm = 0.0, bm = 0.0;
+            for (int i = lane; i < n; i += 32) {
+              double acc = 0.0;
+              const int lo = max(0, i - sr.kl), hi = min(n - 1, i + sr.ku);
+              for (int j = lo; j <= hi; ++j) acc = fma(A[(size_t)j * n + i], xc[j], acc);
+              rm = fmax(rm, fabs(bc[i] - acc));
+              xm = fmax(xm, fabs(xc[i]));
+              bm = fmax(bm, fabs(bc[i]));
+            }
+            rm = warp_max(rm);
+            xm = warp_max(xm);
+            bm = warp_max(bm);
+            const double den = sr.norminf * xm + bm;
+            const double be = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+            if (!(be <= berr)) berr = be;
+          }
+          if (lane == 0) d.info[s].berr = berr;
+        }
       }
       finish_primary_warp(d, s, failed, rc, X, (int64_t)n * nrhs);
       __syncwarp();
@@ -744,137 +790,205 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
 // (p < q) is rotated when |g_p.g_q| > n eps ||g_p|| ||g_q||; sweeps end after
 // one without rotation (at most 30).  Then x = sum_{sigma_i > tau} v_i
 // (u_i^T b) / sigma_i with u_i = g_i / sigma_i (Sec. 2.5).
-__device__ int cta_jacobi_svd(double* G, double* V, int n, double* sigma, int* s_rot) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
-    int r = (int)(e % n), c = (int)(e / n);
-    V[e] = (r == c) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  const int np = (n + 1) & ~1;  // players; index n (odd n) is a dummy
-  const double tol = (double)n * kEps;
-  int sweep = 0;
-  for (; sweep < 30; ++sweep) {
-    if (threadIdx.x == 0) *s_rot = 0;
-    __syncthreads();
-    bool rotated = false;
-    for (int r = 0; r < np - 1; ++r) {
-      for (int pi = w; pi < np / 2; pi += kWarps) {
-        int a, b;
-        auto pos = [&](int k) { return 1 + (k + r) % (np - 1); };
-        if (pi == 0) { a = 0; b = pos(0); }
-        else { a = pos(pi); b = pos(np - 1 - pi); }
-        int p = min(a, b), q = max(a, b);
-        if (q >= n) continue;
-        double* gp = G + (size_t)p * n;
-        double* gq = G + (size_t)q * n;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int k = lane; k < n; k += 32) {
-          double x = gp[k], y = gq[k];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-        double* vp = V + (size_t)p * n;
-        double* vq = V + (size_t)q * n;
-        for (int k = lane; k < n; k += 32) {
-          double x = gp[k], y = gq[k];
-          gp[k] = c * x - sn * y;
-          gq[k] = sn * x + c * y;
-          double u = vp[k], z = vq[k];
-          vp[k] = c * u - sn * z;
-          vq[k] = sn * u + c * z;
-        }
-        rotated = true;
-      }
-      __syncthreads();
-    }
-    if (rotated) *s_rot = 1;
-    __syncthreads();
-    const int any = *s_rot;
-    __syncthreads();
-    if (!any) break;
-  }
-  for (int j = w; j < n; j += kWarps) {
-    double sacc = 0.0;
-    const double* g = G + (size_t)j * n;
-    for (int k = lane; k < n; k += 32) sacc = fma(g[k], g[k], sacc);
-    sacc = warp_sum(sacc);
-    if (lane == 0) sigma[j] = sqrt(sacc);
-  }
-  __syncthreads();
-  return sweep;
+//
+// A thread-block cluster of kSvdCluster CTAs works on one system: the
+// pairs of a round are spread over all warps of the cluster and rounds are
+// separated by hardware cluster barriers.  G = A V and V live in the
+// leader CTA's scratch slot (global memory, L2-resident).
+constexpr int kSvdCluster = 8;
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// address of `p` (this CTA's shared variable) in the shared memory of CTA `rank`
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+  unsigned a = (unsigned)__cvta_generic_to_shared(p), r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ int dsmem_ld(unsigned addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void dsmem_or(unsigned addr, int v) {
+  asm volatile("red.shared::cluster.or.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
-__device__ int64_t cta_svd_solve(const double* __restrict__ A, const double* __restrict__ B, int n,
-                                 int nrhs, double trunc_rel, double* X, double* G, double* V,
-                                 double* sigma, double* wv, int* s_rot, CtaRed& red) {
-  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) G[e] = A[e];
-  __syncthreads();
-  cta_jacobi_svd(G, V, n, sigma, s_rot);
-  double smax = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) smax = fmax(smax, sigma[i]);
-  smax = cta_max(smax, red);
-  const double tau = (trunc_rel > 0.0 ? trunc_rel : (double)n * kEps) * smax;
-  int64_t rank = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rank += sigma[i] > tau ? 1 : 0;
-  rank = (int64_t)cta_sum((double)rank, red);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = 0; c < nrhs; ++c) {
-    const double* b = B + (size_t)c * n;
-    __syncthreads();
-    for (int i = w; i < n; i += kWarps) {
-      const double si = sigma[i];
-      double wi = 0.0;
-      if (si > tau) {
-        const double* g = G + (size_t)i * n;
-        double dsum = 0.0;
-        for (int k = lane; k < n; k += 32) dsum += (g[k] / si) * b[k];
-        dsum = warp_sum(dsum);
-        wi = dsum / si;
-      }
-      if (lane == 0) wv[i] = wi;
-    }
-    __syncthreads();
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      double x = 0.0;
-      for (int i = 0; i < n; ++i) x += V[(size_t)i * n + r] * wv[i];
-      X[(size_t)c * n + r] = x;
+// One warp rotates the column pair (p, q) of G and V if they are not yet
+// orthogonal to the tolerance.  Returns true when it rotated.
+__device__ bool jacobi_pair(double* G, double* V, int n, int p, int q, double tol) {
+  const int lane = threadIdx.x & 31;
+  double* gp = G + (size_t)p * n;
+  double* gq = G + (size_t)q * n;
+  double xr[32], yr[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const int k = lane + 32 * t;
+    xr[t] = (k < n) ? gp[k] : 0.0;
+    yr[t] = (k < n) ? gq[k] : 0.0;
+  }
+  double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    al = fma(xr[t], xr[t], al);
+    be = fma(yr[t], yr[t], be);
+    ga = fma(xr[t], yr[t], ga);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (!(fabs(ga) > tol * sqrt(al) * sqrt(be))) return false;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int k = lane + 32 * u;
+    if (k < n) {
+      gp[k] = c * xr[u] - sn * yr[u];
+      gq[k] = sn * xr[u] + c * yr[u];
     }
   }
-  __syncthreads();
-  return rank;
+  double* vp = V + (size_t)p * n;
+  double* vq = V + (size_t)q * n;
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int k = lane + 32 * u;
+    xr[u] = (k < n) ? vp[k] : 0.0;
+    yr[u] = (k < n) ? vq[k] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int k = lane + 32 * u;
+    if (k < n) {
+      vp[k] = c * xr[u] - sn * yr[u];
+      vq[k] = sn * xr[u] + c * yr[u];
+    }
+  }
+  return true;
 }
 
-__global__ void __launch_bounds__(kThreads) k_svd_class(const BatchDesc* __restrict__ dp) {
-  __shared__ CtaRed red;
+__global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kThreads, 1)
+    k_svd_class(const BatchDesc* __restrict__ dp) {
   __shared__ int s_item, s_rot;
+  __shared__ double s_red[kWarps];
   const BatchDesc& d = *dp;
+  const unsigned crank = cluster_ctarank();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int cw = (int)crank * kWarps + w;        // warp index within the cluster
+  const int ncw = kSvdCluster * kWarps;           // warps per cluster
+  const int ctid = (int)crank * kThreads + threadIdx.x;
+  const int nct = kSvdCluster * kThreads;
+  const int leader_block = blockIdx.x - (int)crank;
+  const unsigned item_addr = dsmem_addr(&s_item, 0);
+  const unsigned rot_addr = dsmem_addr(&s_rot, 0);
   const int len = *(volatile int*)&d.list_len[L_SVD];
   for (;;) {
-    int it = next_item(d, 8 + L_SVD, &s_item);
+    if (crank == 0 && threadIdx.x == 0) s_item = atomicAdd(&d.work_ctr[8 + L_SVD], 1);
+    cluster_sync_all();
+    const int it = dsmem_ld(item_addr);
+    cluster_sync_all();
     if (it >= len) break;
     const int64_t s = d.lists[(int64_t)L_SVD * d.capacity + it];
     const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
-    char* base = d.slot_base + (size_t)blockIdx.x * d.slot_bytes;
+    const double* A = d.A + d.a_off[s];
+    const double* B = d.B + d.b_off[s];
+    double* X = d.X + d.b_off[s];
+    char* base = d.slot_base + (size_t)leader_block * d.slot_bytes;
     double* G = reinterpret_cast<double*>(base);
     double* V = G + (size_t)n * n;
     double* sigma = V + (size_t)n * n;
     double* wv = sigma + n;
-    int64_t rank = cta_svd_solve(d.A + d.a_off[s], d.B + d.b_off[s], n, nrhs, d.svd_trunc_rel,
-                                 d.X + d.b_off[s], G, V, sigma, wv, &s_rot, red);
-    if (threadIdx.x == 0) {
+    for (int64_t e = ctid; e < (int64_t)n * n; e += nct) {
+      G[e] = A[e];
+      V[e] = ((e % n) == (e / n)) ? 1.0 : 0.0;
+    }
+    cluster_sync_all();
+    const int np = (n + 1) & ~1;  // players; index n (odd n) is a dummy
+    const double tol = (double)n * kEps;
+    for (int sweep = 0; sweep < 30; ++sweep) {
+      if (crank == 0 && threadIdx.x == 0) s_rot = 0;
+      cluster_sync_all();
+      bool rotated = false;
+      for (int r = 0; r < np - 1; ++r) {
+        for (int pi = cw; pi < np / 2; pi += ncw) {
+          int a, b;
+          if (pi == 0) { a = 0; b = 1 + r % (np - 1); }
+          else { a = 1 + (pi + r) % (np - 1); b = 1 + (np - 1 - pi + r) % (np - 1); }
+          const int p = min(a, b), q = max(a, b);
+          if (q >= n) continue;
+          if (jacobi_pair(G, V, n, p, q, tol)) rotated = true;
+        }
+        cluster_sync_all();
+      }
+      if (__syncthreads_or(rotated) && threadIdx.x == 0) dsmem_or(rot_addr, 1);
+      cluster_sync_all();
+      const int any = dsmem_ld(rot_addr);
+      cluster_sync_all();
+      if (!any) break;
+    }
+    for (int j = cw; j < n; j += ncw) {
+      double sacc = 0.0;
+      const double* g = G + (size_t)j * n;
+      for (int k = lane; k < n; k += 32) sacc = fma(g[k], g[k], sacc);
+      sacc = warp_sum(sacc);
+      if (lane == 0) sigma[j] = sqrt(sacc);
+    }
+    cluster_sync_all();
+    // truncation threshold and rank (every CTA computes them redundantly)
+    double smax = 0.0;
+    for (int i = threadIdx.x; i < n; i += kThreads) smax = fmax(smax, sigma[i]);
+    smax = warp_max(smax);
+    if (lane == 0) s_red[w] = smax;
+    __syncthreads();
+    smax = 0.0;
+    for (int k = 0; k < kWarps; ++k) smax = fmax(smax, s_red[k]);
+    const double tau = (d.svd_trunc_rel > 0.0 ? d.svd_trunc_rel : (double)n * kEps) * smax;
+    int rank = 0;
+    for (int i = threadIdx.x; i < n; i += kThreads) rank += sigma[i] > tau ? 1 : 0;
+    __syncthreads();
+    {
+      int rr = warp_sum(rank);
+      __shared__ int s_rank[kWarps];
+      if (lane == 0) s_rank[w] = rr;
+      __syncthreads();
+      rank = 0;
+      for (int k = 0; k < kWarps; ++k) rank += s_rank[k];
+    }
+    for (int c = 0; c < nrhs; ++c) {
+      const double* bc = B + (size_t)c * n;
+      for (int i = cw; i < n; i += ncw) {
+        const double si = sigma[i];
+        double wi = 0.0;
+        if (si > tau) {
+          const double* g = G + (size_t)i * n;
+          double dsum = 0.0;
+          for (int k = lane; k < n; k += 32) dsum += (g[k] / si) * bc[k];
+          dsum = warp_sum(dsum);
+          wi = dsum / si;
+        }
+        if (lane == 0) wv[i] = wi;
+      }
+      cluster_sync_all();
+      for (int r = ctid; r < n; r += nct) {
+        double x = 0.0;
+        for (int i = 0; i < n; ++i) x += V[(size_t)i * n + r] * wv[i];
+        X[(size_t)c * n + r] = x;
+      }
+      cluster_sync_all();
+    }
+    if (crank == 0 && threadIdx.x == 0) {
       d.info[s].svd_rank = rank;
       d.info[s].status = ASOLVE_W_APPROX;
     }
-    __syncthreads();
+    cluster_sync_all();
   }
 }
 
@@ -882,7 +996,7 @@ __global__ void __launch_bounds__(kThreads) k_svd_class(const BatchDesc* __restr
 size_t dense_slot_bytes(int nmax) {
   size_t w = ((size_t)8 * ((nmax + 3) & ~3) * nmax + 255) & ~(size_t)255;
   size_t svd = 2 * (size_t)8 * nmax * nmax + 2 * (size_t)8 * nmax + 1024;
-  size_t dense = w + 4096 * 2 + (size_t)8 * 8 * nmax + 1024;
+  size_t dense = w + 8192 + 2 * (size_t)8 * 8 * 1024 + 2 * (size_t)8 * 32 * 1024 + 1024;
   return ((svd > dense ? svd : dense) + 4095) & ~(size_t)4095;
 }
 
@@ -921,6 +1035,7 @@ cudaError_t launch_lu(const BatchDesc* d, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_svd(const BatchDesc* d, int grid, cudaStream_t st) {
+  grid = (grid + kSvdCluster - 1) / kSvdCluster * kSvdCluster;
   k_svd_class<<<grid, kThreads, 0, st>>>(d);
   return cudaGetLastError();
 }

@@ -78,206 +78,284 @@ __device__ __forceinline__ void dmma_8x8x4(double& c0, double& c1, double a, dou
 }
 
 // ------------------------------------------------------------ GEMM update
-// C(m x nc) -= As(m x kb, smem, ld lda) * B(kb x nc, global, ld ldb); C global.
-// Only tiles with (row tile) >= (col tile) when lower_only (Cholesky SYRK).
-// Bs: smem staging of kb x 64 entries of B.
+// Trailing update of a blocked factorisation:  C(m x nc) -= As(m x kb) * Bt,
+// with As in shared memory (column-major, ld lda) and the kb x 64 tile Bt in
+// shared memory (row-major, Bt[k * 64 + c]).  C is global (column-major,
+// ld ldc).  With lower_only, row tiles entirely above the diagonal of C
+// (rows < cols, counting rows from row_off) are skipped.
+//
+// FP32: CTA tile 128 x 64; lane -> rows lane + 32 i (i < 4), warp -> 8
+// columns, so every global access of C is one 128-byte line per warp.
+// FP64: the 8x8x4 tensor instruction (mma.sync f64); warp tile 16 x 32.
 template <typename T>
-__device__ void cta_gemm_sub(T* C, int ldc, const T* As, int lda, const T* B, int ldb, int m, int nc,
-                             int kb, T* Bs, int row_off_for_lower, bool lower_only);
+__device__ void tile_gemm_sub(T* C, int ldc, const T* As, int lda, const T* Bt, int m, int nc, int kb,
+                              int col_off, bool lower_only);
 
-// FP32 SIMT: CTA tile 128 x 64, thread micro-tile 8 x 4.
 template <>
-__device__ void cta_gemm_sub<float>(float* C, int ldc, const float* As, int lda, const float* B,
-                                    int ldb, int m, int nc, int kb, float* Bs, int row_off,
-                                    bool lower_only) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int j0 = 0; j0 < nc; j0 += 64) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb * 64; e += kThreads) {
-      int k = e >> 6, c = e & 63;
-      Bs[e] = (j0 + c < nc) ? B[(size_t)(j0 + c) * ldb + k] : 0.f;
-    }
-    __syncthreads();
-    int istart = 0;
-    if (lower_only) istart = max(0, ((j0 + row_off) / 128) * 128 - row_off);
-    for (int i0 = istart; i0 < m; i0 += 128) {
-      const int r0 = i0 + ty * 8, c0 = j0 + tx * 4;
-      float acc[8][4];
+__device__ __noinline__ void tile_gemm_sub<float>(float* C, int ldc, const float* As, int lda,
+                                                  const float* Bt, int m, int nc, int kb, int col_off,
+                                                  bool lower_only) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int istart = lower_only ? (col_off / 128) * 128 : 0;
+  for (int i0 = istart; i0 < m; i0 += 128) {
+    float acc[4][8];
 #pragma unroll
-      for (int r = 0; r < 8; ++r)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-#pragma unroll 4
-      for (int k = 0; k < kb; ++k) {
-        float a[8], b[4];
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kb; ++k) {
+      float a[4];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) a[r] = (r0 + r < m) ? As[(size_t)k * lda + r0 + r] : 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) b[c] = Bs[k * 64 + tx * 4 + c];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+      for (int i = 0; i < 4; ++i) {
+        const int r = i0 + lane + 32 * i;
+        a[i] = (r < m) ? As[(size_t)k * lda + r] : 0.f;
       }
+      const float4 b0 = *reinterpret_cast<const float4*>(Bt + k * 64 + w * 8);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bt + k * 64 + w * 8 + 4);
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c0 + c >= nc) continue;
-        float* col = C + (size_t)(c0 + c) * ldc;
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
-          if (r0 + r < m) col[r0 + r] -= acc[r][c];
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = w * 8 + j;
+      if (c >= nc) continue;
+      float* col = C + (size_t)c * ldc;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = i0 + lane + 32 * i;
+        if (r < m) col[r] -= acc[i][j];
       }
     }
   }
-  __syncthreads();
 }
 
-// FP64 on the tensor path: CTA tile 64 x 64, warp tile 16 x 32 (2 x 4 mma tiles).
 template <>
-__device__ void cta_gemm_sub<double>(double* C, int ldc, const double* As, int lda, const double* B,
-                                     int ldb, int m, int nc, int kb, double* Bs, int row_off,
-                                     bool lower_only) {
+__device__ __noinline__ void tile_gemm_sub<double>(double* C, int ldc, const double* As, int lda,
+                                                   const double* Bt, int m, int nc, int kb, int col_off,
+                                                   bool lower_only) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int wr = (w & 3) * 16, wc = (w >> 2) * 32;
   const int kb4 = (kb + 3) & ~3;
-  for (int j0 = 0; j0 < nc; j0 += 64) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb4 * 64; e += kThreads) {
-      int k = e >> 6, c = e & 63;
-      Bs[e] = (k < kb && j0 + c < nc) ? B[(size_t)(j0 + c) * ldb + k] : 0.0;
-    }
-    __syncthreads();
-    int istart = 0;
-    if (lower_only) istart = max(0, ((j0 + row_off) / 64) * 64 - row_off);
-    for (int i0 = istart; i0 < m; i0 += 64) {
-      double acc[2][4][2];
+  const int istart = lower_only ? (col_off / 64) * 64 : 0;
+  for (int i0 = istart; i0 < m; i0 += 64) {
+    double acc[2][4][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+    for (int k = 0; k < kb4; k += 4) {
+      double af[2], bf[4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int r = i0 + wr + a * 8 + g;
+        af[a] = (r < m && k + t < kb) ? As[(size_t)(k + t) * lda + r] : 0.0;
+      }
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bf[b] = (k + t < kb) ? Bt[(k + t) * 64 + wc + b * 8 + g] : 0.0;
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
-      for (int k = 0; k < kb4; k += 4) {
-        double af[2], bf[4];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          int r = i0 + wr + a * 8 + g;
-          af[a] = (r < m && k + t < kb) ? As[(size_t)(k + t) * lda + r] : 0.0;
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) bf[b] = Bs[(k + t) * 64 + wc + b * 8 + g];
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) dmma_8x8x4(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
-      }
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        int r = i0 + wr + a * 8 + g;
-        if (r >= m) continue;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            int c = j0 + wc + b * 8 + 2 * t + q;
-            if (c < nc) C[(size_t)c * ldc + r] -= acc[a][b][q];
-          }
-        }
-      }
+        for (int b = 0; b < 4; ++b) dmma_8x8x4(acc[a][b][0], acc[a][b][1], af[a], bf[b]);
     }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      const int r = i0 + wr + a * 8 + g;
+      if (r >= m) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int c = wc + b * 8 + 2 * t + q;
+          if (c < nc) C[(size_t)c * ldc + r] -= acc[a][b][q];
+        }
+    }
+  }
+}
+
+// Inverse of the unit lower triangular kb x kb block L11 (panel rows 0..kb-1,
+// ld m) into Li (32 x 32, column-major, ld 33), by warp 0: lane j forms
+// column j.  Padded with the identity past kb.
+template <typename T>
+__device__ void unit_lower_inverse(const T* Pn, int m, int kb, T* Li) {
+  if (threadIdx.x < 32) {
+    const int j = threadIdx.x;
+    T x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      T s = (i == j) ? T(1) : T(0);
+#pragma unroll
+      for (int k = 0; k < i; ++k)
+        if (i < kb) s -= Pn[(size_t)k * m + i] * x[k];
+      x[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Li[j * 33 + i] = x[i];
+  }
+}
+
+// LU panel epilogue: U12 = inv(L11) A12 and A22 -= L21 U12, column block by
+// column block of 64.  Ta, Tu: smem tiles of 32 x 64.
+template <typename T>
+__device__ __noinline__ void cta_lu_update(T* W, int ldw, int n, int k0, int kb, const T* Pn, int m,
+                                           T* Li, T* Ta, T* Tu) {
+  unit_lower_inverse<T>(Pn, m, kb, Li);
+  const int j_lo = k0 + kb;
+  for (int j0 = j_lo; j0 < n; j0 += 64) {
+    const int nc = min(64, n - j0);
+    __syncthreads();
+    // stage A12 columns j0.. (rows k0..k0+kb-1): lanes over rows ->
+    // coalesced loads; row stride 65 keeps the stores conflict-free
+    for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
+      const int k = e & 31, c = e >> 5;
+      Ta[k * 65 + c] = (k < kb && c < nc) ? W[(size_t)(j0 + c) * ldw + k0 + k] : T(0);
+    }
+    __syncthreads();
+    // U tile = inv(L11) A12 tile
+    for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
+      const int c = e & 63, i = e >> 6;
+      T acc = T(0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc += Li[k * 33 + i] * Ta[k * 65 + c];
+      Tu[i * 64 + c] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
+      const int k = e & 31, c = e >> 5;
+      if (k < kb && c < nc) W[(size_t)(j0 + c) * ldw + k0 + k] = Tu[k * 64 + c];
+    }
+    const int mr = m - kb;
+    if (mr > 0)
+      tile_gemm_sub<T>(W + (size_t)j0 * ldw + k0 + kb, ldw, Pn + kb, m, Tu, mr, nc, kb, 0, false);
   }
   __syncthreads();
 }
 
-// --------------------------------------------------------------- LU factor
-// W: n x n (ld ldw), overwritten by L\U; piv[k] = row swapped with k.
-// smem: panel (m x nb of T) then Bs (nb x 64 of T).  Returns 0 or k+1 at an
-// exact zero pivot (stops there, as the solver then counts as failed).
+// Cholesky panel epilogue: A22 -= L21 L21^T on the lower triangle, column
+// block by column block; the B tile (L21^T) is staged from the panel.
 template <typename T>
-__device__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* smem, int nb, CtaRed& red) {
-  T* Pn = smem;  // panel: column-major, ld = m
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int kb = min(nb, n - k0), m = n - k0;
-    T* Bs = smem + (size_t)m * nb;
+__device__ __noinline__ void cta_chol_update(T* W, int ldw, int n, int k0, int kb, const T* Pn, int m, T* Tu) {
+  const int mr = m - kb;
+  for (int jc = 0; jc < mr; jc += 64) {
+    const int nc = min(64, mr - jc);
     __syncthreads();
-    for (int e = threadIdx.x; e < m * kb; e += kThreads) {
-      int r = e % m, c = e / m;
-      Pn[(size_t)c * m + r] = W[(size_t)(k0 + c) * ldw + k0 + r];
+    for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
+      const int c = e & 63, k = e >> 6;
+      Tu[k * 64 + c] = (k < kb && c < nc) ? Pn[(size_t)k * m + kb + jc + c] : T(0);
     }
     __syncthreads();
-    // unblocked LU of the m x kb panel; thread t owns rows t, t+256, ...
+    // rows jc.. of the trailing block (the diagonal tile and below)
+    tile_gemm_sub<T>(W + (size_t)(k0 + kb + jc) * ldw + k0 + kb + jc, ldw, Pn + kb + jc, m, Tu, mr - jc, nc, kb,
+                     0, false);
+  }
+  __syncthreads();
+}
+
+// 2-D copy of an m x nc column-major block (no integer division per element).
+template <typename D, typename S>
+__device__ __forceinline__ void cta_copy_block(D* dst, int ldd, const S* src, int lds, int m, int nc) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = w; c < nc; c += kWarps)
+    for (int r = lane; r < m; r += 32) dst[(size_t)c * ldd + r] = (D)src[(size_t)c * lds + r];
+}
+
+// Reduction record of the panel pivot search: magnitude, row, signed value.
+template <typename T>
+struct PivRed {
+  T mag[kWarps];
+  T val[kWarps];
+  int idx[kWarps];
+};
+
+// --------------------------------------------------------------- LU factor
+// W: n x n (ld ldw), overwritten by L\U; piv[k] = row swapped with k.
+// smem: panel (m x nb of T, ld m), then the L11 inverse and two 32 x 64
+// tiles (see cta_lu_update).  Returns 0, or
+// k+1 at an exact zero (or NaN-only) pivot, where it stops: the solver has
+// then failed.  Two barriers per panel column.
+template <typename T>
+__device__ __noinline__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* smem, int nb) {
+  __shared__ PivRed<T> pr;
+  __shared__ T prow[32];
+  T* Pn = smem;
+  // after the panel: L11 inverse (32 x 33) and two 32 x 64 tiles
+  T* Li = smem + (size_t)n * nb;
+  T* Ta = Li + 32 * 33 + 3;
+  Ta = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Ta) + 15) & ~(uintptr_t)15);
+  T* Tu = Ta + 32 * 65 + 4;
+  Tu = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Tu) + 15) & ~(uintptr_t)15);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int kb = min(nb, n - k0), m = n - k0;
+    __syncthreads();
+    cta_copy_block<T, T>(Pn, m, W + (size_t)k0 * ldw + k0, ldw, m, kb);
+    __syncthreads();
     for (int c = 0; c < kb; ++c) {
-      T best = T(-1);
+      // pivot search over this thread's rows (written by this thread only)
+      T best = T(-1), bval = T(0);
       int bi = 0x7fffffff;
       for (int r = c + threadIdx.x; r < m; r += kThreads) {
-        T v = fabs(Pn[(size_t)c * m + r]);
-        if (v > best) { best = v; bi = r; }
+        const T v = Pn[(size_t)c * m + r];
+        const T a = fabs(v);
+        if (a > best) { best = a; bi = r; bval = v; }
       }
-      const int p = cta_argmax_first<T>(best, bi, red);  // contains __syncthreads
-      const T pv = Pn[(size_t)c * m + p];
-      if (pv == T(0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, bval, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bval = ov; }
+      }
+      if (lane == 0) { pr.mag[w] = best; pr.idx[w] = bi; pr.val[w] = bval; }
+      __syncthreads();  // S1
+      T bm = pr.mag[0], pv = pr.val[0];
+      int p = pr.idx[0];
+#pragma unroll
+      for (int k = 1; k < kWarps; ++k)
+        if (pr.mag[k] > bm || (pr.mag[k] == bm && pr.idx[k] < p)) { bm = pr.mag[k]; p = pr.idx[k]; pv = pr.val[k]; }
+      if (p < c || p >= m || pv == T(0) || pv != pv) {
         __syncthreads();
         return k0 + c + 1;
       }
-      if (threadIdx.x == 0) piv[k0 + c] = k0 + p;
-      const T inv = T(1) / pv;
-      __syncthreads();
-      if (p != c && threadIdx.x < kb) {
+      // swap rows c and p inside the panel, one thread per column; the new
+      // pivot row is also kept in prow
+      if (threadIdx.x < kb) {  // the whole panel row, multipliers included
         const int cc = threadIdx.x;
-        T a = Pn[(size_t)cc * m + c], b = Pn[(size_t)cc * m + p];
+        const T a = Pn[(size_t)cc * m + c], b = Pn[(size_t)cc * m + p];
         Pn[(size_t)cc * m + c] = b;
         Pn[(size_t)cc * m + p] = a;
+        prow[cc] = b;
       }
-      __syncthreads();
+      if (threadIdx.x == 0) piv[k0 + c] = k0 + p;
+      __syncthreads();  // S2
+      const T inv = T(1) / pv;
       for (int r = c + 1 + threadIdx.x; r < m; r += kThreads) {
-        T l = Pn[(size_t)c * m + r] * inv;
+        const T l = Pn[(size_t)c * m + r] * inv;
         Pn[(size_t)c * m + r] = l;
-        for (int cc = c + 1; cc < kb; ++cc) Pn[(size_t)cc * m + r] -= l * Pn[(size_t)cc * m + c];
+        for (int cc = c + 1; cc < kb; ++cc) Pn[(size_t)cc * m + r] -= l * prow[cc];
       }
-      __syncthreads();
     }
-    // write the panel back
-    for (int e = threadIdx.x; e < m * kb; e += kThreads) {
-      int r = e % m, c = e / m;
-      W[(size_t)(k0 + c) * ldw + k0 + r] = Pn[(size_t)c * m + r];
-    }
+    __syncthreads();
+    cta_copy_block<T, T>(W + (size_t)k0 * ldw + k0, ldw, Pn, m, m, kb);
     // apply this panel's row swaps to the columns left and right of it
     for (int col = threadIdx.x; col < n; col += kThreads) {
       if (col >= k0 && col < k0 + kb) continue;
       T* cp = W + (size_t)col * ldw;
       for (int c = 0; c < kb; ++c) {
-        int p = piv[k0 + c];
+        const int p = piv[k0 + c];
         if (p != k0 + c) {
-          T a = cp[k0 + c];
+          const T a = cp[k0 + c];
           cp[k0 + c] = cp[p];
           cp[p] = a;
         }
       }
     }
     __syncthreads();
-    const int nr = n - k0 - kb;
-    if (nr > 0) {
-      // U12 = inv(L11) A12: unit lower substitution, one thread per column
-      for (int col = k0 + kb + threadIdx.x; col < n; col += kThreads) {
-        T* cp = W + (size_t)col * ldw + k0;
-        T x[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = (i < kb) ? cp[i] : T(0);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j >= kb) break;
-#pragma unroll
-          for (int i = j + 1; i < 32; ++i)
-            if (i < kb) x[i] -= Pn[(size_t)j * m + i] * x[j];
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (i < kb) cp[i] = x[i];
-      }
-      __syncthreads();
-      // A22 -= L21 U12
-      cta_gemm_sub<T>(W + (size_t)(k0 + kb) * ldw + k0 + kb, ldw, Pn + kb, m,
-                      W + (size_t)(k0 + kb) * ldw + k0, ldw, nr, nr, kb, Bs, 0, false);
-    }
+    if (n - k0 - kb > 0) cta_lu_update<T>(W, ldw, n, k0, kb, Pn, m, Li, Ta, Tu);
   }
   __syncthreads();
   return 0;
@@ -285,20 +363,22 @@ __device__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* smem, int nb, Ct
 
 // --------------------------------------------------------- Cholesky factor
 // Lower Cholesky of W (only the lower triangle is read and written).
-// Returns 0 or k+1 where the pivot is not > 0 (incl. NaN).
+// Returns 0, or k+1 where the pivot is not > 0 (incl. NaN).  One barrier
+// per panel column: the step for column c reads the unscaled column c and
+// forms the multipliers on the fly; each thread scales its own rows of
+// column c during the next step, when nobody reads that column any more.
 template <typename T>
-__device__ int cta_chol_factor(T* W, int ldw, int n, T* smem, int nb, CtaRed& red) {
+__device__ __noinline__ int cta_chol_factor(T* W, int ldw, int n, T* smem, int nb) {
   T* Pn = smem;
+  T* Tu = smem + (size_t)n * nb;
+  Tu = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Tu) + 15) & ~(uintptr_t)15);
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = min(nb, n - k0), m = n - k0;
-    T* Bs = smem + (size_t)m * nb;
     __syncthreads();
-    for (int e = threadIdx.x; e < m * kb; e += kThreads) {
-      int r = e % m, c = e / m;
-      Pn[(size_t)c * m + r] = (r >= c) ? W[(size_t)(k0 + c) * ldw + k0 + r] : T(0);
-    }
-    __syncthreads();
+    cta_copy_block<T, T>(Pn, m, W + (size_t)k0 * ldw + k0, ldw, m, kb);
+    T prev_inv = T(0), prev_ljj = T(0);
     for (int c = 0; c < kb; ++c) {
+      __syncthreads();
       const T d = Pn[(size_t)c * m + c];
       if (!(d > T(0))) {
         __syncthreads();
@@ -306,88 +386,197 @@ __device__ int cta_chol_factor(T* W, int ldw, int n, T* smem, int nb, CtaRed& re
       }
       const T ljj = sqrt(d);
       const T inv = T(1) / ljj;
-      __syncthreads();
-      for (int r = c + threadIdx.x; r < m; r += kThreads)
-        Pn[(size_t)c * m + r] = (r == c) ? ljj : Pn[(size_t)c * m + r] * inv;
-      __syncthreads();
-      for (int r = c + 1 + threadIdx.x; r < m; r += kThreads) {
-        const T l = Pn[(size_t)c * m + r];
-        for (int cc = c + 1; cc < kb && cc <= r; ++cc)
-          Pn[(size_t)cc * m + r] -= l * Pn[(size_t)c * m + cc];
+      for (int r = c + threadIdx.x; r < m; r += kThreads) {
+        if (c > 0) Pn[(size_t)(c - 1) * m + r] *= prev_inv;  // deferred scaling of column c-1
+        if (r == c) continue;
+        const T l = Pn[(size_t)c * m + r] * inv;
+        const int cmax = min(kb - 1, r);
+        for (int cc = c + 1; cc <= cmax; ++cc) Pn[(size_t)cc * m + r] -= l * (Pn[(size_t)c * m + cc] * inv);
       }
-      __syncthreads();
-    }
-    for (int e = threadIdx.x; e < m * kb; e += kThreads) {
-      int r = e % m, c = e / m;
-      if (r >= c) W[(size_t)(k0 + c) * ldw + k0 + r] = Pn[(size_t)c * m + r];
+      // rows < c of column c-1 are above the diagonal (unused); row c-1 of
+      // column c-1 is the diagonal entry, stored below
+      if (threadIdx.x == 0 && c > 0) Pn[(size_t)(c - 1) * m + (c - 1)] = prev_ljj;
+      prev_inv = inv;
+      prev_ljj = ljj;
     }
     __syncthreads();
-    const int nr = n - k0 - kb;
-    if (nr > 0) {
-      // A22 -= L21 L21^T on the lower triangle.  B = L21^T is read from
-      // the panel rows kb..m-1 written back to W: B(k, j) = L21(j, k).
-      // Stage it transposed into a column-major kb x nr view through W's
-      // upper triangle (unused by Cholesky): U(k0+k, k0+kb+j) = L21(j, k).
-      for (int e = threadIdx.x; e < nr * kb; e += kThreads) {
-        int j = e % nr, k = e / nr;
-        W[(size_t)(k0 + kb + j) * ldw + k0 + k] = Pn[(size_t)k * m + kb + j];
-      }
-      __syncthreads();
-      cta_gemm_sub<T>(W + (size_t)(k0 + kb) * ldw + k0 + kb, ldw, Pn + kb, m,
-                      W + (size_t)(k0 + kb) * ldw + k0, ldw, nr, nr, kb, Bs, 0, true);
+    {  // scale the last column and store the diagonal
+      const int c = kb - 1;
+      for (int r = c + threadIdx.x; r < m; r += kThreads)
+        Pn[(size_t)c * m + r] = (r == c) ? prev_ljj : Pn[(size_t)c * m + r] * prev_inv;
     }
+    __syncthreads();
+    for (int c = (threadIdx.x >> 5); c < kb; c += kWarps)
+      for (int r = c + (threadIdx.x & 31); r < m; r += 32)
+        W[(size_t)(k0 + c) * ldw + k0 + r] = Pn[(size_t)c * m + r];
+    __syncthreads();
+    if (n - k0 - kb > 0) cta_chol_update<T>(W, ldw, n, k0, kb, Pn, m, Tu);
   }
   __syncthreads();
   return 0;
 }
 
 // ------------------------------------------------------- triangular solves
-// x (smem, n x nrhs, ld ldx) <- inv(E) x with E = trans ? M^T : M, M lower
-// or upper (ld ldm), unit diagonal if `unit`.  Blocked by 32.
-template <typename T, typename V>
-__device__ void cta_tri_solve(const T* M, int ldm, int n, bool lower, bool trans, bool unit, V* x,
-                              int ldx, int nrhs) {
-  const bool elower = (lower != trans);
+// Inverses of the 32 x 32 diagonal blocks of a triangular M (lower/upper,
+// unit or not), padded with the identity past n.  Block b is stored
+// column-major at Dinv + 1024 b.  One warp per block: lane j forms column
+// j of the inverse by substitution against e_j.
+template <typename T>
+__device__ __noinline__ void cta_block_inverses(const T* __restrict__ M, int ldm, int n, bool lower,
+                                                bool unit, T* Dinv) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nblk = (n + 31) / 32;
-  auto E = [&](int r, int c) -> V { return (V)(trans ? M[(size_t)r * ldm + c] : M[(size_t)c * ldm + r]); };
+  for (int b = w; b < nblk; b += kWarps) {
+    const int b0 = b * 32, bs = min(32, n - b0);
+    T x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? T(1) : T(0);
+    if (lower) {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        if (i < bs) {
+          T s = x[i];
+#pragma unroll
+          for (int k = 0; k < i; ++k) s -= M[(size_t)(b0 + k) * ldm + b0 + i] * x[k];
+          x[i] = unit ? s : s / M[(size_t)(b0 + i) * ldm + b0 + i];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int ii = 0; ii < 32; ++ii) {
+        const int i = 31 - ii;
+        if (i < bs) {
+          T s = x[i];
+#pragma unroll
+          for (int k = i + 1; k < 32; ++k)
+            if (k < bs) s -= M[(size_t)(b0 + k) * ldm + b0 + i] * x[k];
+          x[i] = unit ? s : s / M[(size_t)(b0 + i) * ldm + b0 + i];
+        }
+      }
+    }
+    T* out = Dinv + (size_t)b * 1024 + (size_t)lane * 32;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out[i] = x[i];
+  }
+  __syncthreads();
+}
+
+// x (smem, n x nrhs, ld ldx) <- inv(E) x with E = trans ? M^T : M, M lower
+// or upper (ld ldm), unit diagonal if `unit`.  Blocked by 32 rows.  With
+// Dinv (the diagonal-block inverses of M) the block step is a product with
+// the inverse; without it the block is loaded into registers (lane i holds
+// row i) and solved by substitution, one warp per right-hand side.  The
+// rows after the block are then updated by all threads.
+template <typename T, typename V, bool ELOWER>
+__device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm, int n, bool trans, bool unit,
+                                               V* x, int ldx, int nrhs, const T* __restrict__ Dinv,
+                                               T* stage) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nblk = (n + 31) / 32;
   for (int bi = 0; bi < nblk; ++bi) {
-    const int blk = elower ? bi : nblk - 1 - bi;
+    const int blk = ELOWER ? bi : nblk - 1 - bi;
     const int b0 = blk * 32, bs = min(32, n - b0);
     __syncthreads();
-    if (w == 0) {  // diagonal block
-      const int i = lane;
-      for (int c = 0; c < nrhs; ++c) {
-        V xi = (i < bs) ? x[(size_t)c * ldx + b0 + i] : V(0);
-        for (int jj = 0; jj < bs; ++jj) {
-          const int j = elower ? jj : bs - 1 - jj;
-          if (i == j && !unit) xi = xi / E(b0 + i, b0 + i);
-          V xj = __shfl_sync(0xffffffffu, xi, j);
-          bool after = elower ? (i > j) : (i < j);
-          if (after && i < bs) xi -= E(b0 + i, b0 + j) * xj;
+    if (w < nrhs) {
+      if (Dinv) {
+        const T* D = Dinv + (size_t)blk * 1024;
+        for (int c = w; c < nrhs; c += kWarps) {
+          V xin = (lane < bs) ? x[(size_t)c * ldx + b0 + lane] : V(0);
+          V acc = V(0);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const V xj = __shfl_sync(0xffffffffu, xin, j);
+            // inv(E)(lane, j): E = M^T -> inv(D)(j, lane)
+            const V dij = (V)(trans ? D[(size_t)lane * 32 + j] : D[(size_t)j * 32 + lane]);
+            acc += dij * xj;
+          }
+          if (lane < bs) x[(size_t)c * ldx + b0 + lane] = acc;
         }
-        if (i < bs) x[(size_t)c * ldx + b0 + i] = xi;
+      } else {
+        V e[32];
+        const int r = b0 + lane;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          V v = (lane == j) ? V(1) : V(0);
+          if (lane < bs && j < bs) {
+            const bool inside = ELOWER ? (j <= lane) : (j >= lane);
+            if (inside && !(unit && j == lane))
+              v = (V)(trans ? M[(size_t)r * ldm + b0 + j] : M[(size_t)(b0 + j) * ldm + r]);
+          }
+          e[j] = v;
+        }
+        V dinv = V(1);
+        if (!unit) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j == lane) dinv = V(1) / e[j];
+        }
+        for (int c = w; c < nrhs; c += kWarps) {
+          V xi = (lane < bs) ? x[(size_t)c * ldx + b0 + lane] : V(0);
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) {
+            const int j = ELOWER ? jj : 31 - jj;
+            if (lane == j) xi = unit ? xi : xi * dinv;
+            const V xj = __shfl_sync(0xffffffffu, xi, j);
+            if (ELOWER ? (lane > j) : (lane < j)) xi -= e[j] * xj;
+          }
+          if (lane < bs) x[(size_t)c * ldx + b0 + lane] = xi;
+        }
       }
     }
     __syncthreads();
-    // rows not yet solved: x_r -= sum_{j in block} E(r, j) x_j
-    const int r_lo = elower ? b0 + bs : 0, r_hi = elower ? n : b0;
-    if (r_hi > r_lo) {
-      if (!trans) {  // E(r, j) = M(r, j): coalesced over r
-        for (int r = r_lo + threadIdx.x; r < r_hi; r += kThreads) {
-          for (int c = 0; c < nrhs; ++c) {
-            V s = V(0);
-            for (int j = 0; j < bs; ++j) s += (V)M[(size_t)(b0 + j) * ldm + r] * x[(size_t)c * ldx + b0 + j];
-            x[(size_t)c * ldx + r] -= s;
-          }
+    const int r_lo = ELOWER ? b0 + bs : 0, r_hi = ELOWER ? n : b0;
+    if (!trans) {
+      // E(r, j) = M(r, j): thread per row, coalesced over r
+      for (int r = r_lo + threadIdx.x; r < r_hi; r += kThreads) {
+        V acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = V(0);
+        for (int j = 0; j < bs; ++j) {
+          const V m = (V)M[(size_t)(b0 + j) * ldm + r];
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < nrhs) acc[c] += m * x[(size_t)c * ldx + b0 + j];
         }
-      } else {  // E(r, j) = M(j, r): warp per row, lanes over j
-        for (int r = r_lo + w; r < r_hi; r += kWarps) {
-          V m = (lane < bs) ? (V)M[(size_t)r * ldm + b0 + lane] : V(0);
-          for (int c = 0; c < nrhs; ++c) {
-            V s = warp_sum(m * ((lane < bs) ? x[(size_t)c * ldx + b0 + lane] : V(0)));
-            if (lane == 0) x[(size_t)c * ldx + r] -= s;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c < nrhs) x[(size_t)c * ldx + r] -= acc[c];
+      }
+    } else if (stage) {
+      // E(r, j) = M(j, r): each warp stages the 32 x 32 tile M(b0.., r0..)
+      // with coalesced column loads, then lane i finishes row r0 + i
+      T* tile = stage + (size_t)w * 32 * 33;
+      for (int r0 = r_lo + 32 * w; r0 < r_hi; r0 += 32 * kWarps) {
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          const int r = r0 + i;
+          tile[i * 33 + lane] = (r < r_hi && lane < bs) ? M[(size_t)r * ldm + b0 + lane] : T(0);
+        }
+        __syncwarp();
+        const int r = r0 + lane;
+        if (r < r_hi) {
+          V acc[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) acc[c] = V(0);
+          for (int j = 0; j < bs; ++j) {
+            const V m = (V)tile[lane * 33 + j];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              if (c < nrhs) acc[c] += m * x[(size_t)c * ldx + b0 + j];
           }
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            if (c < nrhs) x[(size_t)c * ldx + r] -= acc[c];
+        }
+        __syncwarp();
+      }
+    } else {
+      // E(r, j) = M(j, r): warp per row, lanes over j (coalesced), shuffle sums
+      for (int r = r_lo + w; r < r_hi; r += kWarps) {
+        const V m = (lane < bs) ? (V)M[(size_t)r * ldm + b0 + lane] : V(0);
+        for (int c = 0; c < nrhs; ++c) {
+          const V sum = warp_sum(m * ((lane < bs) ? x[(size_t)c * ldx + b0 + lane] : V(0)));
+          if (lane == 0) x[(size_t)c * ldx + r] -= sum;
         }
       }
     }
@@ -395,42 +584,78 @@ __device__ void cta_tri_solve(const T* M, int ldm, int n, bool lower, bool trans
   __syncthreads();
 }
 
-// LU application: x <- inv(A) x (trans: inv(A)^T x) with A = P L U.
+// stage: optional shared-memory scratch of 8 x 32 x 33 elements of T for
+// the transposed update (without it, warp-per-row shuffle sums are used).
 template <typename T, typename V>
-__device__ void cta_lu_apply(const T* W, int ldw, int n, const int* piv, V* x, int ldx, int nrhs,
-                             bool trans) {
+__device__ void cta_tri_solve(const T* M, int ldm, int n, bool lower, bool trans, bool unit, V* x, int ldx,
+                              int nrhs, const T* Dinv = nullptr, T* stage = nullptr) {
+  if (lower != trans) cta_tri_solve_dir<T, V, true>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage);
+  else cta_tri_solve_dir<T, V, false>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage);
+}
+
+// Row permutation of LU with partial pivoting as one gather: after the
+// swaps k <-> piv[k] (k = 0..n-1), position k holds original row perm[k].
+__device__ void cta_build_perm(const int* piv, int n, int* perm) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < n; ++k) perm[k] = k;
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      const int t = perm[k];
+      perm[k] = perm[p];
+      perm[p] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// x <- P x (forward) or x <- P^T x (inverse), x in smem, n x nrhs, through
+// the scratch buffer tmp (n x nrhs).
+template <typename V>
+__device__ __noinline__ void cta_permute(V* x, int ldx, int n, int nrhs, const int* perm, bool inverse,
+                                         V* tmp) {
+  __syncthreads();  // x may have just been written by other threads
+  for (int c = 0; c < nrhs; ++c)
+    for (int k = threadIdx.x; k < n; k += kThreads) {
+      const int src = inverse ? k : perm[k];
+      const int dst = inverse ? perm[k] : k;
+      tmp[(size_t)c * n + dst] = x[(size_t)c * ldx + src];
+    }
+  __syncthreads();
+  for (int c = 0; c < nrhs; ++c)
+    for (int k = threadIdx.x; k < n; k += kThreads) x[(size_t)c * ldx + k] = tmp[(size_t)c * n + k];
+  __syncthreads();
+}
+
+// LU application: x <- inv(A) x (trans: inv(A)^T x) with A = P L U, where
+// perm is the gather form of the pivots (cta_build_perm).  Linv/Uinv: the
+// diagonal-block inverses of L and U, or null for substitution.
+template <typename T, typename V>
+__device__ void cta_lu_apply(const T* W, int ldw, int n, const int* perm, V* x, int ldx, int nrhs,
+                             bool trans, V* tmp, const T* Linv = nullptr, const T* Uinv = nullptr,
+                             T* stage = nullptr) {
   if (!trans) {
-    __syncthreads();
-    for (int c = threadIdx.x; c < nrhs; c += kThreads)
-      for (int k = 0; k < n; ++k) {
-        int p = piv[k];
-        if (p != k) { V t = x[(size_t)c * ldx + k]; x[(size_t)c * ldx + k] = x[(size_t)c * ldx + p]; x[(size_t)c * ldx + p] = t; }
-      }
-    cta_tri_solve<T, V>(W, ldw, n, true, false, true, x, ldx, nrhs);
-    cta_tri_solve<T, V>(W, ldw, n, false, false, false, x, ldx, nrhs);
+    cta_permute<V>(x, ldx, n, nrhs, perm, false, tmp);
+    cta_tri_solve<T, V>(W, ldw, n, true, false, true, x, ldx, nrhs, Linv, stage);
+    cta_tri_solve<T, V>(W, ldw, n, false, false, false, x, ldx, nrhs, Uinv, stage);
   } else {
-    cta_tri_solve<T, V>(W, ldw, n, false, true, false, x, ldx, nrhs);
-    cta_tri_solve<T, V>(W, ldw, n, true, true, true, x, ldx, nrhs);
-    __syncthreads();
-    for (int c = threadIdx.x; c < nrhs; c += kThreads)
-      for (int k = n - 1; k >= 0; --k) {
-        int p = piv[k];
-        if (p != k) { V t = x[(size_t)c * ldx + k]; x[(size_t)c * ldx + k] = x[(size_t)c * ldx + p]; x[(size_t)c * ldx + p] = t; }
-      }
-    __syncthreads();
+    cta_tri_solve<T, V>(W, ldw, n, false, true, false, x, ldx, nrhs, Uinv, stage);
+    cta_tri_solve<T, V>(W, ldw, n, true, true, true, x, ldx, nrhs, Linv, stage);
+    cta_permute<V>(x, ldx, n, nrhs, perm, true, tmp);
   }
 }
 
 template <typename T, typename V>
-__device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nrhs) {
-  cta_tri_solve<T, V>(W, ldw, n, true, false, false, x, ldx, nrhs);
-  cta_tri_solve<T, V>(W, ldw, n, true, true, false, x, ldx, nrhs);
+__device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nrhs,
+                               const T* Linv = nullptr, T* stage = nullptr) {
+  cta_tri_solve<T, V>(W, ldw, n, true, false, false, x, ldx, nrhs, Linv, stage);
+  cta_tri_solve<T, V>(W, ldw, n, true, true, false, x, ldx, nrhs, Linv, stage);
 }
 
 // -------------------------------------------------------------- residual
 // R = B - A X in FP64 (A: n x n ld lda, Xs: smem n x nrhs ld n), writes R to
 // global (ld n) and returns per-column max |r| in rmax[c].
-__device__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
+__device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
                              const double* Xs, int nrhs, double* R, double* rmax_s, CtaRed& red) {
   constexpr int kRows = 4;
   double acc[kRows][8];
@@ -514,6 +739,10 @@ __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red
     }
     const int j = cta_argmax_first<double>(best, bi, red);
     __syncthreads();
+    if (j < 0 || j >= n) {  // only NaN entries: no estimate
+      est = __longlong_as_double(0x7ff8000000000000ll);
+      break;
+    }
     for (int i = threadIdx.x; i < n; i += kThreads) v[i] = (i == j) ? V(1) : V(0);
     apply(v, false);
     const double estold = est;
@@ -539,6 +768,10 @@ __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red
     }
     const int jn = cta_argmax_first<double>(best2, bi2, red);
     ++k;
+    if (jn < 0 || jn >= n) {
+      est = __longlong_as_double(0x7ff8000000000000ll);
+      break;
+    }
     const double vj = (double)v[j], vjn = fabs((double)v[jn]);
     __syncthreads();
     if (vj == vjn || k > 5) break;

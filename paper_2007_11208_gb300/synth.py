@@ -112,7 +112,8 @@ def banded_dd(n, kl, ku, g, device="cpu"):
 def haar(n, g, device="cpu"):
     """Haar-distributed orthogonal matrix (QR of a Gaussian, R signs fixed)."""
     Z = _randn((n, n), g, device)
-    Q, R = torch.linalg.qr(Z)
+    Q, R = torch.linalg.qr(Z.cpu())  # host LAPACK: no device linear-algebra library needed
+    Q, R = Q.to(device), R.to(device)
     s = torch.sign(torch.diagonal(R))
     s[s == 0] = 1.0
     return Q * s[None, :]
