@@ -182,6 +182,24 @@ int asolve_solve_batched(asolve_ctx* ctx, int64_t count, const int64_t* n,
                          const int64_t* b_off, const double* A, const double* B,
                          double* X, uint32_t flags, asolve_info* infos);
 
+/* Property scan that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory --
+ * code that must not enter the allocator, hosts that own every device byte
+ * through their own pool, or callers without an asolve context).
+ *   A:      device pointer, n x n column-major, n <= 2048.
+ *   out:    DEVICE pointer to one asolve_scan_result, written on `stream`
+ *           (read it after synchronising that stream).
+ *   stream: cudaStream_t to run on; NULL is the legacy default stream.
+ * Uses the paper's default band fraction (0.25) and symmetry tolerance
+ * (100 eps).  The workspace is a fixed 1.125 MiB device array inside the
+ * library, held by every GPU that loads it until the process exits and
+ * shared by all calls: calls that overlap on the GPU race and must be
+ * ordered by the caller.  The first call on each device looks up that
+ * array's device address (make it before any stream capture).
+ * Returns E_UNSUPPORTED for n > 2048, E_INVALID for bad arguments,
+ * E_CUDA if a launch fails; never allocates. */
+int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, void* stream);
+
 /* Per-kernel timing with CUDA events on the context stream (off by default). */
 int asolve_set_profiling(asolve_ctx* ctx, int on);
 int asolve_get_profile(asolve_ctx* ctx, asolve_profile* out);
