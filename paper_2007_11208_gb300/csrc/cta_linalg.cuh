@@ -98,11 +98,17 @@ __device__ __noinline__ void tile_gemm_sub<float>(float* C, int ldc, const float
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int istart = lower_only ? (col_off / 128) * 128 : 0;
   for (int i0 = istart; i0 < m; i0 += 128) {
+    // C tile loaded first, so its latency overlaps the k loop
     float acc[4][8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) {
+      const int c = w * 8 + j;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+      for (int i = 0; i < 4; ++i) {
+        const int r = i0 + lane + 32 * i;
+        acc[i][j] = (c < nc && r < m) ? C[(size_t)c * ldc + r] : 0.f;
+      }
+    }
 #pragma unroll 2
     for (int k = 0; k < kb; ++k) {
       float a[4];
@@ -117,7 +123,7 @@ __device__ __noinline__ void tile_gemm_sub<float>(float* C, int ldc, const float
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
     }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -127,7 +133,7 @@ __device__ __noinline__ void tile_gemm_sub<float>(float* C, int ldc, const float
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int r = i0 + lane + 32 * i;
-        if (r < m) col[r] -= acc[i][j];
+        if (r < m) col[r] = acc[i][j];
       }
     }
   }
@@ -653,46 +659,75 @@ __device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nr
 }
 
 // -------------------------------------------------------------- residual
-// R = B - A X in FP64 (A: n x n ld lda, Xs: smem n x nrhs ld n), writes R to
-// global (ld n) and returns per-column max |r| in rmax[c].
+// R = B - A X in FP64 (A: n x n ld lda; X: n x nrhs ld n), writes R (ld n)
+// and the per-column max |r| to rmax_s[c].  For nrhs >= 3 the products run
+// on the FP64 tensor instruction (8 rows x 8 right-hand sides x 4 columns
+// per mma.sync, one warp per 8-row group); otherwise on DFMA, one thread
+// per row.
 __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
-                             const double* Xs, int nrhs, double* R, double* rmax_s, CtaRed& red) {
-  constexpr int kRows = 4;
-  double acc[kRows][8];
-  const int t = threadIdx.x;
-#pragma unroll
-  for (int q = 0; q < kRows; ++q)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[q][c] = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double xv[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) xv[c] = (c < nrhs) ? Xs[(size_t)c * n + j] : 0.0;
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-      const int i = t + q * kThreads;
-      if (i < n) {
-        const double a = __ldg(A + (size_t)j * lda + i);
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < nrhs) acc[q][c] = fma(a, xv[c], acc[q][c]);
-      }
-    }
-  }
+                                          const double* Xs, int nrhs, double* R, double* rmax_s, CtaRed& red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double mx[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) mx[c] = 0.0;
+  if (nrhs >= 3) {
+    const int g = lane >> 2, t = lane & 3;
+    for (int r0 = 8 * w; r0 < n; r0 += 8 * kWarps) {
+      double c0 = 0.0, c1 = 0.0;
+      const int ra = r0 + g;  // A fragment row
+      const bool xok = g < nrhs;
+#pragma unroll 4
+      for (int k = 0; k < n; k += 4) {
+        const int ka = k + t;
+        const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * lda + ra) : 0.0;
+        const double b = (xok && ka < n) ? Xs[(size_t)g * n + ka] : 0.0;
+        dmma_8x8x4(c0, c1, a, b);
+      }
+      // c0, c1 = (A X)(r0 + g, 2t), (A X)(r0 + g, 2t + 1)
+      const int r = r0 + g;
 #pragma unroll
-  for (int q = 0; q < kRows; ++q) {
-    const int i = t + q * kThreads;
-    if (i < n) {
+      for (int q = 0; q < 2; ++q) {
+        const int c = 2 * t + q;
+        double v = 0.0;
+        if (r < n && c < nrhs) {
+          v = B[(size_t)c * n + r] - (q ? c1 : c0);
+          R[(size_t)c * n + r] = v;
+        }
+        // lane holds column c = 2t + q: fold into mx via a per-lane max
+        const double av = fabs(v);
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c < nrhs) {
-          double r = B[(size_t)c * n + i] - acc[q][c];
+        for (int cc = 0; cc < 8; ++cc)
+          if (cc == c) mx[cc] = fmax(mx[cc], av);
+      }
+    }
+  } else {
+    constexpr int kRows = 4;
+    double acc[kRows][2];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) acc[q][0] = acc[q][1] = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double x0 = Xs[j], x1 = (nrhs > 1) ? Xs[(size_t)n + j] : 0.0;
+#pragma unroll
+      for (int q = 0; q < kRows; ++q) {
+        const int i = tid + q * kThreads;
+        if (i < n) {
+          const double a = __ldg(A + (size_t)j * lda + i);
+          acc[q][0] = fma(a, x0, acc[q][0]);
+          if (nrhs > 1) acc[q][1] = fma(a, x1, acc[q][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      const int i = tid + q * kThreads;
+      if (i < n) {
+        for (int c = 0; c < nrhs; ++c) {
+          const double r = B[(size_t)c * n + i] - acc[q][c];
           R[(size_t)c * n + i] = r;
           mx[c] = fmax(mx[c], fabs(r));
         }
+      }
     }
   }
   for (int c = 0; c < nrhs; ++c) {
