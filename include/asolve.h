@@ -200,6 +200,16 @@ int asolve_solve_batched(asolve_ctx* ctx, int64_t count, const int64_t* n,
  * E_CUDA if a launch fails; never allocates. */
 int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, void* stream);
 
+/* The trailing-update GEMM of the large dense factorisations (Sec. 2.3/2.4
+ * blocked Cholesky/LU updates), exposed so it can be verified on its own:
+ *   C (M x N) -= A (M x K) * B (K x N), FP32, column-major, device pointers,
+ * computed with tcgen05 kind::tf32 MMAs and FP32 accumulation; passes = 3
+ * splits every operand into a TF32 head and remainder (three products,
+ * FP32-level accuracy), passes = 1 is plain TF32.  err: optional device int
+ * set to 1 if a device-side wait gave up.  Asynchronous on `stream`. */
+int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
+                    int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream);
+
 /* Per-kernel timing with CUDA events on the context stream (off by default). */
 int asolve_set_profiling(asolve_ctx* ctx, int on);
 int asolve_get_profile(asolve_ctx* ctx, asolve_profile* out);

@@ -67,7 +67,8 @@ _lib = None
 EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve_create",
            "asolve_destroy", "asolve_stream", "asolve_scan", "asolve_solve",
            "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
-           "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc")
+           "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc",
+           "asolve_gemm_sub")
 
 
 def lib():
@@ -96,6 +97,7 @@ def lib():
     L.asolve_get_profile.argtypes = [vp, P(Profile)]
     L.asolve_reset_profile.argtypes = [vp]
     L.asolve_scan_noalloc.argtypes = [vp, i64, vp, vp]
+    L.asolve_gemm_sub.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, vp, vp]
     for f in EXPORTS:
         if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
             getattr(L, f).restype = i32

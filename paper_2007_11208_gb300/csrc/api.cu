@@ -9,6 +9,7 @@
 
 #include <map>
 #include <mutex>
+#include <stdint.h>
 
 #include "asolve_internal.cuh"
 
@@ -26,6 +27,8 @@ size_t scan_slot_bytes(int nmax);
 size_t scan_large_workspace(int64_t n);
 cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64_t nb, double band_frac,
                               double tol, void* ws, ScanRes* out, int num_sms, cudaStream_t st);
+cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
+                           int K, int passes, int* err, cudaStream_t st);
 }  // namespace asv
 
 using namespace asv;
@@ -477,6 +480,18 @@ extern "C" int asolve_solve_band(asolve_ctx* c, const double* AB, int64_t ldab, 
   (void)AB; (void)ldab; (void)kl; (void)ku; (void)B; (void)n; (void)nrhs; (void)flags; (void)X; (void)info;
   if (!c) return ASOLVE_E_INVALID;
   return ASOLVE_E_UNSUPPORTED;
+}
+
+extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
+                               int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream) {
+  if (!C || !A || !B || M < 0 || N < 0 || K < 0 || (passes != 1 && passes != 3)) return ASOLVE_E_INVALID;
+  if (ldc < (M > 0 ? M : 1) || lda < (M > 0 ? M : 1) || ldb < (K > 0 ? K : 1)) return ASOLVE_E_INVALID;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || ldc > INT32_MAX || lda > INT32_MAX || ldb > INT32_MAX)
+    return ASOLVE_E_UNSUPPORTED;
+  if (M == 0 || N == 0 || K == 0) return ASOLVE_OK;
+  cudaError_t e = launch_gemm_tc(C, (int)ldc, A, (int)lda, B, (int)ldb, (int)M, (int)N, (int)K, passes, err,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
 }
 
 extern "C" int asolve_set_profiling(asolve_ctx* c, int on) {
