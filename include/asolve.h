@@ -90,7 +90,7 @@ typedef struct {
   int32_t precision;       /* ASOLVE_PREC_*; default ASOLVE_PREC_MIXED */
   int32_t ir_max_iter;     /* refinement steps before falling back to FP64; default 10 */
   double  ir_target_berr;  /* stop refining when berr <= this; default 1e-13 */
-  double  ir_kappa_limit;  /* mixed: rcond < 1/limit from the FP32 factors -> FP64; default 1e6 */
+  double  ir_kappa_limit;  /* mixed: rcond < 1/limit from the FP32 factors -> FP64; default 1e9 */
   size_t  hbm_budget;      /* serving admission budget in bytes; default 120 GB */
   void*   stream;          /* cudaStream_t to run on; NULL: the context creates one */
   int32_t device;          /* CUDA device ordinal; < 0: the current device */

@@ -28,7 +28,21 @@ size_t scan_large_workspace(int64_t n);
 cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64_t nb, double band_frac,
                               double tol, void* ws, ScanRes* out, int num_sms, cudaStream_t st);
 cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
-                           int K, int passes, int* err, cudaStream_t st);
+                           int K, int passes, int* err, cudaStream_t st, bool trans_b, bool lower);
+struct LargeArgs {
+  const double* A;
+  const double* B;
+  double* X;
+  int64_t n, nrhs;
+  uint32_t flags;
+  int precision;
+  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
+  int ir_max_iter;
+  int num_sms;
+  cudaStream_t st;
+};
+size_t large_ws_bytes(int64_t n, int64_t nrhs);
+int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
 }  // namespace asv
 
 using namespace asv;
@@ -133,7 +147,7 @@ extern "C" int asolve_default_config(asolve_config* c) {
   c->precision = ASOLVE_PREC_MIXED;
   c->ir_max_iter = 10;
   c->ir_target_berr = 1e-13;
-  c->ir_kappa_limit = 1e6;
+  c->ir_kappa_limit = 1e9;
   c->hbm_budget = (size_t)120 << 30;
   c->stream = nullptr;
   c->device = -1;
@@ -410,8 +424,42 @@ extern "C" int asolve_solve(asolve_ctx* c, const double* A, const double* B, int
     return ASOLVE_OK;
   }
   if (!A || !B || !X) return ASOLVE_E_INVALID;
-  if (n > kBatchNMax || nrhs > kBatchRhsMax) return ASOLVE_E_UNSUPPORTED;
   CK(cudaSetDevice(c->device));
+  if (n > kBatchNMax || nrhs > kBatchRhsMax) {
+    // one large system: blocked factorisations over the whole GPU
+    if (n > 32768 || nrhs > 256) return ASOLVE_E_UNSUPPORTED;
+    cudaStream_t st = c->stream;
+    const double *dA = A, *dB = B;
+    double* dX = X;
+    if (flags & ASOLVE_HOST_BUFFERS) {
+      CK(c->hostA.ensure(sizeof(double) * (size_t)(n * n)));
+      CK(c->hostB.ensure(sizeof(double) * (size_t)(n * nrhs)));
+      CK(c->hostX.ensure(sizeof(double) * (size_t)(n * nrhs)));
+      CK(cudaMemcpyAsync(c->hostA.p, A, sizeof(double) * (size_t)(n * n), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(c->hostB.p, B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyHostToDevice, st));
+      dA = (const double*)c->hostA.p;
+      dB = (const double*)c->hostB.p;
+      dX = (double*)c->hostX.p;
+    }
+    const size_t wsb = large_ws_bytes(n, nrhs);
+    CK(c->large.ensure(wsb));
+    LargeArgs la{dA, dB, dX, n, nrhs, flags, c->cfg.precision, c->cfg.rcond_threshold, c->cfg.sympd_tol,
+                 c->cfg.band_frac, c->cfg.ir_target_berr, c->cfg.ir_kappa_limit, c->cfg.ir_max_iter,
+                 c->num_sms, st};
+    asolve_info li;
+    const int rc = large_solve(la, c->large.p, c->large.bytes, &li);
+    if (rc < 0 && rc != li.status) {  // an error before the solve produced a status
+      li.status = rc;
+      if (info) *info = li;
+      return rc;
+    }
+    if (flags & ASOLVE_HOST_BUFFERS) {
+      CK(cudaMemcpyAsync(X, dX, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    if (info) *info = li;
+    return li.status;
+  }
   int rc = ensure_pipeline(c, 1);
   if (rc) return rc;
   CK(c->single.ensure(4 * sizeof(int64_t) + sizeof(asolve_info)));
@@ -490,7 +538,7 @@ extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t ld
     return ASOLVE_E_UNSUPPORTED;
   if (M == 0 || N == 0 || K == 0) return ASOLVE_OK;
   cudaError_t e = launch_gemm_tc(C, (int)ldc, A, (int)lda, B, (int)ldb, (int)M, (int)N, (int)K, passes, err,
-                                 (cudaStream_t)stream);
+                                 (cudaStream_t)stream, false, false);
   return e == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
 }
 

@@ -16,6 +16,9 @@
 #include "asolve_internal.cuh"
 
 namespace asv {
+// internal linkage: every translation unit that includes this header gets
+// its own copy of these device functions
+namespace {
 
 constexpr int kThreads = kCtaThreads;
 constexpr int kWarps = kThreads / kWarp;
@@ -828,4 +831,5 @@ __device__ __forceinline__ double rcond_from(double anorm, double ainvnm) {
   return (1.0 / ainvnm) / anorm;
 }
 
+}  // namespace
 }  // namespace asv

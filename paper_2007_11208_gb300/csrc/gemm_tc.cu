@@ -81,9 +81,14 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
   lo = x - hi;
 }
 
+// TRANS_B: B is given transposed, element (k, n) at B[k * ldb + n].
+// LOWER: C is square and only its lower triangle is needed; tiles strictly
+// above the diagonal are skipped.
+template <bool TRANS_B, bool LOWER>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc(float* __restrict__ C, int ldc, const float* __restrict__ A, int lda, const float* __restrict__ B,
               int ldb, int M, int N, int K, int passes, int* err) {
+  if (LOWER && blockIdx.y > blockIdx.x) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -122,10 +127,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       *reinterpret_cast<float*>(sAh + tc_off(r, k)) = (passes == 3) ? hi : v;
       if (passes == 3) *reinterpret_cast<float*>(sAl + tc_off(r, k)) = lo;
     }
-    // stage B: element (n, k) = B[(n0 + n) * ldb + k0 + k]; lanes over k
+    // stage B: element (n, k) = B[(n0 + n) * ldb + k0 + k] (lanes over k),
+    // or B[(k0 + k) * ldb + n0 + n] when transposed (lanes over n)
     for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
-      const int k = e & (kTcK - 1), n = e >> 5;
-      const float v = (n0 + n < N && k0 + k < K) ? __ldg(B + (size_t)(n0 + n) * ldb + k0 + k) : 0.f;
+      const int k = TRANS_B ? (e >> 7) : (e & (kTcK - 1)), n = TRANS_B ? (e & (kTcN - 1)) : (e >> 5);
+      float v = 0.f;
+      if (n0 + n < N && k0 + k < K)
+        v = TRANS_B ? __ldg(B + (size_t)(k0 + k) * ldb + n0 + n) : __ldg(B + (size_t)(n0 + n) * ldb + k0 + k);
       float hi, lo;
       tf32_split(v, hi, lo);
       *reinterpret_cast<float*>(sBh + tc_off(n, k)) = (passes == 3) ? hi : v;
@@ -198,21 +206,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
-                           int K, int passes, int* err, cudaStream_t st) {
-  if (M <= 0 || N <= 0) return cudaSuccess;
+template <bool TB, bool LO>
+static cudaError_t launch_gemm_tc_t(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M,
+                                    int N, int K, int passes, int* err, cudaStream_t st) {
   // always 64 KB: at most 3 CTAs per SM, i.e. at most 384 of the 512
   // tensor-memory columns, so an allocation never waits on another CTA
   const int smem = 4 * kTileBytes;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kTileBytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_gemm_tc<TB, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kTileBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN);
-  k_gemm_tc<<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, passes, err);
+  k_gemm_tc<TB, LO><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, passes, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
+                           int K, int passes, int* err, cudaStream_t st, bool trans_b, bool lower) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (trans_b && lower) return launch_gemm_tc_t<true, true>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
+  if (trans_b) return launch_gemm_tc_t<true, false>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
+  if (lower) return launch_gemm_tc_t<false, true>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
+  return launch_gemm_tc_t<false, false>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
 }
 
 }  // namespace asv

@@ -1,0 +1,1136 @@
+// large.cu -- one large dense system (n > 1024), spread over the whole GPU.
+//
+// Routes (paper Sec. 2.2-2.4) for a single large system, orchestrated by the
+// host with one launch (or a few) per block step:
+//   Cholesky (Sec. 2.3)  blocked right-looking, 128-wide panels: diagonal
+//                        block by one CTA, L21 = A21 inv(L11)^T, trailing
+//                        SYRK on the lower triangle;
+//   LU (Sec. 2.4)        blocked right-looking with partial pivoting: the
+//                        128-wide panel is factored by a cooperative kernel
+//                        (one grid barrier per column), its row swaps are
+//                        applied to the other columns, U12 = inv(L11) A12,
+//                        and the trailing update A22 -= L21 U12;
+//   triangular (Sec. 2.2, Eq. 3) blocked forward/back substitution.
+// The working matrix is FP32 in the mixed-precision mode (trailing updates
+// on the tcgen05 tensor cores, 3xTF32 split) and FP64 in the plain mode
+// (trailing updates on the FP64 mma.sync instruction).  Refinement (FP64
+// residual on mma.sync f64), the 1-norm condition estimate and the
+// per-column backward error are driven from the host.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cta_linalg.cuh"
+
+namespace asv {
+
+cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
+                           int K, int passes, int* err, cudaStream_t st, bool trans_b, bool lower);
+
+constexpr int kLB = 128;  // panel / block width of the large path
+
+// ------------------------------------------------------------ utilities
+// Bounded grid-wide barrier for cooperatively launched kernels (all CTAs
+// co-resident).  bar[0] counts arrivals, bar[1] is the generation.
+__device__ bool grid_barrier(unsigned* bar, unsigned G, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned my = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == G) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == my) {
+        if (++it > 200000000ll) {
+          s_ok = 0;
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__global__ void k_to_work(const double* __restrict__ A, int n, T* __restrict__ W, int ldw) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = blockIdx.x * 8 + w; c < n; c += gridDim.x * 8)
+    for (int r = lane; r < n; r += 32) W[(size_t)c * ldw + r] = (T)A[(size_t)c * n + r];
+}
+
+// ------------------------------------------------- diagonal-block Cholesky
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_chol_diag(T* W, int ldw, int k0, int kb, int nb, int* fail) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int f = cta_chol_factor<T>(W + (size_t)k0 * ldw + k0, ldw, kb, reinterpret_cast<T*>(smem), nb);
+  if (f && threadIdx.x == 0) *fail = k0 + f;
+}
+
+// --------------------------------------- inverse of a triangular block
+// Dinv (kLB x kLB, column-major) = inverse of the kb x kb diagonal block at
+// (k0, k0) of W (lower or upper, unit or not), identity past kb.  Thread j
+// forms column j by substitution; the block is staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kLB) k_tri_block_inv(const T* __restrict__ W, int ldw, int k0, int kb, int lower,
+                                                       int unit, T* __restrict__ Dinv) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* S = reinterpret_cast<T*>(smem);  // kLB x (kLB + 1), row-major: S[i * (kLB+1) + k] = D(i, k)
+  const int j = threadIdx.x;
+  for (int k = 0; k < kb; ++k)
+    if (j < kb) S[j * (kLB + 1) + k] = W[(size_t)(k0 + k) * ldw + k0 + j];
+  __syncthreads();
+  T* x = Dinv + (size_t)j * kLB;
+  if (lower) {
+    for (int i = 0; i < kLB; ++i) {
+      T s = (i == j) ? T(1) : T(0);
+      if (i < kb) {
+        for (int k = j; k < i; ++k) s -= S[i * (kLB + 1) + k] * x[k];
+        if (!unit) s /= S[i * (kLB + 1) + i];
+      }
+      x[i] = s;
+    }
+  } else {
+    for (int i = kLB - 1; i >= 0; --i) {
+      T s = (i == j) ? T(1) : T(0);
+      if (i < kb) {
+        for (int k = i + 1; k <= min(j, kb - 1); ++k) s -= S[i * (kLB + 1) + k] * x[k];
+        if (!unit) s /= S[i * (kLB + 1) + i];
+      }
+      x[i] = s;
+    }
+  }
+}
+
+// ------------------------------------------------- TRSM with an inverse
+// side 0 (left):   W[k0:k0+kb, c] = Dinv * W[k0:k0+kb, c]      for c in [lo, hi)
+// side 1 (right):  W[r, k0:k0+kb] = W[r, k0:k0+kb] * Dinv^T    for r in [lo, hi)
+// One CTA per 64 columns (left) or 64 rows (right).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_trsm_inv(T* __restrict__ W, int ldw, int k0, int kb, int lo, int hi,
+                                                      const T* __restrict__ Dinv, int side) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* D = reinterpret_cast<T*>(smem);  // kLB x kLB, column-major, ld kLB + 1
+  T* Tl = D + kLB * (kLB + 1);         // 128 x 64 tile, ld 129 (left: [k][c]; right: [k][r])
+  const int base = lo + blockIdx.x * 64;
+  if (base >= hi) return;
+  const int cnt = min(64, hi - base);
+  for (int e = threadIdx.x; e < kLB * kLB; e += kThreads) D[(e / kLB) * (kLB + 1) + (e % kLB)] = Dinv[e];
+  if (side == 0) {
+    for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
+      const int k = e & (kLB - 1), c = e >> 7;
+      Tl[c * (kLB + 1) + k] = (k < kb && c < cnt) ? W[(size_t)(base + c) * ldw + k0 + k] : T(0);
+    }
+  } else {
+    for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
+      const int r = e & 63, k = e >> 6;
+      Tl[r * (kLB + 1) + k] = (k < kb && r < cnt) ? W[(size_t)(k0 + k) * ldw + base + r] : T(0);
+    }
+  }
+  __syncthreads();
+  // output (i, c): left = sum_k D(i,k) T(k,c); right (r, j) = sum_k T(r,k) D(j,k)
+  for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
+    const int i = e & (kLB - 1), c = e >> 7;
+    if (i >= kb || c >= cnt) continue;
+    T acc = T(0);
+    const T* trow = Tl + c * (kLB + 1);
+#pragma unroll 8
+    for (int k = 0; k < kLB; ++k) acc += D[k * (kLB + 1) + i] * trow[k];
+    if (side == 0) W[(size_t)(base + c) * ldw + k0 + i] = acc;
+    else W[(size_t)(k0 + i) * ldw + base + c] = acc;
+  }
+}
+
+// ------------------------------------------------- LU panel (cooperative)
+// Panel columns k0..k0+kb-1, rows k0..n-1.  CTA b keeps rows
+// [b*R, (b+1)*R) of the panel (relative to k0) in shared memory for the
+// whole panel.  Per column: every CTA publishes its best candidate (value,
+// row, and the whole panel row) and the owner of the diagonal row publishes
+// that row; after one grid barrier every CTA picks the same pivot (largest
+// |value|, first row on ties), swaps locally and updates its own rows.
+// Buffers are double-buffered by column parity.
+struct PanelBuf {
+  void* cand;      // [2][G][4] of T: |v|, row, v, valid
+  void* rows;      // [2][G][kLB] of T
+  void* diag;      // [2][kLB] of T
+  unsigned* bar;   // grid barrier (zeroed before the launch)
+  int* err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ldw, int n, int k0, int kb, int R,
+                                                      int* __restrict__ piv, PanelBuf pb, int* fail) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* S = reinterpret_cast<T*>(smem);  // R x (kLB + 1)
+  T* prow = S + (size_t)R * (kLB + 1);  // kLB
+  __shared__ T s_best[kWarps];
+  __shared__ int s_idx[kWarps];
+  __shared__ T s_val[kWarps];
+  __shared__ int s_idxw[kWarps];
+  __shared__ int s_p, s_wb, s_stop;
+  __shared__ T s_pv;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int m = n - k0;
+  const int rlo = b * R, rhi = min(m, rlo + R);
+  const int nr = max(0, rhi - rlo);
+  for (int c = w; c < kb; c += kWarps)
+    for (int i = lane; i < nr; i += 32) S[i * (kLB + 1) + c] = W[(size_t)(k0 + c) * ldw + k0 + rlo + i];
+  __syncthreads();
+  T* candT = reinterpret_cast<T*>(pb.cand);
+  T* rowsT = reinterpret_cast<T*>(pb.rows);
+  T* diagT = reinterpret_cast<T*>(pb.diag);
+  for (int c = 0; c < kb; ++c) {
+    const int buf = c & 1;
+    // local candidate among own rows >= c
+    T best = T(-1), bval = T(0);
+    int bi = 0x7fffffff;
+    for (int i = tid; i < nr; i += kThreads) {
+      if (rlo + i < c) continue;
+      const T v = S[i * (kLB + 1) + c];
+      const T a = fabs(v);
+      if (a > best) { best = a; bi = rlo + i; bval = v; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      const T ov = __shfl_xor_sync(0xffffffffu, bval, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bval = ov; }
+    }
+    if (lane == 0) { s_best[w] = best; s_idx[w] = bi; s_val[w] = bval; }
+    __syncthreads();
+    if (tid == 0) {
+      T bb = s_best[0], bv = s_val[0];
+      int ii = s_idx[0];
+      for (int k = 1; k < kWarps; ++k)
+        if (s_best[k] > bb || (s_best[k] == bb && s_idx[k] < ii)) { bb = s_best[k]; ii = s_idx[k]; bv = s_val[k]; }
+      T* cd = candT + ((size_t)buf * G + b) * 4;
+      cd[0] = bb;
+      cd[1] = (T)ii;
+      cd[2] = bv;
+      cd[3] = (ii != 0x7fffffff && bb >= T(0)) ? T(1) : T(0);
+      s_p = ii;
+    }
+    __syncthreads();
+    {  // publish the candidate row and, if owned, the diagonal row
+      const int ii = s_p;
+      if (ii != 0x7fffffff && ii >= rlo && ii < rhi)
+        for (int k = tid; k < kb; k += kThreads)
+          rowsT[((size_t)buf * G + b) * kLB + k] = S[(ii - rlo) * (kLB + 1) + k];
+      if (c >= rlo && c < rhi)
+        for (int k = tid; k < kb; k += kThreads) diagT[(size_t)buf * kLB + k] = S[(c - rlo) * (kLB + 1) + k];
+    }
+    __threadfence();
+    if (!grid_barrier(pb.bar, (unsigned)G, pb.err)) return;
+    // every CTA finds the same winner: the candidates are read in parallel
+    // (one per thread) and reduced (largest |v|, then smallest row)
+    {
+      T bb = T(-1), bv = T(0);
+      int ii = 0x7fffffff, wb = 0x7fffffff;
+      for (int k = tid; k < G; k += kThreads) {
+        const volatile T* cd = candT + ((size_t)buf * G + k) * 4;
+        if (cd[3] == T(0)) continue;
+        const T kb_ = cd[0];
+        const int ki = (int)cd[1];
+        if (kb_ > bb || (kb_ == bb && ki < ii)) { bb = kb_; ii = ki; bv = cd[2]; wb = k; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, bb, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ii, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int ow = __shfl_xor_sync(0xffffffffu, wb, o);
+        if (ob > bb || (ob == bb && oi < ii)) { bb = ob; ii = oi; bv = ov; wb = ow; }
+      }
+      __syncthreads();
+      if (lane == 0) { s_best[w] = bb; s_idx[w] = ii; s_val[w] = bv; s_idxw[w] = wb; }
+      __syncthreads();
+      if (tid == 0) {
+        bb = s_best[0]; ii = s_idx[0]; bv = s_val[0]; wb = s_idxw[0];
+        for (int k = 1; k < kWarps; ++k)
+          if (s_best[k] > bb || (s_best[k] == bb && s_idx[k] < ii)) {
+            bb = s_best[k]; ii = s_idx[k]; bv = s_val[k]; wb = s_idxw[k];
+          }
+        s_p = ii;
+        s_wb = wb;
+        s_pv = bv;
+        s_stop = (wb < 0 || wb >= G || ii < c || ii >= m || bv == T(0) || bv != bv) ? 1 : 0;
+        if (s_stop && b == 0) *fail = k0 + c + 1;
+        if (!s_stop && b == 0) piv[k0 + c] = k0 + ii;
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;  // uniform across the grid: every CTA saw the same candidates
+    const int p = s_p;
+    for (int k = tid; k < kb; k += kThreads) prow[k] = ((volatile T*)rowsT)[((size_t)buf * G + s_wb) * kLB + k];
+    __syncthreads();
+    if (p != c) {
+      if (p >= rlo && p < rhi)
+        for (int k = tid; k < kb; k += kThreads) S[(p - rlo) * (kLB + 1) + k] = ((volatile T*)diagT)[(size_t)buf * kLB + k];
+      if (c >= rlo && c < rhi)
+        for (int k = tid; k < kb; k += kThreads) S[(c - rlo) * (kLB + 1) + k] = prow[k];
+    }
+    __syncthreads();
+    const T inv = T(1) / s_pv;
+    for (int i = tid; i < nr; i += kThreads) {
+      if (rlo + i <= c) continue;
+      T* row = S + i * (kLB + 1);
+      const T l = row[c] * inv;
+      row[c] = l;
+      for (int k = c + 1; k < kb; ++k) row[k] -= l * prow[k];
+    }
+    __syncthreads();
+  }
+  for (int c = w; c < kb; c += kWarps)
+    for (int i = lane; i < nr; i += 32) W[(size_t)(k0 + c) * ldw + k0 + rlo + i] = S[i * (kLB + 1) + c];
+}
+
+// Row swaps of one panel applied to every column outside it.
+template <typename T>
+__global__ void k_swap_rows(T* W, int ldw, int n, int k0, int kb, const int* __restrict__ piv) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n || (col >= k0 && col < k0 + kb)) return;
+  T* cp = W + (size_t)col * ldw;
+  for (int c = 0; c < kb; ++c) {
+    const int p = piv[k0 + c];
+    if (p != k0 + c) {
+      const T a = cp[k0 + c];
+      cp[k0 + c] = cp[p];
+      cp[p] = a;
+    }
+  }
+}
+
+// ------------------------------------------- FP64 GEMM (mma.sync f64)
+// C (M x N) -= A (M x K) * B (K x N) (B transposed when TB); LO skips tiles
+// strictly above the diagonal.  64 x 64 tiles, K chunks of 16.
+template <bool TB, bool LO>
+__global__ void __launch_bounds__(kThreads) k_gemm_dmma(double* __restrict__ C, int ldc, const double* __restrict__ A,
+                                                       int lda, const double* __restrict__ B, int ldb, int M, int N,
+                                                       int K) {
+  if (LO && blockIdx.y > blockIdx.x) return;
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int wr = (w & 3) * 16, wc = (w >> 2) * 32;
+  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+  double acc[2][4][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q][0] = acc[a][q][1] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
+      const int r = e & 63, k = e >> 6;
+      As[k][r] = (m0 + r < M && k0 + k < K) ? A[(size_t)(k0 + k) * lda + m0 + r] : 0.0;
+      if (TB) Bs[k][r] = (n0 + r < N && k0 + k < K) ? B[(size_t)(k0 + k) * ldb + n0 + r] : 0.0;
+    }
+    if (!TB)
+      for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
+        const int k = e & 15, c = e >> 4;
+        Bs[k][c] = (n0 + c < N && k0 + k < K) ? B[(size_t)(n0 + c) * ldb + k0 + k] : 0.0;
+      }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; kk += 4) {
+      double af[2], bf[4];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) af[a] = As[kk + t][wr + a * 8 + g];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bf[q] = Bs[kk + t][wc + q * 8 + g];
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dmma_8x8x4(acc[a][q][0], acc[a][q][1], af[a], bf[q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int r = m0 + wr + a * 8 + g;
+    if (r >= M) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = n0 + wc + q * 8 + 2 * t + h;
+        if (c < N) C[(size_t)c * ldc + r] -= acc[a][q][h];
+      }
+  }
+}
+
+// --------------------------------------- blocked triangular solve steps
+// Diagonal block: x[b0:b0+bs, cols] <- inv(E_bb) x, E = trans ? M^T : M, by
+// substitution (cta_tri_solve) on an 8-column chunk per CTA.
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) k_tri_diag(const T* __restrict__ M, int ldm, int b0, int bs, int lower,
+                                                      int trans, int unit, V* x, int ldx, int nrhs) {
+  __shared__ V xs[kLB * 8];
+  const int c0 = blockIdx.x * 8, nc = min(8, nrhs - c0);
+  if (nc <= 0) return;
+  for (int e = threadIdx.x; e < kLB * 8; e += kThreads) {
+    const int r = e & (kLB - 1), c = e >> 7;
+    xs[e] = (r < bs && c < nc) ? x[(size_t)(c0 + c) * ldx + b0 + r] : V(0);
+  }
+  __syncthreads();
+  cta_tri_solve<T, V>(M + (size_t)b0 * ldm + b0, ldm, bs, lower != 0, trans != 0, unit != 0, xs, kLB, nc);
+  for (int e = threadIdx.x; e < kLB * 8; e += kThreads) {
+    const int r = e & (kLB - 1), c = e >> 7;
+    if (r < bs && c < nc) x[(size_t)(c0 + c) * ldx + b0 + r] = xs[e];
+  }
+}
+
+// Update: x[r, c] -= sum_{j < bs} E(r, b0 + j) x[b0 + j, c] for r in [rlo, rhi).
+// CTA tile: 64 rows x 16 right-hand sides; E tile and x block in shared memory.
+template <typename T, typename V>
+__global__ void __launch_bounds__(kThreads) k_tri_update(const T* __restrict__ M, int ldm, int b0, int bs, int rlo,
+                                                        int rhi, int trans, V* x, int ldx, int nrhs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  V(*Es)[kLB + 1] = reinterpret_cast<V(*)[kLB + 1]>(smem);                         // [64][kLB+1]
+  V(*xb)[kLB + 1] = reinterpret_cast<V(*)[kLB + 1]>(smem + sizeof(V) * 64 * (kLB + 1));  // [16][kLB+1]
+  const int r0 = rlo + blockIdx.x * 64, c0 = blockIdx.y * 16;
+  if (r0 >= rhi) return;
+  const int nrow = min(64, rhi - r0), nc = min(16, nrhs - c0);
+  if (!trans) {  // E(r, j) = M[j * ldm + r]: lanes over r
+    for (int e = threadIdx.x; e < 64 * kLB; e += kThreads) {
+      const int r = e & 63, j = e >> 6;
+      Es[r][j] = (r < nrow && j < bs) ? (V)M[(size_t)(b0 + j) * ldm + r0 + r] : V(0);
+    }
+  } else {  // E(r, j) = M[r * ldm + j]: lanes over j
+    for (int e = threadIdx.x; e < 64 * kLB; e += kThreads) {
+      const int j = e & (kLB - 1), r = e >> 7;
+      Es[r][j] = (r < nrow && j < bs) ? (V)M[(size_t)(r0 + r) * ldm + b0 + j] : V(0);
+    }
+  }
+  for (int e = threadIdx.x; e < 16 * kLB; e += kThreads) {
+    const int j = e & (kLB - 1), c = e >> 7;
+    xb[c][j] = (j < bs && c < nc) ? x[(size_t)(c0 + c) * ldx + b0 + j] : V(0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 16; e += kThreads) {
+    const int r = e & 63, c = e >> 6;
+    if (r >= nrow || c >= nc) continue;
+    V acc = V(0);
+#pragma unroll 8
+    for (int j = 0; j < kLB; ++j) acc += Es[r][j] * xb[c][j];
+    x[(size_t)(c0 + c) * ldx + r0 + r] -= acc;
+  }
+}
+
+// ------------------------------------------------------ FP64 residual
+// R = B - A X (FP64), one warp per 8-row group, all right-hand sides in
+// chunks of 8 on mma.sync f64 (A fragment loaded once per chunk set).
+// rmax[c] (as bits of a non-negative double) <- max |R(:, c)|.
+__global__ void __launch_bounds__(kThreads) k_residual_large(const double* __restrict__ A, int n,
+                                                            const double* __restrict__ B, const double* __restrict__ X,
+                                                            int nrhs, double* __restrict__ R,
+                                                            unsigned long long* rmax) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int nchunk = (nrhs + 7) / 8;
+  for (int r0 = (blockIdx.x * kWarps + w) * 8; r0 < n; r0 += gridDim.x * kWarps * 8) {
+    for (int cc = 0; cc < nchunk; cc += 8) {  // up to 64 right-hand sides per pass
+      double acc[8][2];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = 0.0;
+      const int ra = r0 + g;
+      for (int k = 0; k < n; k += 4) {
+        const int ka = k + t;
+        const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * n + ra) : 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int col = (cc + q) * 8 + g;
+          if ((cc + q) < nchunk) {
+            const double bv = (col < nrhs && ka < n) ? X[(size_t)col * n + ka] : 0.0;
+            dmma_8x8x4(acc[q][0], acc[q][1], a, bv);
+          }
+        }
+      }
+      const int r = r0 + g;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if ((cc + q) >= nchunk) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = (cc + q) * 8 + 2 * t + h;
+          if (r < n && col < nrhs) {
+            const double v = B[(size_t)col * n + r] - acc[q][h];
+            R[(size_t)col * n + r] = v;
+            atomicMax(rmax + col, (unsigned long long)__double_as_longlong(fabs(v)));
+          }
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ vector helpers
+template <typename V>
+__global__ void k_colmax_abs(const V* __restrict__ x, int n, int nrhs, unsigned long long* out) {
+  for (int c = blockIdx.y; c < nrhs; c += gridDim.y) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      m = fmax(m, fabs((double)x[(size_t)c * n + i]));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) atomicMax(out + c, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// xs = (V)(src / scale[c])  and  x += (double)xs * scale[c]
+template <typename V>
+__global__ void k_scale_down(const double* __restrict__ src, int n, int nrhs, const double* scale, V* dst) {
+  const size_t tot = (size_t)n * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x)
+    dst[e] = (V)(src[e] / scale[e / n]);
+}
+template <typename V>
+__global__ void k_scale_add(double* __restrict__ x, int n, int nrhs, const double* scale, const V* d, int assign) {
+  const size_t tot = (size_t)n * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const double v = (double)d[e] * scale[e / n];
+    x[e] = assign ? v : x[e] + v;
+  }
+}
+
+// permutation: dst[k] = src[perm[k]] (forward) or dst[perm[k]] = src[k]
+template <typename V>
+__global__ void k_permute(const V* __restrict__ src, V* __restrict__ dst, int n, int nrhs, const int* perm, int inverse) {
+  const size_t tot = (size_t)n * nrhs;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % n);
+    const size_t c = e / n;
+    if (!inverse) dst[e] = src[c * n + perm[k]];
+    else dst[c * n + perm[k]] = src[e];
+  }
+}
+
+__global__ void k_build_perm(const int* piv, int n, int* perm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int k = 0; k < n; ++k) perm[k] = k;
+  for (int k = 0; k < n; ++k) {
+    const int p = piv[k];
+    const int t = perm[k];
+    perm[k] = perm[p];
+    perm[p] = t;
+  }
+}
+
+// estimator helpers (one CTA of 1024 threads each)
+template <typename V>
+__global__ void k_vec_sumabs(const V* x, int n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs((double)x[i]);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    *out = t;
+  }
+}
+template <typename V>
+__global__ void k_vec_argmax(const V* x, int n, int* out, double* vals, int jprev) {
+  __shared__ double rv[32];
+  __shared__ int ri[32];
+  double best = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs((double)x[i]);
+    if (a > best) { best = a; bi = i; }
+  }
+  warp_argmax_first(best, bi);
+  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = rv[0];
+    int ii = ri[0];
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
+      if (rv[k] > b || (rv[k] == b && ri[k] < ii)) { b = rv[k]; ii = ri[k]; }
+    *out = ii;
+    vals[0] = (ii >= 0 && ii < n) ? fabs((double)x[ii]) : 0.0;
+    vals[1] = (jprev >= 0 && jprev < n) ? (double)x[jprev] : 0.0;
+  }
+}
+// mode 0: x = 1/n; 1: x = e_j; 2: alternating test vector;
+// 3: xi = sign(x), x = xi, flag[0] |= (sign changed)
+template <typename V>
+__global__ void k_vec_set(V* x, V* xi, int n, int mode, int j, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (mode == 0) x[i] = V(1) / V(n);
+    else if (mode == 1) x[i] = (i == j) ? V(1) : V(0);
+    else if (mode == 2) x[i] = ((i & 1) ? V(-1) : V(1)) * (V(1) + V(i) / V(n - 1));
+    else {
+      const V sg = x[i] >= V(0) ? V(1) : V(-1);
+      if (sg != xi[i]) atomicOr(flag, 1);
+      xi[i] = sg;
+      x[i] = sg;
+    }
+  }
+}
+
+
+// ===================================================================== host
+size_t scan_large_workspace(int64_t n);
+cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64_t nb, double band_frac,
+                              double tol, void* ws, ScanRes* out, int num_sms, cudaStream_t st);
+
+struct LargeArgs {
+  const double* A;
+  const double* B;
+  double* X;
+  int64_t n, nrhs;
+  uint32_t flags;
+  int precision;
+  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
+  int ir_max_iter;
+  int num_sms;
+  cudaStream_t st;
+};
+
+namespace {
+
+struct Arena {
+  char* base;
+  size_t used, cap;
+  void* take(size_t bytes) {
+    const size_t off = (used + 255) & ~(size_t)255;
+    if (off + bytes > cap) return nullptr;
+    used = off + bytes;
+    return base + off;
+  }
+};
+
+#define LCK(x)                                      \
+  do {                                              \
+    cudaError_t _e = (x);                           \
+    if (_e != cudaSuccess) return ASOLVE_E_CUDA;    \
+  } while (0)
+
+template <typename T>
+struct Fac {  // a factorisation of the large path and its scratch
+  T* W;
+  int ldw;
+  int* piv;
+  int* perm;
+  T* Dtmp;       // 128 x 128 inverse of the current diagonal block
+  int* fail;     // device
+  PanelBuf pb;
+  size_t panel_smem;
+};
+
+template <typename T>
+int tri_solve_large(const T* M, int ldm, int n, bool lower, bool trans, bool unit, void* xv, int nrhs,
+                    bool vfloat, cudaStream_t st) {
+  const bool elower = (lower != trans);
+  const int nblk = (n + kLB - 1) / kLB;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = elower ? bi : nblk - 1 - bi;
+    const int b0 = blk * kLB, bs = std::min(kLB, n - b0);
+    const int rlo = elower ? b0 + bs : 0, rhi = elower ? n : b0;
+    if (vfloat) {
+      float* x = static_cast<float*>(xv);
+      k_tri_diag<T, float><<<(nrhs + 7) / 8, kThreads, 0, st>>>(M, ldm, b0, bs, lower, trans, unit, x, n, nrhs);
+      if (rhi > rlo) {
+        dim3 g((rhi - rlo + 63) / 64, (nrhs + 15) / 16);
+        k_tri_update<T, float><<<g, kThreads, sizeof(float) * 80 * (kLB + 1), st>>>(M, ldm, b0, bs, rlo, rhi, trans, x,
+                                                                                   n, nrhs);
+      }
+    } else {
+      double* x = static_cast<double*>(xv);
+      k_tri_diag<T, double><<<(nrhs + 7) / 8, kThreads, 0, st>>>(M, ldm, b0, bs, lower, trans, unit, x, n, nrhs);
+      if (rhi > rlo) {
+        dim3 g((rhi - rlo + 63) / 64, (nrhs + 15) / 16);
+        k_tri_update<T, double><<<g, kThreads, sizeof(double) * 80 * (kLB + 1), st>>>(M, ldm, b0, bs, rlo, rhi, trans,
+                                                                                     x, n, nrhs);
+      }
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
+}
+
+template <typename T, typename V>
+int apply_large(const Fac<T>& f, bool lu, int n, V* x, int nrhs, bool trans, V* tmp, cudaStream_t st) {
+  const bool vf = sizeof(V) == 4;
+  const int g = 1024;
+  if (lu) {
+    if (!trans) {
+      k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 0);
+      LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+      int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, true, x, nrhs, vf, st);
+      if (rc) return rc;
+      return tri_solve_large<T>(f.W, f.ldw, n, false, false, false, x, nrhs, vf, st);
+    }
+    int rc = tri_solve_large<T>(f.W, f.ldw, n, false, true, false, x, nrhs, vf, st);
+    if (rc) return rc;
+    rc = tri_solve_large<T>(f.W, f.ldw, n, true, true, true, x, nrhs, vf, st);
+    if (rc) return rc;
+    k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 1);
+    LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+    return ASOLVE_OK;
+  }
+  int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, false, x, nrhs, vf, st);
+  if (rc) return rc;
+  return tri_solve_large<T>(f.W, f.ldw, n, true, true, false, x, nrhs, vf, st);
+}
+
+template <typename T>
+cudaError_t gemm_update(T* C, int ldc, const T* A, int lda, const T* B, int ldb, int M, int N, int K, bool tb,
+                        bool lower, int* err, cudaStream_t st);
+template <>
+cudaError_t gemm_update<float>(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
+                               int K, bool tb, bool lower, int* err, cudaStream_t st) {
+  return launch_gemm_tc(C, ldc, A, lda, B, ldb, M, N, K, 3, err, st, tb, lower);
+}
+template <>
+cudaError_t gemm_update<double>(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N,
+                                int K, bool tb, bool lower, int* err, cudaStream_t st) {
+  dim3 g((M + 63) / 64, (N + 63) / 64);
+  if (tb && lower) k_gemm_dmma<true, true><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else if (tb) k_gemm_dmma<true, false><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else if (lower) k_gemm_dmma<false, true><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else k_gemm_dmma<false, false><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  return cudaGetLastError();
+}
+
+template <typename T>
+int set_large_attrs() {
+  static bool done = false;
+  if (done) return ASOLVE_OK;
+  LCK(cudaFuncSetAttribute(k_tri_block_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(T) * kLB * (kLB + 1))));
+  LCK(cudaFuncSetAttribute(k_trsm_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(T) * (kLB + 64) * (kLB + 1))));
+  // the panel kernel also has a little static shared memory
+  LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  LCK(cudaFuncSetAttribute(k_tri_update<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(float) * 80 * (kLB + 1))));
+  LCK(cudaFuncSetAttribute(k_tri_update<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * 80 * (kLB + 1))));
+  LCK(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  done = true;
+  return ASOLVE_OK;
+}
+
+// Blocked Cholesky of the working matrix; returns 0 or (failing column + 1).
+template <typename T>
+int chol_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
+  LCK(cudaMemsetAsync(f.fail, 0, sizeof(int) * 2, st));
+  const int nb = sizeof(T) == 4 ? 32 : 16;
+  const size_t dsm = (size_t)kLB * nb * sizeof(T) + 64 * 32 * sizeof(T) * 2 + 256;
+  for (int k0 = 0; k0 < n; k0 += kLB) {
+    const int kb = std::min(kLB, n - k0);
+    k_chol_diag<T><<<1, kThreads, dsm, st>>>(f.W, f.ldw, k0, kb, nb, f.fail);
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      k_tri_block_inv<T><<<1, kLB, sizeof(T) * kLB * (kLB + 1), st>>>(f.W, f.ldw, k0, kb, 1, 0, f.Dtmp);
+      k_trsm_inv<T><<<(rest + 63) / 64, kThreads, sizeof(T) * (kLB + 64) * (kLB + 1), st>>>(
+          f.W, f.ldw, k0, kb, k0 + kb, n, f.Dtmp, 1);
+      T* L21 = f.W + (size_t)k0 * f.ldw + k0 + kb;
+      LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, L21, f.ldw, L21, f.ldw, rest, rest, kb,
+                         true, true, f.fail + 1, st));
+    }
+  }
+  LCK(cudaGetLastError());
+  int h[2];
+  LCK(cudaMemcpyAsync(h, f.fail, sizeof(h), cudaMemcpyDeviceToHost, st));
+  LCK(cudaStreamSynchronize(st));
+  if (h[1]) return ASOLVE_E_TIMEOUT;
+  *fail_out = h[0];
+  return ASOLVE_OK;
+}
+
+template <typename T>
+int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
+  LCK(cudaMemsetAsync(f.fail, 0, sizeof(int) * 2, st));
+  const int G = num_sms;
+  for (int k0 = 0; k0 < n; k0 += kLB) {
+    const int kb = std::min(kLB, n - k0), m = n - k0;
+    const int R = (m + G - 1) / G;
+    const size_t psmem = sizeof(T) * ((size_t)R * (kLB + 1) + kLB) + 64;
+    if (psmem > 226 * 1024) return ASOLVE_E_UNSUPPORTED;
+    LCK(cudaMemsetAsync(f.pb.bar, 0, sizeof(unsigned) * 2, st));
+    T* W = f.W;
+    int ldw = f.ldw;
+    int* piv = f.piv;
+    PanelBuf pb = f.pb;
+    int* fail = f.fail;
+    void* args[] = {&W, &ldw, &n, &k0, (void*)&kb, (void*)&R, &piv, &pb, &fail};
+    LCK(cudaLaunchCooperativeKernel((void*)k_lu_panel<T>, dim3(G), dim3(kThreads), args, psmem, st));
+    k_swap_rows<T><<<(n + 255) / 256, 256, 0, st>>>(f.W, f.ldw, n, k0, kb, f.piv);
+    const int rest = n - k0 - kb;
+    if (rest > 0) {
+      k_tri_block_inv<T><<<1, kLB, sizeof(T) * kLB * (kLB + 1), st>>>(f.W, f.ldw, k0, kb, 1, 1, f.Dtmp);
+      k_trsm_inv<T><<<(rest + 63) / 64, kThreads, sizeof(T) * (kLB + 64) * (kLB + 1), st>>>(
+          f.W, f.ldw, k0, kb, k0 + kb, n, f.Dtmp, 0);
+      LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, f.W + (size_t)k0 * f.ldw + k0 + kb,
+                         f.ldw, f.W + (size_t)(k0 + kb) * f.ldw + k0, f.ldw, rest, rest, kb, false, false,
+                         f.fail + 1, st));
+    }
+  }
+  LCK(cudaGetLastError());
+  k_build_perm<<<1, 32, 0, st>>>(f.piv, n, f.perm);
+  int h[2], perr = 0;
+  LCK(cudaMemcpyAsync(h, f.fail, sizeof(h), cudaMemcpyDeviceToHost, st));
+  LCK(cudaMemcpyAsync(&perr, f.pb.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LCK(cudaStreamSynchronize(st));
+  if (h[1] || perr) return ASOLVE_E_TIMEOUT;
+  *fail_out = h[0];
+  return ASOLVE_OK;
+}
+
+// 1-norm estimate of inv(A) (Hager 1984, Higham 1988), the iteration driven
+// from the host; apply(v, trans) overwrites the device vector v.
+template <typename V, typename Apply>
+int est_large(int n, V* v, V* xi, double* dscal, int* dint, Apply apply, cudaStream_t st, double* out) {
+  auto sumabs = [&](double* r) -> int {
+    k_vec_sumabs<V><<<1, 1024, 0, st>>>(v, n, dscal);
+    LCK(cudaMemcpyAsync(r, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    return ASOLVE_OK;
+  };
+  const int g = (n + 255) / 256;
+  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 0, 0, dint);
+  int rc = apply(v, false);
+  if (rc) return rc;
+  double est;
+  if (n == 1) {
+    V h;
+    LCK(cudaMemcpyAsync(&h, v, sizeof(V), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    *out = fabs((double)h);
+    return ASOLVE_OK;
+  }
+  if ((rc = sumabs(&est))) return rc;
+  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 3, 0, dint);
+  if ((rc = apply(v, true))) return rc;
+  int k = 2;
+  int jprev = -1;
+  for (;;) {
+    int j;
+    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, jprev);
+    LCK(cudaMemcpyAsync(&j, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    if (j < 0 || j >= n) { est = NAN; break; }
+    k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 1, j, dint);
+    if ((rc = apply(v, false))) return rc;
+    const double estold = est;
+    if ((rc = sumabs(&est))) return rc;
+    LCK(cudaMemsetAsync(dint, 0, sizeof(int), st));
+    k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 3, 0, dint);
+    int changed = 0;
+    LCK(cudaMemcpyAsync(&changed, dint, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    if (!changed || est <= estold) break;
+    if ((rc = apply(v, true))) return rc;
+    double vals[2];
+    int jn;
+    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, j);
+    LCK(cudaMemcpyAsync(&jn, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LCK(cudaMemcpyAsync(vals, dscal + 1, sizeof(vals), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    ++k;
+    if (jn < 0 || jn >= n) { est = NAN; break; }
+    jprev = j;
+    if (vals[1] == vals[0] || k > 5) break;
+  }
+  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 2, 0, dint);
+  if ((rc = apply(v, false))) return rc;
+  double s2;
+  if ((rc = sumabs(&s2))) return rc;
+  const double temp = 2.0 * s2 / (double)(3 * n);
+  if (temp > est) est = temp;
+  *out = est;
+  return ASOLVE_OK;
+}
+
+double rcond_of(double anorm, double est) {
+  if (anorm == 0.0 || std::isinf(est) || est == 0.0) return 0.0;
+  return (1.0 / est) / anorm;
+}
+
+}  // namespace
+
+size_t large_ws_bytes(int64_t n, int64_t nrhs) {
+  const size_t ldw = (size_t)((n + 3) & ~3);
+  size_t b = 0;
+  b += sizeof(double) * ldw * n + 256;                 // working matrix (FP64 worst case)
+  b += 2 * sizeof(int) * n + 512;                      // piv, perm
+  b += sizeof(double) * kLB * kLB + 256;               // Dtmp
+  b += 4 * sizeof(double) * (size_t)n * nrhs + 1024;   // R, Xs, tmp, (spare)
+  b += 4 * sizeof(double) * (size_t)n + 512;           // estimator vectors
+  b += 2 * sizeof(double) * 1024 * (kLB + 4) + 2 * sizeof(double) * kLB + 1024;  // panel buffers (G <= 1024)
+  b += scan_large_workspace(n) + 4096;
+  return b + (1 << 20);
+}
+
+// The adaptive solve of one large system.  ws: device workspace of at least
+// large_ws_bytes(n, nrhs).  Fills *info; returns the status.
+int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info) {
+  cudaStream_t st = a.st;
+  const int n = (int)a.n, nrhs = (int)a.nrhs;
+  Arena ar{static_cast<char*>(ws), 0, ws_bytes};
+  memset(info, 0, sizeof(*info));
+  info->rcond = NAN;
+  info->berr = NAN;
+  info->svd_rank = -1;
+  // ---- scan (Sec. 2.1, 2.2, Fig. 4)
+  void* sws = ar.take(scan_large_workspace(n));
+  ScanRes* dsr = static_cast<ScanRes*>(ar.take(sizeof(ScanRes)));
+  double* dscal = static_cast<double*>(ar.take(sizeof(double) * 8));
+  int* dint = static_cast<int*>(ar.take(sizeof(int) * 8));
+  if (!sws || !dsr || !dscal || !dint) return ASOLVE_E_NOMEM;
+  LCK(launch_scan_large(a.A, n, a.B, (int64_t)n * nrhs, a.band_frac, a.sympd_tol, sws, dsr, a.num_sms, st));
+  ScanRes sr;
+  LCK(cudaMemcpyAsync(&sr, dsr, sizeof(sr), cudaMemcpyDeviceToHost, st));
+  LCK(cudaStreamSynchronize(st));
+  info->cls = sr.cls;
+  info->kl = sr.kl;
+  info->ku = sr.ku;
+  if (sr.flags & (SF_NONFINITE | SF_B_NONFINITE)) return info->status = ASOLVE_E_NONFINITE;
+  if (a.flags & ASOLVE_FORCE_SVD) return info->status = ASOLVE_E_UNSUPPORTED;
+  int cls = (a.flags & ASOLVE_FORCE_LU) ? ASOLVE_CLS_GENERAL : sr.cls;
+  if (cls == ASOLVE_CLS_BANDED) return info->status = ASOLVE_E_UNSUPPORTED;  // dense input, band route: n <= 1024
+  const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
+  const int ldw = (n + 3) & ~3;
+  double* R = static_cast<double*>(ar.take(sizeof(double) * (size_t)n * nrhs));
+  void* xs = ar.take(sizeof(double) * (size_t)n * nrhs);
+  void* tmp = ar.take(sizeof(double) * (size_t)n * nrhs);
+  void* ev = ar.take(sizeof(double) * (size_t)n);
+  void* exi = ar.take(sizeof(double) * (size_t)n);
+  unsigned long long* colmax = static_cast<unsigned long long*>(ar.take(sizeof(unsigned long long) * 3 * nrhs));
+  if (!R || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
+  // ---- triangular route (Sec. 2.2): FP64 substitution on A itself
+  if (cls == ASOLVE_CLS_LOWER || cls == ASOLVE_CLS_UPPER) {
+    const bool lower = cls == ASOLVE_CLS_LOWER;
+    info->route = lower ? ASOLVE_ROUTE_TRI_LOWER : ASOLVE_ROUTE_TRI_UPPER;
+    info->precision = ASOLVE_PREC_FP64;
+    // singular iff some A_ii == 0 (the scan's diagonal is not kept: check here)
+    LCK(cudaMemsetAsync(dint, 0, sizeof(int), st));
+    {
+      std::vector<double> diag((size_t)n);
+      LCK(cudaMemcpy2DAsync(diag.data(), sizeof(double), a.A, sizeof(double) * (n + 1), sizeof(double), n,
+                            cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      for (int i = 0; i < n; ++i)
+        if (diag[(size_t)i] == 0.0) {
+          LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
+          info->status = (a.flags & ASOLVE_NO_APPROX) ? ASOLVE_E_SINGULAR : ASOLVE_E_UNSUPPORTED;
+          return info->status;
+        }
+    }
+    LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+    int rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, st);
+    if (rc) return rc;
+    double rc_val = NAN;
+    if (!no_rcond) {
+      double est;
+      auto apply = [&](double* v, bool tr) { return tri_solve_large<double>(a.A, n, n, lower, tr, false, v, 1, false, st); };
+      rc = est_large<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est);
+      if (rc) return rc;
+      rc_val = rcond_of(sr.norm1, est);
+    }
+    info->rcond = rc_val;
+    if (a.flags & ASOLVE_BERR) {
+      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+      k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+      std::vector<unsigned long long> hm((size_t)3 * nrhs);
+      LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      double be = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        double rm, xm, bm;
+        memcpy(&rm, &hm[c], 8);
+        memcpy(&xm, &hm[nrhs + c], 8);
+        memcpy(&bm, &hm[2 * nrhs + c], 8);
+        const double den = sr.norminf * xm + bm;
+        const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+        if (!(b1 <= be)) be = b1;
+      }
+      info->berr = be;
+    }
+    const bool poor = !no_rcond && !(rc_val >= a.rcond_threshold);
+    info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
+    return info->status;
+  }
+  // ---- dense routes: Cholesky (Sec. 2.3) or LU (Sec. 2.4)
+  int* piv = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
+  int* perm = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
+  int* fail = static_cast<int*>(ar.take(sizeof(int) * 4));
+  void* Dtmp = ar.take(sizeof(double) * kLB * kLB);
+  void* pcand = ar.take(sizeof(double) * 2 * a.num_sms * 4);
+  void* prows = ar.take(sizeof(double) * 2 * a.num_sms * kLB);
+  void* pdiag = ar.take(sizeof(double) * 2 * kLB);
+  unsigned* pbar = static_cast<unsigned*>(ar.take(sizeof(unsigned) * 4));
+  int* perr = static_cast<int*>(ar.take(sizeof(int) * 4));
+  void* Wv = ar.take(sizeof(double) * (size_t)ldw * n);
+  if (!piv || !perm || !fail || !Dtmp || !pcand || !prows || !pdiag || !pbar || !perr || !Wv) return ASOLVE_E_NOMEM;
+  LCK(cudaMemsetAsync(perr, 0, sizeof(int) * 4, st));
+  PanelBuf pb{pcand, prows, pdiag, pbar, perr};
+  bool chol = (cls == ASOLVE_CLS_SYMPD);
+  info->route = chol ? ASOLVE_ROUTE_CHOL : ASOLVE_ROUTE_LU;
+  int detail = 0;
+  int rc;
+  // ---- mixed precision: FP32 factors, FP64 refinement
+  if (a.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
+    if ((rc = set_large_attrs<float>())) return rc;
+    Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0};
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const bool try_chol = chol && attempt == 0;
+      if (!chol && attempt == 1) break;
+      k_to_work<float><<<a.num_sms * 4, 256, 0, st>>>(a.A, n, f.W, ldw);
+      int fcol = 0;
+      rc = try_chol ? chol_large<float>(f, n, a.num_sms, &fcol, st) : lu_large<float>(f, n, a.num_sms, &fcol, st);
+      if (rc) return rc;
+      if (fcol) {
+        if (try_chol) detail |= 4;
+        break;  // FP32 factorisation failed: FP64 path decides
+      }
+      const bool lu = !try_chol;
+      double rcv = NAN;
+      bool gate_ok = true;
+      if (!no_rcond) {
+        double est;
+        auto apply = [&](float* v, bool tr) { return apply_large<float, float>(f, lu, n, v, 1, tr, (float*)tmp, st); };
+        rc = est_large<float>(n, (float*)ev, (float*)exi, dscal, dint, apply, st, &est);
+        if (rc) return rc;
+        rcv = rcond_of(sr.norm1, est);
+        gate_ok = rcv >= 1.0 / a.ir_kappa_limit;
+      }
+      if (!gate_ok) { detail |= 1; break; }
+      // refinement: x0 = inv(A32) b; loop r = b - A x (FP64), x += inv(A32) r
+      std::vector<unsigned long long> hm((size_t)3 * nrhs);
+      std::vector<double> scale((size_t)nrhs);
+      double* dscale = static_cast<double*>(ev);  // reuse (n >= nrhs)
+      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+      LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      std::vector<double> bmax((size_t)nrhs);
+      for (int c = 0; c < nrhs; ++c) {
+        memcpy(&bmax[c], &hm[2 * nrhs + c], 8);
+        scale[c] = bmax[c] > 0.0 ? bmax[c] : 1.0;
+      }
+      LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+      k_scale_down<float><<<1024, 256, 0, st>>>(a.B, n, nrhs, dscale, (float*)xs);
+      if ((rc = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st))) return rc;
+      k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 1);
+      double berr_prev = INFINITY, berr = INFINITY;
+      int iters = 0;
+      bool ok = false;
+      for (int it = 0;; ++it) {
+        LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
+        k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+        k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+        LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+        LCK(cudaStreamSynchronize(st));
+        berr = 0.0;
+        for (int c = 0; c < nrhs; ++c) {
+          double rm, xm;
+          memcpy(&rm, &hm[c], 8);
+          memcpy(&xm, &hm[nrhs + c], 8);
+          const double den = sr.norminf * xm + bmax[c];
+          const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+          if (!(b1 <= berr)) berr = b1;
+          scale[c] = rm > 0.0 ? rm : 1.0;
+        }
+        const bool conv = berr <= a.ir_target_berr;
+        if (!conv && (it >= a.ir_max_iter || !(berr < 0.5 * berr_prev))) break;
+        berr_prev = berr;
+        LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+        k_scale_down<float><<<1024, 256, 0, st>>>(R, n, nrhs, dscale, (float*)xs);
+        if ((rc = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st))) return rc;
+        k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 0);
+        ++iters;
+        if (conv) { ok = true; break; }
+      }
+      LCK(cudaStreamSynchronize(st));
+      if (ok) {
+        info->route = try_chol ? ASOLVE_ROUTE_CHOL : (chol ? ASOLVE_ROUTE_CHOL_FAIL_LU : ASOLVE_ROUTE_LU);
+        info->rcond = rcv;
+        info->berr = berr;
+        info->ir_iters = iters;
+        info->precision = ASOLVE_PREC_MIXED;
+        info->detail = detail;
+        return info->status = ASOLVE_OK;
+      }
+      detail |= 2;
+      break;
+    }
+  }
+  // ---- FP64 path
+  if ((rc = set_large_attrs<double>())) return rc;
+  Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0};
+  info->precision = ASOLVE_PREC_FP64;
+  info->detail = detail;
+  bool lu = !chol;
+  int fcol = 0;
+  if (chol) {
+    k_to_work<double><<<a.num_sms * 4, 256, 0, st>>>(a.A, n, f.W, ldw);
+    if ((rc = chol_large<double>(f, n, a.num_sms, &fcol, st))) return rc;
+    if (fcol) {  // not sympd after all (Sec. 2.3): the general solver
+      lu = true;
+      info->route = ASOLVE_ROUTE_CHOL_FAIL_LU;
+    }
+  }
+  if (lu) {
+    k_to_work<double><<<a.num_sms * 4, 256, 0, st>>>(a.A, n, f.W, ldw);
+    fcol = 0;
+    if ((rc = lu_large<double>(f, n, a.num_sms, &fcol, st))) return rc;
+  }
+  if (fcol) {
+    LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
+    LCK(cudaStreamSynchronize(st));
+    return info->status = ASOLVE_E_SINGULAR;  // the SVD fallback is limited to n <= 1024
+  }
+  LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+  if ((rc = apply_large<double, double>(f, lu, n, a.X, nrhs, false, (double*)tmp, st))) return rc;
+  double rcv = NAN;
+  if (!no_rcond) {
+    double est;
+    auto apply = [&](double* v, bool tr) { return apply_large<double, double>(f, lu, n, v, 1, tr, (double*)tmp, st); };
+    if ((rc = est_large<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est))) return rc;
+    rcv = rcond_of(sr.norm1, est);
+  }
+  info->rcond = rcv;
+  if (a.flags & ASOLVE_BERR) {
+    LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+    std::vector<unsigned long long> hm((size_t)3 * nrhs);
+    LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    double be = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      double rm, xm, bm;
+      memcpy(&rm, &hm[c], 8);
+      memcpy(&xm, &hm[nrhs + c], 8);
+      memcpy(&bm, &hm[2 * nrhs + c], 8);
+      const double den = sr.norminf * xm + bm;
+      const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+      if (!(b1 <= be)) be = b1;
+    }
+    info->berr = be;
+  }
+  LCK(cudaStreamSynchronize(st));
+  const bool poor = !no_rcond && !(rcv >= a.rcond_threshold);
+  return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
+}
+
+}  // namespace asv
