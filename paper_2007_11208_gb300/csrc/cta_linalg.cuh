@@ -225,12 +225,38 @@ __device__ __noinline__ void cta_lu_update(T* W, int ldw, int n, int k0, int kb,
     }
     __syncthreads();
     // U tile = inv(L11) A12 tile
-    for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
-      const int c = e & 63, i = e >> 6;
-      T acc = T(0);
+    if constexpr (sizeof(T) == 8) {
+      // FP64: 32 x 64 x 32 on mma.sync f64; warp w owns row tile (w & 3)
+      // and column tiles 4 (w >> 2) .. 4 (w >> 2) + 3
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      const int g = lane >> 2, t = lane & 3;
+      const int ri = (w & 3) * 8;
+      double acc[4][2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q][0] = acc[q][1] = 0.0;
+#pragma unroll
+      for (int k = 0; k < 32; k += 4) {
+        const double a = Li[(k + t) * 33 + ri + g];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int cj = ((w >> 2) * 4 + q) * 8;
+          dmma_8x8x4(acc[q][0], acc[q][1], a, Ta[(k + t) * 65 + cj + g]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int cj = ((w >> 2) * 4 + q) * 8;
+        Tu[(ri + g) * 64 + cj + 2 * t] = acc[q][0];
+        Tu[(ri + g) * 64 + cj + 2 * t + 1] = acc[q][1];
+      }
+    } else {
+      for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {
+        const int c = e & 63, i = e >> 6;
+        T acc = T(0);
 #pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc += Li[k * 33 + i] * Ta[k * 65 + c];
-      Tu[i * 64 + c] = acc;
+        for (int k = 0; k < 32; ++k) acc += Li[k * 33 + i] * Ta[k * 65 + c];
+        Tu[i * 64 + c] = acc;
+      }
     }
     __syncthreads();
     for (int e = threadIdx.x; e < 32 * 64; e += kThreads) {

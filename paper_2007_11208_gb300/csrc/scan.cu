@@ -18,8 +18,8 @@
 // dominance predicates fall back to FP64 only for pairs an integer test
 // cannot decide (unequal bit patterns, or exponents too close); the norms
 // are summed from bit-truncated FP32 magnitudes in 32-element partials
-// (relative error below 2^-18) and combined in FP64 in a fixed order, so
-// the result does not depend on scheduling.  A is read once, tile pair by
+// (relative error below 2^-18), which are combined with a compensated FP32
+// sum in a fixed order, so the result does not depend on scheduling.  A is read once, tile pair by
 // tile pair: tile (P,Q) is staged through shared memory and its mirror
 // (Q,P) is read row-wise straight from global memory, which puts every
 // element next to its transpose partner.
@@ -215,19 +215,29 @@ __device__ void scan_diag(const double* __restrict__ A, int n, double* diag, Sca
   __syncthreads();
 }
 
+// Compensated (Kahan) FP32 sum of the T partials of column/row j: the FP64
+// pipe is far too slow on this part to spend one FP64 add per partial.
+__device__ __forceinline__ float kahan_partials(const float* part, int n, int T, int j) {
+  float s = 0.f, c = 0.f;
+  for (int R = 0; R < T; ++R) {
+    const float y = part[(size_t)R * n + j] - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  return s;
+}
+
 // ||A||_1 and ||A||_inf from the partials (fixed summation order).
 __device__ void reduce_norms(const float* colpart, const float* rowpart, int n, int T,
                              double& norm1, double& norminf, ScanShared& sh) {
-  double c1 = 0.0, ci = 0.0;
+  float c1f = 0.f, cif = 0.f;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double s = 0.0, r = 0.0;
-    for (int R = 0; R < T; ++R) {
-      s += (double)colpart[(size_t)R * n + j];
-      r += (double)rowpart[(size_t)R * n + j];
-    }
-    c1 = s > c1 ? s : c1;
-    ci = r > ci ? r : ci;
+    const float s = kahan_partials(colpart, n, T, j), r = kahan_partials(rowpart, n, T, j);
+    c1f = s > c1f ? s : c1f;
+    cif = r > cif ? r : cif;
   }
+  double c1 = (double)c1f, ci = (double)cif;
   c1 = warp_max(c1);
   ci = warp_max(ci);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -388,7 +398,7 @@ __global__ void __launch_bounds__(kScanThreads, 2) k_scan_batched(const BatchDes
       }
       continue;
     }
-    cta_scan_system(d.A + d.a_off[s], n, d.B + d.b_off[s], (int64_t)n * nr, scratch,
+    cta_scan_system(sys_A(d, s), n, sys_B(d, s), (int64_t)n * nr, scratch,
                     d.sympd_tol, d.band_frac, diag, sh, out);
   }
 }
@@ -455,16 +465,13 @@ __global__ void __launch_bounds__(1024) k_scan_large_final(const double* __restr
   __shared__ double red[32];
   const int n = (int)n64;
   const int T = (n + 31) / 32;
-  double c1 = 0.0, ci = 0.0;
+  float c1f = 0.f, cif = 0.f;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double s = 0.0, r = 0.0;
-    for (int R = 0; R < T; ++R) {
-      s += (double)colpart[(size_t)R * n + j];
-      r += (double)rowpart[(size_t)R * n + j];
-    }
-    c1 = s > c1 ? s : c1;
-    ci = r > ci ? r : ci;
+    const float s = kahan_partials(colpart, n, T, j), r = kahan_partials(rowpart, n, T, j);
+    c1f = s > c1f ? s : c1f;
+    cif = r > cif ? r : cif;
   }
+  double c1 = (double)c1f, ci = (double)cif;
   bool bbad = false;
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x)
     if (is_nonfinite_bits(dbits(B[i]))) bbad = true;
