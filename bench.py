@@ -15,12 +15,25 @@ is timed beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) each rank solves its own batch (weak scaling).
+
+Two more workloads print their own JSON line (not the headline):
+  --workload large   single dense systems n in --sizes (default 8192,16384),
+                     general U diag(logspace(0,-k)) V^T and SPD with kappa in
+                     {1e2, 1e4, 1e6}, nrhs in {1, 64}: mixed precision
+                     (FP32 factors on tcgen05, FP64 refinement) vs the FP64
+                     path, time per solve with CUDA events.
+  --workload serve   request server: Poisson arrivals of FP64 requests in
+                     host memory, n log-uniform in [32, 8192], the batched
+                     class mix, kappa log-uniform in [1e1, 1e12], HBM budget
+                     120 GB; capacity at saturation, then p50/p99 latency at
+                     fractions of it.
 """
 from __future__ import annotations
 
 import argparse
 import ctypes as C
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -408,6 +421,193 @@ def reference(args):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+# --------------------------------------------------------------- large dense
+def large_workload(args):
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in args.sizes.split(",")]
+    kappas = [1e2, 1e4, 1e6]
+    ctxs = {p: asolve.Context(precision=p) for p in (asolve.PREC_MIXED, asolve.PREC_FP64)}
+    cases = []
+    with ClockSampler(0) as clk:
+        for n in sizes:
+            for kind in ("general", "spd"):
+                for kappa in kappas:
+                    g = synth.gen(int(n + 17 * kappa) % 100003, dev)
+                    A = synth.spectrum_fast(n, g, kappa, spd=(kind == "spd"), device=dev)
+                    B64 = synth.rhs(n, 64, g, dev)
+                    for nrhs in (1, 64):
+                        B = B64[:nrhs].contiguous()
+                        X = torch.zeros_like(B)
+                        row = {"n": n, "kind": kind, "kappa": kappa, "nrhs": nrhs}
+                        for p, name in ((asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64")):
+                            c = ctxs[p]
+                            st = torch.cuda.ExternalStream(c.stream)
+                            rc, info = c.solve(A, B, n, nrhs, X, asolve.BERR)  # warm-up (workspace)
+                            times = []
+                            for _ in range(args.steps):
+                                e0 = torch.cuda.Event(enable_timing=True)
+                                e1 = torch.cuda.Event(enable_timing=True)
+                                torch.cuda.synchronize()
+                                e0.record(st)
+                                rc, info = c.solve(A, B, n, nrhs, X, asolve.BERR)
+                                e1.record(st)
+                                torch.cuda.synchronize()
+                                times.append(e0.elapsed_time(e1))
+                            ms = statistics.median(times)
+                            row[name] = {"ms": ms, "rc": rc, "route": info["route"],
+                                         "precision": info["precision"], "ir_iters": info["ir_iters"],
+                                         "berr": info["berr"], "rcond": info["rcond"],
+                                         "detail": info["detail"],
+                                         "flops_per_s": (2.0 / 3.0 if kind == "general" else 1.0 / 3.0)
+                                         * n ** 3 / (ms * 1e-3)}
+                            log(n, kind, f"{kappa:.0e}", nrhs, name, f"{ms:.2f} ms", info["route"],
+                                info["precision"], info["ir_iters"], f"{info['berr']:.2e}")
+                        row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+                        cases.append(row)
+                    del A, B64
+                    torch.cuda.empty_cache()
+    for c in ctxs.values():
+        c.close()
+    head = [c for c in cases if c["n"] == sizes[-1] and c["kind"] == "general" and c["kappa"] == 1e4
+            and c["nrhs"] == 1]
+    head = head[0] if head else cases[-1]
+    ok = head["mixed"]["rc"] == 0 and head["mixed"]["berr"] <= BERR_BAR
+    print(json.dumps({
+        "metric": "solves/s at backward err <=1e-13 (single large dense system)",
+        "value": (1000.0 / head["mixed"]["ms"]) if ok else 0.0, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": head["mixed"]["ms"],
+        "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None,
+        "dtype": "f64 (FP32 factors on tcgen05 3xTF32 + FP64 refinement)", "data": "synthetic",
+        "config": {"workload": f"large-dense: general U diag(logspace(0,-4)) V^T, n={head['n']}, nrhs=1",
+                   "l2": "inputs larger than L2"},
+        "fp64_path_ms": head["fp64"]["ms"], "speedup_vs_fp64_path": head["speedup"],
+        "clocks": clk.summary(), "cases": cases}), flush=True)
+
+
+# --------------------------------------------------------------- serving
+def _serve_templates(count, seed, dev, nmin=32, nmax=8192):
+    """Request templates: n log-uniform, batched class mix, kappa log-uniform."""
+    from paper_2007_11208_gb300 import synth
+    g = synth.gen(seed, dev)
+    gc = synth.gen(seed)
+    out = []
+    for t in range(count):
+        u = torch.rand(4, generator=gc, dtype=torch.float64).tolist()
+        n = int(round(math.exp(math.log(nmin) + u[0] * (math.log(nmax) - math.log(nmin)))))
+        kappa = 10.0 ** (1.0 + 11.0 * u[1])
+        nrhs = 1 + int(u[2] * 8) % 8
+        if u[3] < 0.45:
+            kind, M = "general", synth.spectrum_fast(n, g, kappa, device=dev)
+        elif u[3] < 0.70:
+            kind, M = "spd", synth.spectrum_fast(n, g, kappa, spd=True, device=dev)
+        elif u[3] < 0.85:
+            kl = 1 + int(u[0] * 1e6) % 16
+            ku = 1 + int(u[1] * 1e6) % 16
+            kind, M = "banded", synth.banded_kappa(n, kl, ku, g, kappa, device=dev)
+        else:
+            lower = int(u[2] * 1e6) % 2 == 0
+            kind, M = "tri", synth.tri_kappa(n, g, kappa, lower=lower, device=dev)
+        B = synth.rhs(n, nrhs, g, dev)
+        out.append({"kind": kind, "n": n, "nrhs": nrhs, "kappa": kappa,
+                    "A": M.cpu().pin_memory(), "B": B.cpu().pin_memory()})
+        del M, B
+    torch.cuda.empty_cache()
+    return out
+
+
+def serve_workload(args):
+    from paper_2007_11208_gb300 import asolve, build
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    tm = _serve_templates(args.templates, SEED + 5, dev)
+    log(f"{len(tm)} templates in {time.perf_counter() - t0:.1f}s; "
+        f"host bytes {sum(t['A'].numel() for t in tm) * 8 / 1e9:.2f} GB; "
+        f"n: {sorted(t['n'] for t in tm)}")
+    rng = np.random.default_rng(SEED + 6)
+    R = args.requests
+    pick = rng.integers(0, len(tm), size=R)
+    Xs = [torch.zeros_like(tm[k]["B"]).pin_memory() for k in pick]
+    flags = asolve.HOST_BUFFERS | asolve.BERR
+    ctx = asolve.Context(hbm_budget=120 << 30)
+    # warm the server (graphs, pools, workspaces) on every template once
+    for k in range(len(tm)):
+        t = tm[k]
+        Xw = torch.zeros_like(t["B"])
+        rc, tk = ctx.submit(t["A"].data_ptr(), t["B"].data_ptr(), t["n"], t["nrhs"], Xw.data_ptr(), flags)
+        assert rc == 0
+        ctx.poll(tk, -1)
+
+    def run(rate):
+        """Submit R requests with exponential gaps (rate <= 0: all at once)."""
+        gaps = rng.exponential(1.0 / rate, size=R) if rate > 0 else np.zeros(R)
+        before = ctx.serve_stats()
+        tickets = []
+        tstart = time.perf_counter()
+        due = tstart
+        for i, k in enumerate(pick):
+            due += gaps[i]
+            d = due - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            t = tm[k]
+            rc, tk = ctx.submit(t["A"].data_ptr(), t["B"].data_ptr(), t["n"], t["nrhs"],
+                                Xs[i].data_ptr(), flags)
+            assert rc == 0, rc
+            tickets.append(tk)
+        lat, ok, infos = [], 0, []
+        for tk in tickets:
+            st, info, l = ctx.poll(tk, -1)
+            lat.append(l)
+            infos.append(info)
+            if st == 0 and info["berr"] <= BERR_BAR:
+                ok += 1
+        after = ctx.serve_stats()
+        wall = time.perf_counter() - tstart
+        busy = after["busy_ms"] - before["busy_ms"]
+        lat = np.array(lat)
+        return {"rate": rate, "requests": R, "wall_s": wall, "solves_per_s": ok / wall,
+                "completed_per_s": R / wall, "verified": ok,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "busy_frac": busy / (wall * 1e3),
+                "rounds": after["rounds"] - before["rounds"],
+                "batches": after["batches"] - before["batches"],
+                "large": after["large_solves"] - before["large_solves"],
+                "peak_charged_gb": after["peak_charged_bytes"] / 1e9}
+
+    points = []
+    with ClockSampler(0) as clk:
+        sat = run(0.0)
+        log("saturation", sat)
+        points.append(sat)
+        cap = sat["completed_per_s"]
+        for f in [float(x) for x in args.load.split(",")]:
+            p = run(f * cap)
+            p["load"] = f
+            log("load", f, p)
+            points.append(p)
+    ctx.close()
+    h2d = sum(8 * (tm[k]["n"] ** 2 + tm[k]["n"] * tm[k]["nrhs"]) for k in pick)
+    d2h = sum(8 * tm[k]["n"] * tm[k]["nrhs"] for k in pick)
+    print(json.dumps({
+        "metric": "solves/s at backward err <=1e-13 (request server, saturated)",
+        "value": sat["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": sat["wall_s"] * 1e3, "higher_is_better": True, "scaling": "replicas only",
+        "vs_baseline": None, "dtype": "f64 (mixed: FP32 factors + FP64 refinement)",
+        "data": "synthetic",
+        "config": {"workload": f"serve: {R} requests from {len(tm)} templates, n log-uniform [32,8192], "
+                               "batched class mix, kappa log-uniform [1e1,1e12], host FP64 in/out, "
+                               "HBM budget 120 GB"},
+        "e2e": {"value": sat["solves_per_s"], "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"], "busy_frac": sat["busy_frac"],
+        "clocks": clk.summary(), "points": points}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,10 +618,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per GPU (smaller values are for profiling runs only)")
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve"])
+    ap.add_argument("--sizes", default="8192,16384", help="large: matrix sizes")
+    ap.add_argument("--templates", type=int, default=40, help="serve: distinct request matrices")
+    ap.add_argument("--requests", type=int, default=160, help="serve: requests per load point")
+    ap.add_argument("--load", default="0.25,0.5,0.8", help="serve: arrival rates as fractions of capacity")
     ap.add_argument("--quick", action="store_true",
                     help="headline arm only (no FP64 comparator, profile, e2e or CPU baseline)")
     args = ap.parse_args()
     globals()["COUNT"] = args.count
+    if args.workload == "large":
+        return large_workload(args)
+    if args.workload == "serve":
+        return serve_workload(args)
     if args.impl == "reference":
         reference(args)
     else:

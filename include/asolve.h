@@ -131,6 +131,22 @@ typedef struct {           /* per-kernel CUDA-event timing, enabled by asolve_se
   } k[24];
 } asolve_profile;
 
+typedef struct {           /* request-server counters (asolve_get_serve_stats) */
+  int64_t submitted;       /* requests accepted (tickets issued) */
+  int64_t completed;       /* requests finished, any status */
+  int64_t failed;          /* finished with an error status (< 0) */
+  int64_t rejected;        /* refused at submission: alone over the HBM budget */
+  int64_t queued;          /* waiting for admission now */
+  int64_t rounds;          /* server rounds run */
+  int64_t batches;         /* batched launches of small requests */
+  int64_t large_solves;    /* large systems solved */
+  size_t  budget;          /* the context's hbm_budget */
+  size_t  charged_bytes;   /* bytes admitted and not yet released */
+  size_t  peak_charged_bytes;
+  double  busy_ms;         /* host wall time the server spent inside rounds */
+  double  wall_ms;         /* first submission to last completion */
+} asolve_serve_stats;
+
 /* Version string of this library. */
 const char* asolve_version(void);
 /* Text for a status code. */
@@ -181,6 +197,49 @@ int asolve_solve_batched(asolve_ctx* ctx, int64_t count, const int64_t* n,
                          const int64_t* nrhs, const int64_t* a_off,
                          const int64_t* b_off, const double* A, const double* B,
                          double* X, uint32_t flags, asolve_info* infos);
+
+/* Batched adaptive solve over per-system pointers (the paper has no batched
+ * call; this is asolve_solve applied to `count` independent systems, Sec. 2
+ * per system): system s solves A[s] X[s] = B[s] with A[s] n[s] x n[s] and
+ * B[s], X[s] n[s] x nrhs[s], all column-major with ld = n[s], n[s] <= 1024,
+ * nrhs[s] <= 8.  n, nrhs, A, B, X (arrays of device pointers) and infos are
+ * DEVICE arrays; every matrix pointer must be 8-byte aligned.  Otherwise as
+ * asolve_solve_batched (ASOLVE_HOST_BUFFERS is not accepted here). */
+int asolve_solve_batched_ptrs(asolve_ctx* ctx, int64_t count, const int64_t* n,
+                              const int64_t* nrhs, const double* const* A,
+                              const double* const* B, double* const* X, uint32_t flags,
+                              asolve_info* infos);
+
+/* Request server with continuous batching (the paper has no counterpart:
+ * it serves many asolve_solve calls, Sec. 2 per request, from one context).
+ * asolve_submit queues one request and returns at once with a ticket; a
+ * server thread, started by the first submission, admits queued requests in
+ * arrival order while the device bytes they hold fit cfg.hbm_budget, solves
+ * the admitted small ones (n <= 1024, nrhs <= 8, same solver flags) as one
+ * class-routed batch and at most one larger one per round, and records each
+ * result.  A, B, X: device pointers, or host pointers with
+ * ASOLVE_HOST_BUFFERS (the server stages them in device memory it charges
+ * to the budget); they must stay valid, and A and B unchanged, until the
+ * request completes.  Allowed flags: NO_APPROX, FORCE_LU, FORCE_SVD,
+ * NO_RCOND, BERR, HOST_BUFFERS.  Errors: E_INVALID, E_UNSUPPORTED
+ * (n > 32768 or nrhs > 256), E_NOMEM (the request alone needs more than the
+ * budget; no ticket is issued), E_CUDA.  n = 0 completes at once.
+ * The server runs on its own stream and workspaces: synchronous calls on the
+ * same context may run meanwhile.  asolve_destroy waits for every submitted
+ * request to complete. */
+int asolve_submit(asolve_ctx* ctx, const double* A, const double* B, int64_t n, int64_t nrhs,
+                  uint32_t flags, double* X, uint64_t* ticket);
+/* Wait up to wait_us microseconds (< 0: without limit, 0: do not wait) for
+ * a ticket.  Returns ASOLVE_PENDING while the request runs.  Once it has
+ * completed, returns ASOLVE_OK, fills *info (the request's own status is
+ * info->status) and the submission-to-completion latency in milliseconds
+ * (either pointer may be NULL), and forgets the ticket.  An unknown or
+ * already returned ticket: ASOLVE_E_INVALID. */
+int asolve_poll(asolve_ctx* ctx, uint64_t ticket, int64_t wait_us, asolve_info* info,
+                double* latency_ms);
+/* Counters of the context's request server (all zero before the first
+ * submission, except budget). */
+int asolve_get_serve_stats(asolve_ctx* ctx, asolve_serve_stats* out);
 
 /* Property scan that allocates nothing (the paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory --

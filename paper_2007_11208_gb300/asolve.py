@@ -50,6 +50,14 @@ class ScanResult(C.Structure):
                 ("norminf", C.c_double)]
 
 
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("rejected", C.c_int64), ("queued", C.c_int64), ("rounds", C.c_int64),
+                ("batches", C.c_int64), ("large_solves", C.c_int64), ("budget", C.c_size_t),
+                ("charged_bytes", C.c_size_t), ("peak_charged_bytes", C.c_size_t),
+                ("busy_ms", C.c_double), ("wall_ms", C.c_double)]
+
+
 class _ProfEntry(C.Structure):
     _fields_ = [("name", C.c_char * 40), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -68,7 +76,8 @@ EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve
            "asolve_destroy", "asolve_stream", "asolve_scan", "asolve_solve",
            "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
            "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc",
-           "asolve_gemm_sub")
+           "asolve_gemm_sub", "asolve_solve_batched_ptrs", "asolve_submit", "asolve_poll",
+           "asolve_get_serve_stats")
 
 
 def lib():
@@ -98,6 +107,10 @@ def lib():
     L.asolve_reset_profile.argtypes = [vp]
     L.asolve_scan_noalloc.argtypes = [vp, i64, vp, vp]
     L.asolve_gemm_sub.argtypes = [vp, i64, vp, i64, vp, i64, i64, i64, i64, i32, vp, vp]
+    L.asolve_solve_batched_ptrs.argtypes = [vp, i64, vp, vp, vp, vp, vp, u32, vp]
+    L.asolve_submit.argtypes = [vp, vp, vp, i64, i64, u32, vp, P(C.c_uint64)]
+    L.asolve_poll.argtypes = [vp, C.c_uint64, i64, P(Info), P(C.c_double)]
+    L.asolve_get_serve_stats.argtypes = [vp, P(ServeStats)]
     for f in EXPORTS:
         if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
             getattr(L, f).restype = i32
@@ -189,6 +202,32 @@ class Context:
         return lib().asolve_solve_batched(self._h, count, _ptr(n), _ptr(nrhs), _ptr(a_off),
                                           _ptr(b_off), _ptr(A), _ptr(B), _ptr(X), flags,
                                           _ptr(infos))
+
+    def solve_batched_ptrs(self, count, n, nrhs, A_ptrs, B_ptrs, X_ptrs, infos, flags: int = 0) -> int:
+        """n, nrhs: int64 device tensors; *_ptrs: int64 device tensors of addresses."""
+        return lib().asolve_solve_batched_ptrs(self._h, count, _ptr(n), _ptr(nrhs), _ptr(A_ptrs),
+                                               _ptr(B_ptrs), _ptr(X_ptrs), flags, _ptr(infos))
+
+    def submit(self, A, B, n: int, nrhs: int, X, flags: int = 0):
+        """Queue one request; returns (rc, ticket).  The buffers must outlive it."""
+        t = C.c_uint64(0)
+        rc = lib().asolve_submit(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket: int, wait_us: int = -1):
+        """Returns (status, info dict, latency_ms) once the request completed
+        (status = info["status"]), else (PENDING or E_INVALID, None, None)."""
+        inf = Info()
+        lat = C.c_double(0.0)
+        rc = lib().asolve_poll(self._h, ticket, wait_us, C.byref(inf), C.byref(lat))
+        if rc != OK:
+            return rc, None, None
+        return inf.status, info_dict(inf), lat.value
+
+    def serve_stats(self) -> dict:
+        st = ServeStats()
+        lib().asolve_get_serve_stats(self._h, C.byref(st))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
 
     def set_profiling(self, on: bool):
         lib().asolve_set_profiling(self._h, int(on))

@@ -43,6 +43,7 @@ struct LargeArgs {
 };
 size_t large_ws_bytes(int64_t n, int64_t nrhs);
 int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
+void serve_shutdown(asolve_ctx* c);
 }  // namespace asv
 
 using namespace asv;
@@ -100,12 +101,22 @@ struct asolve_ctx {
   DevBuf hostA, hostB, hostX, hostMeta;  // device copies for ASOLVE_HOST_BUFFERS
   DevBuf large;        // large-scan workspace
   ScanRes* h_scan = nullptr;  // pinned
+  // request server (created by the first asolve_submit)
+  void* serve = nullptr;
   // profiling
   bool profiling = false;
   cudaEvent_t ev[K_COUNT + 1] = {};
   double prof_ms[K_COUNT] = {};
   int64_t prof_launches[K_COUNT] = {};
 };
+
+namespace asv {
+// Accessors for the request server (serve.cu).
+const asolve_config* ctx_config(asolve_ctx* c) { return &c->cfg; }
+int ctx_device(asolve_ctx* c) { return c->device; }
+int ctx_num_sms(asolve_ctx* c) { return c->num_sms; }
+void** ctx_serve_slot(asolve_ctx* c) { return &c->serve; }
+}  // namespace asv
 
 static int cuda_fail(cudaError_t e) {
   if (e == cudaErrorMemoryAllocation) return ASOLVE_E_NOMEM;
@@ -202,6 +213,7 @@ extern "C" int asolve_create(asolve_ctx** out, const asolve_config* cfg) {
 
 extern "C" int asolve_destroy(asolve_ctx* c) {
   if (!c) return ASOLVE_E_INVALID;
+  serve_shutdown(c);  // waits for every submitted request
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (auto& kv : c->graphs)
@@ -405,6 +417,27 @@ extern "C" int asolve_solve_batched(asolve_ctx* c, int64_t count, const int64_t*
     return ASOLVE_OK;
   }
   fill_desc(c, c->h_desc, count, n, nrhs, a_off, b_off, A, B, X, infos, flags);
+  rc = run_pipeline(c, count);
+  if (rc) return rc;
+  if (flags & ASOLVE_SYNC) CK(cudaStreamSynchronize(c->stream));
+  return ASOLVE_OK;
+}
+
+extern "C" int asolve_solve_batched_ptrs(asolve_ctx* c, int64_t count, const int64_t* n,
+                                         const int64_t* nrhs, const double* const* A,
+                                         const double* const* B, double* const* X, uint32_t flags,
+                                         asolve_info* infos) {
+  if (!c || count < 0) return ASOLVE_E_INVALID;
+  if (count == 0) return ASOLVE_OK;
+  if (!n || !nrhs || !A || !B || !X || !infos) return ASOLVE_E_INVALID;
+  if (flags & ASOLVE_HOST_BUFFERS) return ASOLVE_E_UNSUPPORTED;
+  CK(cudaSetDevice(c->device));
+  int rc = ensure_pipeline(c, count);
+  if (rc) return rc;
+  fill_desc(c, c->h_desc, count, n, nrhs, nullptr, nullptr, nullptr, nullptr, nullptr, infos, flags);
+  c->h_desc->Ap = A;
+  c->h_desc->Bp = B;
+  c->h_desc->Xp = X;
   rc = run_pipeline(c, count);
   if (rc) return rc;
   if (flags & ASOLVE_SYNC) CK(cudaStreamSynchronize(c->stream));

@@ -49,6 +49,11 @@ struct BatchDesc {
   const double* A;
   const double* B;
   double* X;
+  // optional per-system base pointers [count]; when set they replace
+  // A + a_off[s], B + b_off[s] and X + b_off[s]
+  const double* const* Ap;
+  const double* const* Bp;
+  double* const* Xp;
   asolve_info* info;       // [count]
   uint32_t flags;
   int32_t precision;
@@ -69,6 +74,17 @@ struct BatchDesc {
   int32_t pad1;
   int32_t* err_flag;       // device-side error (e.g. a scratch slot too small)
 };
+
+// Column-major A, B and X of system s of a batch.
+__device__ __forceinline__ const double* sys_A(const BatchDesc& d, int64_t s) {
+  return d.Ap ? d.Ap[s] : d.A + d.a_off[s];
+}
+__device__ __forceinline__ const double* sys_B(const BatchDesc& d, int64_t s) {
+  return d.Bp ? d.Bp[s] : d.B + d.b_off[s];
+}
+__device__ __forceinline__ double* sys_X(const BatchDesc& d, int64_t s) {
+  return d.Xp ? d.Xp[s] : d.X + d.b_off[s];
+}
 
 // --------------------------------------------------------------------------
 // Small device helpers.

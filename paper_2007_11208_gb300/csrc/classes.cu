@@ -313,9 +313,9 @@ __device__ double berr_fp64(const double* __restrict__ A, const double* __restri
 template <int KIND>
 __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem, CtaRed& red) {
   const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
-  const double* A = d.A + d.a_off[s];
-  const double* B = d.B + d.b_off[s];
-  double* X = d.X + d.b_off[s];
+  const double* A = sys_A(d, s);
+  const double* B = sys_B(d, s);
+  double* X = sys_X(d, s);
   const ScanRes sr = d.scan[s];
   asolve_info* inf = d.info + s;
   DenseSlot sl = dense_slot(d, n);
@@ -475,9 +475,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
     if (it >= len) break;
     const int64_t s = d.lists[(int64_t)L_TRI * d.capacity + it];
     const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
-    const double* A = d.A + d.a_off[s];
-    const double* B = d.B + d.b_off[s];
-    double* X = d.X + d.b_off[s];
+    const double* A = sys_A(d, s);
+    const double* B = sys_B(d, s);
+    double* X = sys_X(d, s);
     const ScanRes sr = d.scan[s];
     const bool lower = d.info[s].route == ASOLVE_ROUTE_TRI_LOWER;
     DenseSlot sl = dense_slot(d, n);
@@ -731,9 +731,9 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
       double* v = reinterpret_cast<double*>(base + fbytes + (((size_t)n * 4 + 255) & ~(size_t)255));
       double* xi = v + n;
       double* xv = xi + n;
-      const double* A = d.A + d.a_off[s];
-      const double* B = d.B + d.b_off[s];
-      double* X = d.X + d.b_off[s];
+      const double* A = sys_A(d, s);
+      const double* B = sys_B(d, s);
+      double* X = sys_X(d, s);
       // pack (Sec. 2.1 compact storage) with zeroed fill rows
       for (int64_t e = lane; e < (int64_t)b.ldf * n; e += 32) b.F[e] = 0.0;
       __syncwarp();
@@ -898,9 +898,9 @@ __global__ void __cluster_dims__(kSvdCluster, 1, 1) __launch_bounds__(kThreads, 
     if (it >= len) break;
     const int64_t s = d.lists[(int64_t)L_SVD * d.capacity + it];
     const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
-    const double* A = d.A + d.a_off[s];
-    const double* B = d.B + d.b_off[s];
-    double* X = d.X + d.b_off[s];
+    const double* A = sys_A(d, s);
+    const double* B = sys_B(d, s);
+    double* X = sys_X(d, s);
     char* base = d.slot_base + (size_t)leader_block * d.slot_bytes;
     double* G = reinterpret_cast<double*>(base);
     double* V = G + (size_t)n * n;

@@ -904,6 +904,11 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (a.flags & ASOLVE_FORCE_SVD) return info->status = ASOLVE_E_UNSUPPORTED;
   int cls = (a.flags & ASOLVE_FORCE_LU) ? ASOLVE_CLS_GENERAL : sr.cls;
   if (cls == ASOLVE_CLS_BANDED) return info->status = ASOLVE_E_UNSUPPORTED;  // dense input, band route: n <= 1024
+  // dynamic shared memory limits of every kernel below (the triangular
+  // route uses the FP64 kernels even in mixed precision)
+  int arc = set_large_attrs<float>();
+  if (!arc) arc = set_large_attrs<double>();
+  if (arc) return info->status = arc;
   const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
   const int ldw = (n + 3) & ~3;
   double* R = static_cast<double*>(ar.take(sizeof(double) * (size_t)n * nrhs));

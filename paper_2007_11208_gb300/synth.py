@@ -24,6 +24,8 @@ distributions below are the ones the benchmark configurations name):
                Gaussian with sign-corrected R)
   reflector    U, V products of 8 random Householder reflectors and random
                signs (exact spectrum at O(n^2) cost, for large n)
+  tri_kappa    T = D (I + s N), N strictly triangular N(0,1), s = 1/n,
+               D = diag(logspace(0, -log10 kappa))
 """
 from __future__ import annotations
 
@@ -148,6 +150,56 @@ def spectrum_spd(n, g, kappa, device="cpu", orth=reflector_orth):
     U = orth(n, g, device=device)
     s = torch.logspace(0.0, -math.log10(kappa), n, dtype=F64, device=device)
     return colmajor(mirror_lower((U * s[None, :]) @ U.t()))
+
+
+def _signs(n, g, device):
+    return torch.where(torch.rand(n, generator=g, device=device, dtype=F64) < 0.5, -1.0, 1.0)
+
+
+def _unit(n, g, device):
+    v = _randn((n,), g, device)
+    return v / torch.linalg.vector_norm(v)
+
+
+def spectrum_fast(n, g, kappa, spd=False, nref=8, device="cpu"):
+    """U diag(logspace(0, -log10 kappa, n)) V^T (V = U when spd) with U, V
+    products of nref random reflectors and random signs, built by applying
+    the reflectors to the diagonal one at a time: O(nref n^2) work and one
+    n x n buffer, for the largest sizes.  Column-major buffer."""
+    s = torch.logspace(0.0, -math.log10(kappa), n, dtype=F64, device=device)
+    M = torch.diag(s)
+    for _ in range(nref):
+        v = _unit(n, g, device)
+        M.addr_(v, v @ M, alpha=-2.0)          # H M
+        w = v if spd else _unit(n, g, device)
+        M.addr_(M @ w, w, alpha=-2.0)          # M H'
+    d = _signs(n, g, device)
+    e = d if spd else _signs(n, g, device)
+    M.mul_(d[:, None]).mul_(e[None, :])
+    if spd:
+        M = mirror_lower(M)
+    return colmajor(M)
+
+
+def tri_kappa(n, g, kappa, lower=True, device="cpu"):
+    """T = D (I + s N), N strictly triangular N(0,1), s = 1/n, D =
+    diag(logspace(0, -log10 kappa, n)) in random order of rows."""
+    N = _randn((n, n), g, device)
+    N = torch.tril(N, -1) if lower else torch.triu(N, 1)
+    T = N.mul_(1.0 / n)
+    T.diagonal().add_(1.0)
+    dd = torch.logspace(0.0, -math.log10(kappa), n, dtype=F64, device=device)
+    dd = dd[torch.randperm(n, generator=g, device=device)]
+    return colmajor(T * dd[:, None])
+
+
+def banded_kappa(n, kl, ku, g, kappa, device="cpu"):
+    """Diagonally dominant band matrix with rows scaled by
+    logspace(0, -log10 kappa) in random order (same band, kappa grown)."""
+    A = colmajor_to_dense(banded_dd(n, kl, ku, g, device))
+    dd = torch.logspace(0.0, -math.log10(kappa), n, dtype=F64, device=device)
+    dd = dd[torch.randperm(n, generator=g, device=device)]
+    return colmajor(A * dd[:, None])
 
 
 def rhs(n, nrhs, g, device="cpu"):

@@ -1,0 +1,266 @@
+"""GPU tests of the request server (asolve_submit / asolve_poll).
+
+The server must not change any answer: each request served in a mix of
+classes, sizes and storage modes gives the same X (bit for bit) and the same
+info as the same system solved alone with asolve_solve, and the routes agree
+with the oracle.  Admission under a small HBM budget, ticket bookkeeping,
+flag grouping and concurrent producers are checked too.
+"""
+import threading
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import dev_colmajor, dev_rhs, host_from_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _mat(kind, n, rng):
+    if kind == "general":
+        return rng.standard_normal((n, n)) + 2 * np.sqrt(n) * np.eye(n)
+    if kind == "spd":
+        G = rng.standard_normal((n, n))
+        S = G.T @ G / n + np.eye(n)
+        return np.tril(S) + np.tril(S, -1).T
+    if kind == "lower":
+        A = np.tril(rng.standard_normal((n, n)), -1)
+        return A + np.diag(1 + np.abs(A).sum(1))
+    if kind == "upper":
+        A = np.triu(rng.standard_normal((n, n)), 1)
+        return A + np.diag(1 + np.abs(A).sum(1))
+    if kind == "band":
+        A = np.zeros((n, n))
+        for d in range(-3, 4):
+            A += np.diag(rng.standard_normal(n - abs(d)), d)
+        return A + np.diag(1 + np.abs(A).sum(1))
+    raise ValueError(kind)
+
+
+KINDS = ["general", "spd", "lower", "upper", "band"]
+# small (batched) and large (blocked whole-GPU) requests
+SPECS = [(k, n, r) for n, r in [(5, 1), (33, 2), (100, 3), (257, 8), (700, 1), (1024, 4)]
+         for k in KINDS] + [("general", 1100, 1), ("spd", 1300, 2), ("lower", 1111, 1),
+                            ("general", 200, 9)]
+
+
+@pytest.fixture(scope="module")
+def lib_ready():
+    from paper_2007_11208_gb300 import build
+    build.build()
+
+
+def _requests(seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for kind, n, r in SPECS:
+        A = _mat(kind, n, rng)
+        B = rng.standard_normal((n, r))
+        out.append((kind, A, B))
+    return out
+
+
+def _alone(ctx, A, B, flags=0):
+    n = A.shape[0]
+    dA = dev_colmajor(A)
+    dB, r = dev_rhs(B, n)
+    dX = torch.zeros_like(dB)
+    rc, info = ctx.solve(dA, dB, n, r, dX, flags)
+    return rc, info, host_from_dev(dX, n, r)
+
+
+KEYS = ("cls", "route", "status", "ir_iters", "kl", "ku", "rcond", "berr", "svd_rank", "precision",
+        "detail")
+
+
+def _same_info(a, b):
+    for k in KEYS:
+        x, y = a[k], b[k]
+        if isinstance(x, float) and np.isnan(x):
+            assert np.isnan(y), k
+        else:
+            assert x == y, (k, x, y)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_mix_equals_alone(lib_ready, orc, prec):
+    from paper_2007_11208_gb300 import asolve
+    p = asolve.PREC_MIXED if prec == "mixed" else asolve.PREC_FP64
+    reqs = _requests(11)
+    with_alone = asolve.Context(precision=p)
+    alone = [_alone(with_alone, A, B) for _, A, B in reqs]
+    with_alone.close()
+    assert all(a[0] >= 0 for a in alone), [(r[0], r[1].shape[0], a[0]) for r, a in zip(reqs, alone)]
+
+    ctx = asolve.Context(precision=p)
+    bufs, tickets = [], []
+    for i, (_, A, B) in enumerate(reqs):
+        n = A.shape[0]
+        dA = dev_colmajor(A)
+        dB, r = dev_rhs(B, n)
+        dX = torch.full_like(dB, np.nan)
+        bufs.append((dA, dB, dX, n, r))
+    torch.cuda.synchronize()
+    for dA, dB, dX, n, r in bufs:
+        rc, t = ctx.submit(dA, dB, n, r, dX)
+        assert rc == asolve.OK
+        tickets.append(t)
+    for i, t in enumerate(tickets):
+        rc, info, lat = ctx.poll(t, -1)
+        rc0, info0, X0 = alone[i]
+        assert rc == rc0 and info["status"] == rc
+        _same_info(info, info0)
+        assert lat is not None and lat >= 0.0
+        dA, dB, dX, n, r = bufs[i]
+        X = host_from_dev(dX, n, r)
+        assert np.array_equal(X, X0), (reqs[i][0], n)
+        # the route the paper's detection order gives
+        _, io = orc.solve(reqs[i][1], reqs[i][2])
+        assert (info["cls"], info["kl"], info["ku"]) == (io["cls"], io["kl"], io["ku"])
+        assert info["route"] == io["route"], (reqs[i][0], n, info["route"], io["route"])
+    st = ctx.serve_stats()
+    assert st["submitted"] == len(reqs) and st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["large_solves"] == 4
+    assert st["charged_bytes"] == 0 and st["queued"] == 0
+    ctx.close()
+
+
+def test_host_buffers_and_device_mixed(lib_ready):
+    from paper_2007_11208_gb300 import asolve
+    reqs = _requests(12)[::3]
+    ctx = asolve.Context()
+    alone = [_alone(ctx, A, B) for _, A, B in reqs]
+    keep, tickets = [], []
+    for i, (_, A, B) in enumerate(reqs):
+        n, r = A.shape[0], B.shape[1]
+        if i % 2:
+            hA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+            hB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+            hX = torch.zeros((r, n), dtype=torch.float64).pin_memory()
+            rc, t = ctx.submit(hA.data_ptr(), hB.data_ptr(), n, r, hX.data_ptr(), asolve.HOST_BUFFERS)
+            keep.append(("host", hA, hB, hX, n, r))
+        else:
+            dA = dev_colmajor(A)
+            dB, _ = dev_rhs(B, n)
+            dX = torch.zeros_like(dB)
+            torch.cuda.synchronize()
+            rc, t = ctx.submit(dA, dB, n, r, dX)
+            keep.append(("dev", dA, dB, dX, n, r))
+        assert rc == asolve.OK
+        tickets.append(t)
+    for i, t in enumerate(tickets):
+        rc, info, _ = ctx.poll(t, -1)
+        rc0, info0, X0 = alone[i]
+        assert rc == rc0
+        _same_info(info, info0)
+        mode, _, _, Xb, n, r = keep[i]
+        X = Xb.numpy().reshape(r, n).T if mode == "host" else host_from_dev(Xb, n, r)
+        assert np.array_equal(X, X0)
+    ctx.close()
+
+
+def test_budget_admission(lib_ready):
+    """A budget that holds about two staged small requests: every request
+    still completes, in rounds that never hold more than the budget; one
+    that alone exceeds the budget is refused at submission."""
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(5)
+    n, r = 200, 2
+    per = 8 * (n * n + 2 * n * r) + 4096
+    ctx = asolve.Context(hbm_budget=2 * per + 1000)
+    mats = [_mat(KINDS[i % 5], n, rng) for i in range(9)]
+    rhs = [rng.standard_normal((n, r)) for _ in range(9)]
+    alone = [_alone(ctx, A, B) for A, B in zip(mats, rhs)]
+    host = []
+    tickets = []
+    for A, B in zip(mats, rhs):
+        hA = torch.from_numpy(np.ascontiguousarray(A.T))
+        hB = torch.from_numpy(np.ascontiguousarray(B.T))
+        hX = torch.zeros((r, n), dtype=torch.float64)
+        host.append((hA, hB, hX))
+        rc, t = ctx.submit(hA.data_ptr(), hB.data_ptr(), n, r, hX.data_ptr(), asolve.HOST_BUFFERS)
+        assert rc == asolve.OK
+        tickets.append(t)
+    big = torch.zeros(1024 * 1024, dtype=torch.float64)
+    rc, _ = ctx.submit(big.data_ptr(), big.data_ptr(), 1024, 1, big.data_ptr(), asolve.HOST_BUFFERS)
+    assert rc == asolve.E_NOMEM
+    for i, t in enumerate(tickets):
+        rc, info, _ = ctx.poll(t, -1)
+        assert rc == alone[i][0]
+        assert np.array_equal(host[i][2].numpy().reshape(r, n).T, alone[i][2])
+    st = ctx.serve_stats()
+    assert st["rejected"] == 1 and st["completed"] == 9
+    assert st["peak_charged_bytes"] <= st["budget"]
+    assert st["rounds"] >= 5  # at most two requests fit a round
+    ctx.close()
+
+
+def test_tickets_and_flags(lib_ready):
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(9)
+    ctx = asolve.Context()
+    rc, info, _ = ctx.poll(12345, 0)
+    assert rc == asolve.E_INVALID  # no server yet
+    A = _mat("general", 64, rng)
+    B = rng.standard_normal((64, 1))
+    dA, dB = dev_colmajor(A), dev_rhs(B, 64)[0]
+    X1, X2 = torch.zeros_like(dB), torch.zeros_like(dB)
+    torch.cuda.synchronize()
+    # different solver flags go to different batches; FORCE_SVD solves by SVD
+    rc1, t1 = ctx.submit(dA, dB, 64, 1, X1)
+    rc2, t2 = ctx.submit(dA, dB, 64, 1, X2, asolve.FORCE_SVD)
+    rc0, t0 = ctx.submit(None, None, 0, 1, None)
+    assert rc1 == rc2 == rc0 == asolve.OK
+    assert ctx.submit(dA, dB, -1, 1, X1)[0] == asolve.E_INVALID
+    assert ctx.submit(dA, dB, 40000, 1, X1)[0] == asolve.E_UNSUPPORTED
+    assert ctx.submit(dA, dB, 64, 1, X1, 0x10000)[0] == asolve.E_INVALID
+    assert ctx.poll(t0, 0)[0] == asolve.OK
+    r1, i1, _ = ctx.poll(t1, -1)
+    r2, i2, _ = ctx.poll(t2, -1)
+    assert r1 == asolve.OK and i1["route"] == asolve.ROUTE_LU
+    assert r2 == asolve.W_APPROX and i2["route"] == asolve.ROUTE_SVD
+    x1, x2 = X1.cpu().numpy(), X2.cpu().numpy()
+    assert np.abs(x1 - x2).max() <= 1e-10 * np.abs(x1).max()
+    assert ctx.poll(t1, 0)[0] == asolve.E_INVALID  # forgotten after its result
+    ctx.close()
+
+
+def test_concurrent_producers(lib_ready):
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(21)
+    ctx = asolve.Context()
+    items = []
+    for i in range(48):
+        n = int(rng.integers(16, 300))
+        A = _mat(KINDS[i % 5], n, rng)
+        B = rng.standard_normal((n, 1 + i % 3))
+        items.append((A, B))
+    alone = [_alone(ctx, A, B) for A, B in items]
+    dev = []
+    for A, B in items:
+        n = A.shape[0]
+        dB, r = dev_rhs(B, n)
+        dev.append((dev_colmajor(A), dB, torch.zeros_like(dB), n, r))
+    torch.cuda.synchronize()
+    results = [None] * len(items)
+
+    def producer(k):
+        for i in range(k, len(items), 4):
+            dA, dB, dX, n, r = dev[i]
+            rc, t = ctx.submit(dA, dB, n, r, dX)
+            assert rc == asolve.OK
+            rc, info, lat = ctx.poll(t, -1)
+            results[i] = (rc, info)
+
+    th = [threading.Thread(target=producer, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for i, (rc, info) in enumerate(results):
+        assert rc == alone[i][0]
+        _same_info(info, alone[i][1])
+        dA, dB, dX, n, r = dev[i]
+        assert np.array_equal(host_from_dev(dX, n, r), alone[i][2])
+    ctx.close()
