@@ -428,21 +428,25 @@ def large_workload(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     sizes = [int(x) for x in args.sizes.split(",")]
-    kappas = [1e2, 1e4, 1e6]
-    ctxs = {p: asolve.Context(precision=p) for p in (asolve.PREC_MIXED, asolve.PREC_FP64)}
+    kappas = [float(x) for x in args.kappas.split(",")]
+    kinds = args.kinds.split(",")
+    nrhs_list = [int(x) for x in args.nrhs_list.split(",")]
+    precs = [(asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64")]
+    precs = [p for p in precs if p[1] in args.precs.split(",")]
+    ctxs = {p: asolve.Context(precision=p) for p, _ in precs}
     cases = []
     with ClockSampler(0) as clk:
         for n in sizes:
-            for kind in ("general", "spd"):
+            for kind in kinds:
                 for kappa in kappas:
                     g = synth.gen(int(n + 17 * kappa) % 100003, dev)
                     A = synth.spectrum_fast(n, g, kappa, spd=(kind == "spd"), device=dev)
                     B64 = synth.rhs(n, 64, g, dev)
-                    for nrhs in (1, 64):
+                    for nrhs in nrhs_list:
                         B = B64[:nrhs].contiguous()
                         X = torch.zeros_like(B)
                         row = {"n": n, "kind": kind, "kappa": kappa, "nrhs": nrhs}
-                        for p, name in ((asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64")):
+                        for p, name in precs:
                             c = ctxs[p]
                             st = torch.cuda.ExternalStream(c.stream)
                             rc, info = c.solve(A, B, n, nrhs, X, asolve.BERR)  # warm-up (workspace)
@@ -465,7 +469,8 @@ def large_workload(args):
                                          * n ** 3 / (ms * 1e-3)}
                             log(n, kind, f"{kappa:.0e}", nrhs, name, f"{ms:.2f} ms", info["route"],
                                 info["precision"], info["ir_iters"], f"{info['berr']:.2e}")
-                        row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
+                        if "fp64" in row and "mixed" in row:
+                            row["speedup"] = row["fp64"]["ms"] / row["mixed"]["ms"]
                         cases.append(row)
                     del A, B64
                     torch.cuda.empty_cache()
@@ -474,16 +479,18 @@ def large_workload(args):
     head = [c for c in cases if c["n"] == sizes[-1] and c["kind"] == "general" and c["kappa"] == 1e4
             and c["nrhs"] == 1]
     head = head[0] if head else cases[-1]
-    ok = head["mixed"]["rc"] == 0 and head["mixed"]["berr"] <= BERR_BAR
+    hp = "mixed" if "mixed" in head else "fp64"
+    ok = head[hp]["rc"] == 0 and head[hp]["berr"] <= BERR_BAR
     print(json.dumps({
         "metric": "solves/s at backward err <=1e-13 (single large dense system)",
-        "value": (1000.0 / head["mixed"]["ms"]) if ok else 0.0, "unit": "solves/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": head["mixed"]["ms"],
+        "value": (1000.0 / head[hp]["ms"]) if ok else 0.0, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 1, "ms_per_step": head[hp]["ms"],
         "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None,
         "dtype": "f64 (FP32 factors on tcgen05 3xTF32 + FP64 refinement)", "data": "synthetic",
-        "config": {"workload": f"large-dense: general U diag(logspace(0,-4)) V^T, n={head['n']}, nrhs=1",
+        "config": {"workload": f"large-dense: {head['kind']} U diag(logspace(0,-k)) V^T, n={head['n']}, "
+                               f"kappa={head['kappa']:.0e}, nrhs={head['nrhs']}, {hp}",
                    "l2": "inputs larger than L2"},
-        "fp64_path_ms": head["fp64"]["ms"], "speedup_vs_fp64_path": head["speedup"],
+        "fp64_path_ms": head.get("fp64", {}).get("ms"), "speedup_vs_fp64_path": head.get("speedup"),
         "clocks": clk.summary(), "cases": cases}), flush=True)
 
 
@@ -620,6 +627,10 @@ def main():
                     help="systems per GPU (smaller values are for profiling runs only)")
     ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve"])
     ap.add_argument("--sizes", default="8192,16384", help="large: matrix sizes")
+    ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds")
+    ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
+    ap.add_argument("--nrhs-list", default="1,64", help="large: right-hand-side counts")
+    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions")
     ap.add_argument("--templates", type=int, default=40, help="serve: distinct request matrices")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests per load point")
     ap.add_argument("--load", default="0.25,0.5,0.8", help="serve: arrival rates as fractions of capacity")
