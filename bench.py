@@ -22,6 +22,10 @@ Two more workloads print their own JSON line (not the headline):
                      {1e2, 1e4, 1e6}, nrhs in {1, 64}: mixed precision
                      (FP32 factors on tcgen05, FP64 refinement) vs the FP64
                      path, time per solve with CUDA events.
+  --workload plain   five single systems at n = 200 (general N(0,1), lower
+                     triangular, SPD, tridiagonal, U diag(logspace(0,-14)) V^T
+                     with Haar U, V), one right-hand side: latency of one
+                     asolve_solve call per system over --reps repetitions.
   --workload serve   request server: Poisson arrivals of FP64 requests in
                      host memory, n log-uniform in [32, 8192], the batched
                      class mix, kappa log-uniform in [1e1, 1e12], HBM budget
@@ -229,6 +233,24 @@ def oracle_sample(pk, budget_s=15.0, max_threads=None):
                       f"(threads across systems), {dt:.1f} s"}
 
 
+def aggregate_ranks(local_ms, local_ok, dist=None, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time (max) and the
+    verified systems of every rank (sum).  No data moves between ranks:
+    each rank solves its own batch."""
+    tt = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    okt = torch.tensor([float(local_ok)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.barrier()
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(okt, op=dist.ReduceOp.SUM)
+    return tt.item(), okt.item()
+
+
+def rank_seed(rank):
+    """Seed of rank `rank`'s batch (independent systems per rank)."""
+    return SEED + 7919 * rank
+
+
 def ours(args):
     from paper_2007_11208_gb300 import asolve, build
     rank = int(os.environ.get("RANK", "0"))
@@ -242,7 +264,7 @@ def ours(args):
     build.build()
     dev = torch.device("cuda", local)
     t_gen = time.perf_counter()
-    pk = make_batch(dev, SEED + 7919 * rank, COUNT)
+    pk = make_batch(dev, rank_seed(rank), COUNT)
     torch.cuda.synchronize()
     log(f"[rank {rank}] batch generated in {time.perf_counter() - t_gen:.1f}s; "
         f"A bytes {pk['A'].numel() * 8 / 1e9:.2f} GB")
@@ -268,15 +290,8 @@ def ours(args):
     # headline: mixed precision path
     times, inf_mixed, clocks, _ = arm(asolve.PREC_MIXED, args.steps, args.warmup)
     ok, hist = verified_count(inf_mixed)
-    # max over ranks
-    tt = torch.tensor([sum(times)], dtype=torch.float64, device=dev)
-    okt = torch.tensor([float(ok)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.barrier()
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(okt, op=dist.ReduceOp.SUM)
-    total_ms = tt.item()
-    value = okt.item() * args.steps / (total_ms / 1e3)
+    total_ms, ok_all = aggregate_ranks(sum(times), ok, dist, dev)
+    value = ok_all * args.steps / (total_ms / 1e3)
     if args.quick:
         print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "quick": True,
                           "ms_per_step": total_ms / args.steps, "count": COUNT}), flush=True)
@@ -494,6 +509,62 @@ def large_workload(args):
         "clocks": clk.summary(), "cases": cases}), flush=True)
 
 
+# --------------------------------------------------------------- plain
+def plain_workload(args):
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = 200
+    g = synth.gen(0, dev)
+    mats = {"general": synth.general(n, g, dev), "lower": synth.lower_tri(n, g, dev),
+            "spd": synth.spd(n, g, dev), "tridiag": synth.tridiag(n, g, dev),
+            "ill": synth.ill(n, g, k=14.0, device=dev)}
+    b = synth.rhs(n, 1, g, dev)
+    ctx = asolve.Context()
+    st = torch.cuda.ExternalStream(ctx.stream)
+    x = torch.zeros_like(b)
+    hb = b.cpu().pin_memory()
+    hx = torch.zeros_like(hb).pin_memory()
+    rows = []
+    with ClockSampler(0) as clk:
+        for name, A in mats.items():
+            hA = A.cpu().pin_memory()
+            for _ in range(20):
+                ctx.solve(A, b, n, 1, x, 0)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.reps)]
+            wall = []
+            for e0, e1 in ev:
+                t0 = time.perf_counter()
+                e0.record(st)
+                rc, info = ctx.solve(A, b, n, 1, x, 0)
+                e1.record(st)
+                wall.append((time.perf_counter() - t0) * 1e6)
+            torch.cuda.synchronize()
+            dev_us = np.array([e0.elapsed_time(e1) * 1e3 for e0, e1 in ev])
+            e2e = []
+            for _ in range(min(args.reps, 200)):
+                t0 = time.perf_counter()
+                ctx.solve(hA.data_ptr(), hb.data_ptr(), n, 1, hx.data_ptr(), asolve.HOST_BUFFERS)
+                e2e.append((time.perf_counter() - t0) * 1e6)
+            rows.append({"system": name, "route": info["route"], "status": rc, "rcond": info["rcond"],
+                         "p50_us": float(np.percentile(wall, 50)), "p99_us": float(np.percentile(wall, 99)),
+                         "device_p50_us": float(np.percentile(dev_us, 50)),
+                         "e2e_p50_us": float(np.percentile(e2e, 50))})
+            log(rows[-1])
+    ctx.close()
+    med = float(np.median([r["p50_us"] for r in rows]))
+    print(json.dumps({
+        "metric": "latency of one adaptive solve (n=200, 1 rhs), median over the five systems",
+        "value": med, "unit": "us", "n_gpus": 1, "steps": args.reps, "warmup": 20, "ms_per_step": med / 1e3,
+        "higher_is_better": False, "scaling": "replicas only", "vs_baseline": None, "dtype": "f64 (mixed)",
+        "data": "synthetic", "config": {"workload": "plain-200: general/lower/spd/tridiag/ill, seed 0"},
+        "e2e": {"value": float(np.median([r["e2e_p50_us"] for r in rows])), "unit": "us",
+                "h2d_bytes_per_step": 8 * (n * n + n), "d2h_bytes_per_step": 8 * n + 64},
+        "clocks": clk.summary(), "systems": rows}), flush=True)
+
+
 # --------------------------------------------------------------- serving
 def _serve_templates(count, seed, dev, nmin=32, nmax=8192):
     """Request templates: n log-uniform, batched class mix, kappa log-uniform."""
@@ -625,7 +696,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per GPU (smaller values are for profiling runs only)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve", "plain"])
+    ap.add_argument("--reps", type=int, default=1000, help="plain: repetitions per system")
     ap.add_argument("--sizes", default="8192,16384", help="large: matrix sizes")
     ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds")
     ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
@@ -642,6 +714,8 @@ def main():
         return large_workload(args)
     if args.workload == "serve":
         return serve_workload(args)
+    if args.workload == "plain":
+        return plain_workload(args)
     if args.impl == "reference":
         reference(args)
     else:

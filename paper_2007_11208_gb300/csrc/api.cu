@@ -99,7 +99,8 @@ struct asolve_ctx {
   DevBuf single;       // n, nrhs, a_off, b_off, info (device)
   int64_t* h_single = nullptr;  // pinned: 4 int64 + asolve_info
   DevBuf hostA, hostB, hostX, hostMeta;  // device copies for ASOLVE_HOST_BUFFERS
-  DevBuf large;        // large-scan workspace
+  DevBuf large;        // large-system / banded workspace
+  DevBuf bandDense;    // dense copy of a band-stored matrix (SVD fallback)
   ScanRes* h_scan = nullptr;  // pinned
   // request server (created by the first asolve_submit)
   void* serve = nullptr;
@@ -229,6 +230,7 @@ extern "C" int asolve_destroy(asolve_ctx* c) {
   c->hostX.release();
   c->hostMeta.release();
   c->large.release();
+  c->bandDense.release();
   if (c->d_desc) cudaFree(c->d_desc);
   if (c->h_desc) cudaFreeHost(c->h_desc);
   if (c->h_single) cudaFreeHost(c->h_single);
@@ -558,9 +560,61 @@ extern "C" int asolve_scan(asolve_ctx* c, const double* A, int64_t n, asolve_sca
 extern "C" int asolve_solve_band(asolve_ctx* c, const double* AB, int64_t ldab, int64_t kl, int64_t ku,
                                  const double* B, int64_t n, int64_t nrhs, uint32_t flags, double* X,
                                  asolve_info* info) {
-  (void)AB; (void)ldab; (void)kl; (void)ku; (void)B; (void)n; (void)nrhs; (void)flags; (void)X; (void)info;
-  if (!c) return ASOLVE_E_INVALID;
-  return ASOLVE_E_UNSUPPORTED;
+  if (!c || n < 0 || nrhs < 1 || kl < 0 || ku < 0 || ldab < kl + ku + 1) return ASOLVE_E_INVALID;
+  if (n == 0) {
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->rcond = NAN;
+      info->berr = NAN;
+      info->svd_rank = -1;
+    }
+    return ASOLVE_OK;
+  }
+  if (!AB || !B || !X) return ASOLVE_E_INVALID;
+  if (n > INT32_MAX / 2 || nrhs > 256) return ASOLVE_E_UNSUPPORTED;
+  // the true bandwidths never exceed n - 1
+  const int64_t kle = kl < n - 1 ? kl : n - 1, kue = ku < n - 1 ? ku : n - 1;
+  if (!band_window_fits(kle, kue)) return ASOLVE_E_UNSUPPORTED;
+  CK(cudaSetDevice(c->device));
+  cudaStream_t st = c->stream;
+  const double* dAB = AB;
+  const double* dB = B;
+  double* dX = X;
+  if (flags & ASOLVE_HOST_BUFFERS) {
+    CK(c->hostA.ensure(sizeof(double) * (size_t)(ldab * n)));
+    CK(c->hostB.ensure(sizeof(double) * (size_t)(n * nrhs)));
+    CK(c->hostX.ensure(sizeof(double) * (size_t)(n * nrhs)));
+    CK(cudaMemcpyAsync(c->hostA.p, AB, sizeof(double) * (size_t)(ldab * n), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->hostB.p, B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyHostToDevice, st));
+    dAB = (const double*)c->hostA.p;
+    dB = (const double*)c->hostB.p;
+    dX = (double*)c->hostX.p;
+  }
+  CK(c->large.ensure(band_ws_bytes(n, kle, kue, nrhs)));
+  BandArgs ba{dAB, ldab, kl, ku, nullptr, dB, dX, n, nrhs, flags, c->cfg.rcond_threshold, 0, 0, 0.0, 0.0, st};
+  asolve_info li;
+  int rc = band_solve(ba, c->large.p, c->large.bytes, &li);
+  if (rc == ASOLVE_PENDING) {
+    // solver failed or rcond below the threshold: the SVD fallback of
+    // Sec. 2.5 on a dense copy (n <= 1024 here)
+    CK(c->bandDense.ensure(sizeof(double) * (size_t)(n * n)));
+    int r2 = band_to_dense(dAB, ldab, kl, ku, n, (double*)c->bandDense.p, st);
+    if (r2 != ASOLVE_OK) return r2;
+    asolve_info si;
+    r2 = asolve_solve(c, (const double*)c->bandDense.p, dB, n, nrhs,
+                      (flags & ~(ASOLVE_HOST_BUFFERS | ASOLVE_FORCE_LU)) | ASOLVE_FORCE_SVD, dX, &si);
+    if (r2 < 0 && si.status >= 0) si.status = r2;
+    li.status = si.status;
+    li.svd_rank = si.svd_rank;
+    li.berr = si.berr;
+    rc = li.status;
+  }
+  if (flags & ASOLVE_HOST_BUFFERS) {
+    CK(cudaMemcpyAsync(X, dX, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (info) *info = li;
+  return li.status;
 }
 
 extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,

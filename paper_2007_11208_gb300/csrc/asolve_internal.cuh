@@ -75,6 +75,27 @@ struct BatchDesc {
   int32_t* err_flag;       // device-side error (e.g. a scratch slot too small)
 };
 
+// One system for the banded route (band_large.cu): band storage input
+// (AB, ldab, declared kld/kud) or a dense matrix A with its scan results.
+struct BandArgs {
+  const double* AB;
+  int64_t ldab;
+  int64_t kld, kud;
+  const double* A;
+  const double* B;
+  double* X;
+  int64_t n, nrhs;
+  uint32_t flags;
+  double rcond_threshold;
+  int64_t kl, ku;          // dense input: the scan's bandwidths and norms
+  double norm1, norminf;
+  cudaStream_t st;
+};
+size_t band_ws_bytes(int64_t n, int64_t kl, int64_t ku, int64_t nrhs);
+bool band_window_fits(int64_t kl, int64_t ku);
+int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
+int band_to_dense(const double* AB, int64_t ldab, int64_t kld, int64_t kud, int64_t n, double* A, cudaStream_t st);
+
 // Column-major A, B and X of system s of a batch.
 __device__ __forceinline__ const double* sys_A(const BatchDesc& d, int64_t s) {
   return d.Ap ? d.Ap[s] : d.A + d.a_off[s];

@@ -1,0 +1,807 @@
+// band_large.cu -- the banded route (Sec. 2.1) for one system of any order:
+// a matrix given in band storage (asolve_solve_band), or a dense matrix the
+// scan classified as banded with n > 1024.  xGBTRF / xGBTRS / xGBCON
+// semantics: LU with partial pivoting inside the band (U fills out to kl+ku
+// super-diagonals), the solve with those factors, and the Hager/Higham
+// 1-norm estimate of inv(A) through them.
+//
+// The elimination is a chain of n dependent column steps, so one warp runs
+// it and the kernels are built around the latency of one step:
+//   k_band_lu_win  the active window of the factor (columns j .. j+kl+ku)
+//                  lives in shared memory; columns stream in with cp.async
+//                  a few steps ahead and go back to global memory once final;
+//   k_band_solve   one warp per right-hand side: the window of the vector
+//                  being eliminated sits in registers across the lanes (one
+//                  element per lane and register), the factor columns
+//                  stream through a cp.async ring;
+//   k_band_est     the estimate, driven on the device by one warp with the
+//                  same sweeps.
+// Bandwidths beyond those windows fall back to the warp routines that work
+// on global memory directly (band_warp.cuh).  Scan, packing and the FP64
+// backward error are ordinary data-parallel kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include "band_warp.cuh"
+
+namespace asv {
+
+namespace {
+
+constexpr int kD = 4;           // cp.async prefetch distance (column steps)
+constexpr int kMaxR = 8;        // register-window width: kl+ku+1 <= 32 * kMaxR
+constexpr size_t kWinSmemMax = 200 * 1024;
+constexpr size_t kTailBytes = 16384;  // scan record, scalars and per-column maxima (nrhs <= 256)
+
+#define BCK(x)                                        \
+  do {                                                \
+    cudaError_t _e = (x);                             \
+    if (_e != cudaSuccess) {                          \
+      cudaGetLastError();                             \
+      return _e == cudaErrorMemoryAllocation ? ASOLVE_E_NOMEM : ASOLVE_E_CUDA; \
+    }                                                 \
+  } while (0)
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ------------------------------------------------------------ scan / pack
+struct BandScan {
+  int kl, ku, nonfinite, b_nonfinite;
+  unsigned long long norm1, norminf;  // bit patterns of non-negative doubles
+};
+
+// True bandwidths inside the declared band, non-finite flags, and the 1- and
+// inf-norms (Sec. 2.1 finds kl, ku by the last non-zero diagonal).
+__global__ void k_bscan(const double* __restrict__ AB, int64_t ldab, int kld, int kud, int64_t n,
+                        const double* __restrict__ B, int64_t nb, BandScan* out) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int kl = 0, ku = 0, bad = 0;
+  double n1 = 0.0, ninf = 0.0;
+  for (int64_t j = tid; j < n; j += stride) {
+    const int64_t lo = j - kud > 0 ? j - kud : 0, hi = j + kld < n - 1 ? j + kld : n - 1;
+    double cs = 0.0;
+    for (int64_t i = lo; i <= hi; ++i) {
+      const double v = AB[(size_t)(kud + i - j) + (size_t)j * ldab];
+      if (is_nonfinite_bits(dbits(v))) bad = 1;
+      if (is_nonzero_bits(dbits(v))) {
+        if (i > j && (int)(i - j) > kl) kl = (int)(i - j);
+        if (j > i && (int)(j - i) > ku) ku = (int)(j - i);
+      }
+      cs += fabs(v);
+    }
+    n1 = fmax(n1, cs);
+  }
+  for (int64_t i = tid; i < n; i += stride) {
+    const int64_t lo = i - kld > 0 ? i - kld : 0, hi = i + kud < n - 1 ? i + kud : n - 1;
+    double rs = 0.0;
+    for (int64_t j = lo; j <= hi; ++j) rs += fabs(AB[(size_t)(kud + i - j) + (size_t)j * ldab]);
+    ninf = fmax(ninf, rs);
+  }
+  int bbad = 0;
+  for (int64_t e = tid; e < nb; e += stride)
+    if (is_nonfinite_bits(dbits(B[e]))) bbad = 1;
+  kl = warp_max(kl);
+  ku = warp_max(ku);
+  bad = warp_max(bad);
+  bbad = warp_max(bbad);
+  n1 = warp_max(n1);
+  ninf = warp_max(ninf);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out->kl, kl);
+    atomicMax(&out->ku, ku);
+    atomicMax(&out->nonfinite, bad);
+    atomicMax(&out->b_nonfinite, bbad);
+    atomicMax(&out->norm1, (unsigned long long)dbits(n1));
+    atomicMax(&out->norminf, (unsigned long long)dbits(ninf));
+  }
+}
+
+// Band factor storage F (ldf = 2kl+ku+1, kv = kl+ku): A(i,j) at
+// F[(kv+i-j) + j*ldf]; rows 0..kl-1 (the fill of U) start at zero.
+__global__ void k_bpack(const double* __restrict__ AB, int64_t ldab, int kud, const double* __restrict__ A,
+                        int64_t n, int kl, int ku, double* __restrict__ F) {
+  const int ldf = 2 * kl + ku + 1, kv = kl + ku;
+  const int64_t total = (int64_t)ldf * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % ldf);
+    const int64_t j = e / ldf, i = r - kv + j;
+    double v = 0.0;
+    if (r >= kl && i >= 0 && i < n) v = A ? A[(size_t)j * n + i] : AB[(size_t)(kud + i - j) + (size_t)j * ldab];
+    F[e] = v;
+  }
+}
+
+__global__ void k_band_to_dense(const double* __restrict__ AB, int64_t ldab, int kld, int kud, int64_t n,
+                                double* __restrict__ A) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / n, i = e % n;
+    A[e] = (i - j <= kld && j - i <= kud) ? AB[(size_t)(kud + i - j) + (size_t)j * ldab] : 0.0;
+  }
+}
+
+// ------------------------------------------------------------ factor
+// GBTRF on F with the active window in shared memory: S = kv+1+kD column
+// slots of ldf doubles; column c lives in slot c % S while it is active.
+__global__ void __launch_bounds__(32) k_band_lu_win(double* __restrict__ F, int ldf, int n, int kl, int ku,
+                                                    int* __restrict__ piv, int* __restrict__ fail) {
+  extern __shared__ double win[];
+  const int lane = threadIdx.x;
+  const int kv = kl + ku, S = kv + 1 + kD;
+  auto slot = [&](int c) { return win + (size_t)(c % S) * ldf; };
+  // columns 0 .. S-1 in flight, one commit group each
+  for (int c = 0; c < S; ++c) {
+    if (c < n)
+      for (int r = lane; r < ldf; r += 32) cp_async8(slot(c) + r, F + (size_t)c * ldf + r);
+    cp_commit();
+  }
+  int ju = 0;
+  for (int j = 0; j < n; ++j) {
+    // column j + kv is the last one step j touches: kD newer groups may pend
+    cp_wait<kD>();
+    __syncwarp();
+    double* cj = slot(j);
+    const int km = min(kl, n - 1 - j);
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int t = lane; t <= km; t += 32) {
+      const double v = fabs(cj[kv + t]);
+      if (v > best) { best = v; bi = t; }
+    }
+    warp_argmax_first(best, bi);
+    if (bi < 0 || bi > km || !(cj[kv + bi] != 0.0)) {  // exact zero (or invalid) pivot
+      if (lane == 0) *fail = j + 1;
+      cp_wait_all();
+      __syncwarp();
+      // leave the columns already final in F; the factor is not used
+      return;
+    }
+    if (lane == 0) piv[j] = j + bi;
+    ju = max(ju, min(j + ku + bi, n - 1));
+    if (bi != 0)
+      for (int c = j + lane; c <= ju; c += 32) {
+        double* cc = slot(c);
+        const double t0 = cc[kv + j - c];
+        cc[kv + j - c] = cc[kv + j + bi - c];
+        cc[kv + j + bi - c] = t0;
+      }
+    __syncwarp();
+    const double inv = 1.0 / cj[kv];
+    for (int t = 1 + lane; t <= km; t += 32) cj[kv + t] *= inv;
+    __syncwarp();
+    // rank-1 update of rows j+1..j+km, columns j+1..ju; lane <-> row
+    for (int t0 = 1; t0 <= km; t0 += 32) {
+      const int t = t0 + lane;
+      const bool on = t <= km;
+      const double l = on ? cj[kv + t] : 0.0;
+      int sc = (j + 1) % S;
+#pragma unroll 4
+      for (int c = j + 1; c <= ju; ++c) {
+        double* cc = win + (size_t)sc * ldf;
+        const double u = cc[kv + j - c];
+        if (on) cc[kv + j + t - c] = fma(-l, u, cc[kv + j + t - c]);
+        sc = (sc + 1 == S) ? 0 : sc + 1;
+      }
+    }
+    __syncwarp();
+    // column j is final
+    for (int r = lane; r < ldf; r += 32) F[(size_t)j * ldf + r] = cj[r];
+    __syncwarp();
+    const int cn = j + S;
+    if (cn < n)
+      for (int r = lane; r < ldf; r += 32) cp_async8(cj + r, F + (size_t)cn * ldf + r);
+    cp_commit();
+  }
+  cp_wait_all();
+  // columns still resident are final too (they were written above as j passed)
+}
+
+// The general-bandwidth fallback: the warp routine on global memory.
+__global__ void __launch_bounds__(32) k_band_lu_glob(double* F, int ldf, int n, int kl, int ku, int* piv,
+                                                     int* fail) {
+  WarpBand b;
+  b.F = F;
+  b.piv = piv;
+  b.n = n;
+  b.kl = kl;
+  b.ku = ku;
+  b.kv = kl + ku;
+  b.ldf = ldf;
+  const int f = warp_band_lu(b);
+  if ((threadIdx.x & 31) == 0 && f) *fail = f;
+}
+
+// ------------------------------------------------------------ sweeps
+// The vector window: element e sits in register e >> 5 of lane e & 31.
+template <int R>
+struct Win {
+  double w[R];
+  // (selects on shuffled copies keep every w[r] in a register)
+  __device__ __forceinline__ double get(int e) const {
+    const int re = e >> 5, le = e & 31;
+    double v = __shfl_sync(0xffffffffu, w[0], le);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const double t = __shfl_sync(0xffffffffu, w[r], le);
+      v = (r == re) ? t : v;
+    }
+    return v;
+  }
+  __device__ __forceinline__ void set(int e, double v) {
+    const int lane = threadIdx.x & 31;
+    const bool mine = lane == (e & 31);
+#pragma unroll
+    for (int r = 0; r < R; ++r) w[r] = (mine && r == (e >> 5)) ? v : w[r];
+  }
+  // element e <- element e+1; the top element becomes 0
+  __device__ __forceinline__ void shift_down() {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double nxt = (r + 1 < R) ? __shfl_sync(0xffffffffu, w[(r + 1 < R) ? r + 1 : r], 0) : 0.0;
+      w[r] = __shfl_down_sync(0xffffffffu, w[r], 1);
+      if (lane == 31) w[r] = nxt;
+    }
+  }
+  // element e <- element e-1; element 0 becomes v0
+  __device__ __forceinline__ void shift_up(double v0) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = R - 1; r >= 0; --r) {
+      const double prv = (r > 0) ? __shfl_sync(0xffffffffu, w[r > 0 ? r - 1 : 0], 31) : v0;
+      w[r] = __shfl_up_sync(0xffffffffu, w[r], 1);
+      if (lane == 0) w[r] = prv;
+    }
+  }
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// x <- inv(A) x with the band factors (Sec. 2.1 solve), one warp, one vector.
+// ring: kD * (kv + 2) doubles + kD ints of shared memory.
+template <int R>
+__device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl, int ku, const int* __restrict__ piv,
+                           double* x, double* ring, int* pring) {
+  const int lane = threadIdx.x & 31;
+  const int kv = kl + ku, SL = kv + 2;
+  Win<R> W;
+  // ---- forward: apply P_j then L_j, j = 0..n-1; element t = x[j+t], t <= kl
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = r * 32 + lane;
+    W.w[r] = (t <= kl && t < n) ? x[t] : 0.0;
+  }
+  __syncwarp();
+  auto pre_f = [&](int c) {
+    if (c < n) {
+      double* sl = ring + (size_t)(c % kD) * SL;
+      const int kmc = min(kl, n - 1 - c);
+      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)c * ldf);
+      if (lane == 0) {
+        if (c + kl + 1 < n) cp_async8(sl + kl, x + c + kl + 1);
+        cp_async4(pring + c % kD, piv + c);
+      }
+    }
+    cp_commit();
+  };
+  for (int c = 0; c < kD; ++c) pre_f(c);
+  for (int j = 0; j < n; ++j) {
+    cp_wait<kD - 1>();
+    __syncwarp();
+    const double* sl = ring + (size_t)(j % kD) * SL;
+    const int km = min(kl, n - 1 - j);
+    const int d = pring[j % kD] - j;
+    const double e0 = W.get(0);
+    const double ed = W.get(d);
+    if (d) {
+      W.set(0, ed);
+      W.set(d, e0);
+    }
+    const double xj = d ? ed : e0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = r * 32 + lane;
+      if (t >= 1 && t <= km) W.w[r] = fma(-sl[t - 1], xj, W.w[r]);
+    }
+    if (lane == 0) x[j] = xj;
+    const double inc = (j + kl + 1 < n) ? sl[kl] : 0.0;
+    W.shift_down();
+    W.set(kl, inc);
+    __syncwarp();
+    pre_f(j + kD);
+  }
+  cp_wait_all();
+  __syncwarp();
+  __threadfence();
+  // ---- backward: U x = y, i = n-1..0; element s = y[i-s], s <= kv
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int s = r * 32 + lane;
+    W.w[r] = (s <= kv && n - 1 - s >= 0) ? x[n - 1 - s] : 0.0;
+  }
+  __syncwarp();
+  auto pre_b = [&](int q) {
+    const int i = n - 1 - q;
+    if (i >= 0) {
+      double* sl = ring + (size_t)(q % kD) * SL;
+      for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)i * ldf);
+      if (lane == 0 && i - kv - 1 >= 0) cp_async8(sl + kv + 1, x + i - kv - 1);
+    }
+    cp_commit();
+  };
+  for (int q = 0; q < kD; ++q) pre_b(q);
+  for (int q = 0; q < n; ++q) {
+    const int i = n - 1 - q;
+    cp_wait<kD - 1>();
+    __syncwarp();
+    const double* sl = ring + (size_t)(q % kD) * SL;
+    const double xi = W.get(0) / sl[kv];
+    if (lane == 0) x[i] = xi;
+    const int lim = min(kv, i);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int s = r * 32 + lane;
+      if (s >= 1 && s <= lim) W.w[r] = fma(-sl[kv - s], xi, W.w[r]);
+    }
+    const double inc = (i - kv - 1 >= 0) ? sl[kv + 1] : 0.0;
+    W.shift_down();
+    W.set(kv, inc);
+    __syncwarp();
+    pre_b(q + kD);
+  }
+  cp_wait_all();
+  __syncwarp();
+  __threadfence();
+}
+
+// x <- inv(A)^T x: U^T z = x forward, then L_j^T and P_j backward.
+template <int R>
+__device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int kl, int ku,
+                             const int* __restrict__ piv, double* x, double* ring, int* pring) {
+  const int lane = threadIdx.x & 31;
+  const int kv = kl + ku, SL = kv + 2;
+  Win<R> W;
+  // ---- U^T z = b, i = 0..n-1: element 0 = b_i, element s = z_{i-s}
+#pragma unroll
+  for (int r = 0; r < R; ++r) W.w[r] = (r == 0 && lane == 0) ? x[0] : 0.0;
+  __syncwarp();
+  auto pre_u = [&](int c) {
+    if (c < n) {
+      double* sl = ring + (size_t)(c % kD) * SL;
+      for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)c * ldf);
+      if (lane == 0 && c + 1 < n) cp_async8(sl + kv + 1, x + c + 1);
+    }
+    cp_commit();
+  };
+  for (int c = 0; c < kD; ++c) pre_u(c);
+  for (int i = 0; i < n; ++i) {
+    cp_wait<kD - 1>();
+    __syncwarp();
+    const double* sl = ring + (size_t)(i % kD) * SL;
+    const int lim = min(kv, i);
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int s = r * 32 + lane;
+      if (s >= 1 && s <= lim) acc = fma(sl[kv - s], W.w[r], acc);
+    }
+    acc = warp_sum_d(acc);
+    const double zi = (W.get(0) - acc) / sl[kv];
+    if (lane == 0) x[i] = zi;
+    W.set(0, zi);
+    const double inc = (i + 1 < n) ? sl[kv + 1] : 0.0;
+    W.shift_up(inc);
+    __syncwarp();
+    pre_u(i + kD);
+  }
+  cp_wait_all();
+  __syncwarp();
+  __threadfence();
+  // ---- L^T with interchanges, j = n-1..0: element t = x[j+t], t <= kl
+#pragma unroll
+  for (int r = 0; r < R; ++r) W.w[r] = (r == 0 && lane == 0) ? x[n - 1] : 0.0;
+  __syncwarp();
+  auto pre_l = [&](int q) {
+    const int j = n - 1 - q;
+    if (j >= 0) {
+      double* sl = ring + (size_t)(q % kD) * SL;
+      const int kmc = min(kl, n - 1 - j);
+      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)j * ldf);
+      if (lane == 0) {
+        if (j - 1 >= 0) cp_async8(sl + kl, x + j - 1);
+        cp_async4(pring + q % kD, piv + j);
+      }
+    }
+    cp_commit();
+  };
+  for (int q = 0; q < kD; ++q) pre_l(q);
+  for (int q = 0; q < n; ++q) {
+    const int j = n - 1 - q;
+    cp_wait<kD - 1>();
+    __syncwarp();
+    const double* sl = ring + (size_t)(q % kD) * SL;
+    const int km = min(kl, n - 1 - j);
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = r * 32 + lane;
+      if (t >= 1 && t <= km) acc = fma(sl[t - 1], W.w[r], acc);
+    }
+    acc = warp_sum_d(acc);
+    const double v = W.get(0) - acc;
+    const int d = pring[q % kD] - j;
+    if (d) {
+      const double ed = W.get(d);
+      W.set(0, ed);
+      W.set(d, v);
+    } else {
+      W.set(0, v);
+    }
+    if (j == 0) break;
+    // element kl (x[j+kl]) is final: no later step reads or swaps it
+    const double ek = W.get(kl);
+    if (lane == 0 && j + kl < n) x[j + kl] = ek;
+    const double inc = sl[kl];
+    W.shift_up(inc);
+    __syncwarp();
+    pre_l(q + kD);
+  }
+  cp_wait_all();
+  __syncwarp();
+  // flush the window: elements 0..kl are x[0..kl]
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int t = r * 32 + lane;
+    if (t <= kl && t < n) x[t] = W.w[r];
+  }
+  __syncwarp();
+  __threadfence();
+}
+
+template <int R>
+__global__ void __launch_bounds__(32) k_band_solve(const double* F, int ldf, int n, int kl, int ku, const int* piv,
+                                                   double* X) {
+  __shared__ double ring[kD * (32 * kMaxR + 2)];
+  __shared__ int pring[kD];
+  band_apply<R>(F, ldf, n, kl, ku, piv, X + (size_t)blockIdx.x * n, ring, pring);
+}
+
+// General-bandwidth fallback of the solve (global-memory warp routine).
+__global__ void __launch_bounds__(32) k_band_solve_glob(double* F, int ldf, int n, int kl, int ku, int* piv,
+                                                        double* X) {
+  WarpBand b;
+  b.F = F;
+  b.piv = piv;
+  b.n = n;
+  b.kl = kl;
+  b.ku = ku;
+  b.kv = kl + ku;
+  b.ldf = ldf;
+  warp_band_apply(b, X + (size_t)blockIdx.x * n, false);
+}
+
+// ------------------------------------------------------------ estimate
+// 1-norm estimate of inv(A) (Hager 1984, Higham 1988) with the band factors,
+// driven by one warp: the same iteration as the other routes' estimators.
+template <int R, bool GLOB>
+__global__ void __launch_bounds__(32) k_band_est(double* F, int ldf, int n, int kl, int ku, int* piv, double* v,
+                                                 double* xi, double* out) {
+  __shared__ double ring[kD * (32 * kMaxR + 2)];
+  __shared__ int pring[kD];
+  const int lane = threadIdx.x & 31;
+  WarpBand b;
+  b.F = F;
+  b.piv = piv;
+  b.n = n;
+  b.kl = kl;
+  b.ku = ku;
+  b.kv = kl + ku;
+  b.ldf = ldf;
+  auto apply = [&](bool trans) {
+    __syncwarp();
+    __threadfence();
+    if (GLOB) warp_band_apply(b, v, trans);
+    else if (trans) band_apply_t<R>(F, ldf, n, kl, ku, piv, v, ring, pring);
+    else band_apply<R>(F, ldf, n, kl, ku, piv, v, ring, pring);
+    __syncwarp();
+    __threadfence();
+  };
+  auto sum_abs = [&]() {
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += fabs(v[i]);
+    return warp_sum_d(s);
+  };
+  auto argmax = [&]() {
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      const double a = fabs(v[i]);
+      if (a > best) { best = a; bi = i; }
+    }
+    warp_argmax_first(best, bi);
+    return bi;
+  };
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  for (int i = lane; i < n; i += 32) v[i] = 1.0 / (double)n;
+  apply(false);
+  if (n == 1) {
+    if (lane == 0) *out = fabs(v[0]);
+    return;
+  }
+  double est = sum_abs();
+  for (int i = lane; i < n; i += 32) {
+    const double sg = v[i] >= 0.0 ? 1.0 : -1.0;
+    xi[i] = sg;
+    v[i] = sg;
+  }
+  apply(true);
+  int k = 2;
+  for (;;) {
+    const int j = argmax();
+    if (j < 0 || j >= n) {
+      est = nan;
+      break;
+    }
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) v[i] = (i == j) ? 1.0 : 0.0;
+    apply(false);
+    const double estold = est;
+    est = sum_abs();
+    bool same = true;
+    for (int i = lane; i < n; i += 32)
+      if ((v[i] >= 0.0 ? 1.0 : -1.0) != xi[i]) same = false;
+    same = __all_sync(0xffffffffu, same);
+    if (same || est <= estold) break;
+    for (int i = lane; i < n; i += 32) {
+      const double sg = v[i] >= 0.0 ? 1.0 : -1.0;
+      xi[i] = sg;
+      v[i] = sg;
+    }
+    apply(true);
+    const int jn = argmax();
+    ++k;
+    if (jn < 0 || jn >= n) {
+      est = nan;
+      break;
+    }
+    const double vj = v[j], vjn = fabs(v[jn]);
+    __syncwarp();
+    if (vj == vjn || k > 5) break;
+  }
+  if (est == est) {
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) v[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
+    apply(false);
+    const double temp = 2.0 * sum_abs() / (double)(3 * n);
+    if (temp > est) est = temp;
+  }
+  if (lane == 0) *out = est;
+}
+
+// ------------------------------------------------------------ berr
+// Per column: max |b - A x|, max |x|, max |b| (FP64; A read in its input form).
+__global__ void k_band_berr(const double* __restrict__ AB, int64_t ldab, int kud, const double* __restrict__ A,
+                            int64_t n, int kl, int ku, const double* __restrict__ B, const double* __restrict__ X,
+                            int nrhs, unsigned long long* colmax) {
+  const int c = blockIdx.y;
+  const double* b = B + (size_t)c * n;
+  const double* x = X + (size_t)c * n;
+  double rm = 0.0, xm = 0.0, bm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = i - kl > 0 ? i - kl : 0, hi = i + ku < n - 1 ? i + ku : n - 1;
+    double acc = 0.0;
+    for (int64_t j = lo; j <= hi; ++j) {
+      const double a = A ? A[(size_t)j * n + i] : AB[(size_t)(kud + i - j) + (size_t)j * ldab];
+      acc = fma(a, x[j], acc);
+    }
+    rm = fmax(rm, fabs(b[i] - acc));
+    xm = fmax(xm, fabs(x[i]));
+    bm = fmax(bm, fabs(b[i]));
+  }
+  rm = warp_max(rm);
+  xm = warp_max(xm);
+  bm = warp_max(bm);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(colmax + c, (unsigned long long)dbits(rm));
+    atomicMax(colmax + nrhs + c, (unsigned long long)dbits(xm));
+    atomicMax(colmax + 2 * nrhs + c, (unsigned long long)dbits(bm));
+  }
+}
+
+int window_r(int kv) {
+  const int need = (kv + 1 + 31) / 32;
+  if (need <= 1) return 1;
+  if (need <= 2) return 2;
+  if (need <= 4) return 4;
+  if (need <= 8) return 8;
+  return 0;  // beyond the register window: global fallback
+}
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+double rcond_from_est(double anorm, double est) {
+  if (anorm == 0.0 || isinf(est) || est == 0.0) return 0.0;
+  return (1.0 / est) / anorm;
+}
+
+}  // namespace
+
+// Whether the fast kernels (shared-memory window, register window) cover
+// these bandwidths.
+bool band_window_fits(int64_t kl, int64_t ku) {
+  const int64_t kv = kl + ku, ldf = 2 * kl + ku + 1;
+  return kv + 1 <= 32 * kMaxR && (size_t)(kv + 1 + kD) * (size_t)ldf * sizeof(double) <= kWinSmemMax;
+}
+
+size_t band_ws_bytes(int64_t n, int64_t kl, int64_t ku, int64_t nrhs) {
+  (void)nrhs;
+  const size_t ldf = (size_t)(2 * kl + ku + 1);
+  return round256(sizeof(double) * ldf * (size_t)n) + round256(sizeof(int) * (size_t)n) +
+         2 * round256(sizeof(double) * (size_t)n) + kTailBytes;
+}
+
+// Device memory needed before the true bandwidths are known (declared band).
+size_t band_ws_bytes_declared(int64_t n, int64_t kld, int64_t kud, int64_t nrhs) {
+  return band_ws_bytes(n, kld, kud, nrhs);
+}
+
+// The banded route for one system.  Returns the status (also in info).
+// status ASOLVE_PENDING means: the factor failed or rcond is below the
+// threshold, the SVD fallback is allowed and n <= 1024 -- the caller runs it.
+int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) {
+  cudaStream_t st = a.st;
+  const int64_t n = a.n, nrhs = a.nrhs;
+  memset(info, 0, sizeof(*info));
+  info->rcond = NAN;
+  info->berr = NAN;
+  info->svd_rank = -1;
+  info->cls = ASOLVE_CLS_BANDED;
+  info->route = ASOLVE_ROUTE_BAND_LU;
+  info->precision = ASOLVE_PREC_FP64;
+  if (n > INT32_MAX / 2) return info->status = ASOLVE_E_UNSUPPORTED;
+  if (nrhs > 256) return info->status = ASOLVE_E_UNSUPPORTED;
+  if (ws_bytes < kTailBytes) return info->status = ASOLVE_E_NOMEM;
+  char* base = static_cast<char*>(ws);
+  char* tail = base + ((ws_bytes - kTailBytes) & ~(size_t)255);
+  BandScan* dscan = reinterpret_cast<BandScan*>(tail);
+  double* dscal = reinterpret_cast<double*>(tail + 256);
+  int* dint = reinterpret_cast<int*>(tail + 512);
+  unsigned long long* colmax = reinterpret_cast<unsigned long long*>(tail + 1024);
+  int kl, ku;
+  double norm1, norminf;
+  if (a.AB) {
+    BCK(cudaMemsetAsync(dscan, 0, sizeof(BandScan), st));
+    k_bscan<<<1024, 256, 0, st>>>(a.AB, a.ldab, (int)a.kld, (int)a.kud, n, a.B, n * nrhs, dscan);
+    BCK(cudaGetLastError());
+    BandScan h;
+    BCK(cudaMemcpyAsync(&h, dscan, sizeof(h), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    kl = h.kl;
+    ku = h.ku;
+    memcpy(&norm1, &h.norm1, 8);
+    memcpy(&norminf, &h.norminf, 8);
+    info->kl = kl;
+    info->ku = ku;
+    if (h.nonfinite || h.b_nonfinite) return info->status = ASOLVE_E_NONFINITE;
+  } else {
+    kl = (int)a.kl;
+    ku = (int)a.ku;
+    norm1 = a.norm1;
+    norminf = a.norminf;
+    info->kl = kl;
+    info->ku = ku;
+  }
+  const int kv = kl + ku, ldf = 2 * kl + ku + 1;
+  if (band_ws_bytes(n, kl, ku, nrhs) > ws_bytes) return info->status = ASOLVE_E_NOMEM;
+  double* F = reinterpret_cast<double*>(base);
+  int* piv = reinterpret_cast<int*>(base + round256(sizeof(double) * (size_t)ldf * n));
+  double* ev = reinterpret_cast<double*>(reinterpret_cast<char*>(piv) + round256(sizeof(int) * (size_t)n));
+  double* exi = ev + ((n + 31) & ~(int64_t)31);
+  k_bpack<<<4 * 152, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, F);
+  BCK(cudaGetLastError());
+  BCK(cudaMemsetAsync(dint, 0, sizeof(int) * 4, st));
+  const size_t wsm = sizeof(double) * (size_t)(kv + 1 + kD) * ldf;
+  const int R = window_r(kv);
+  if (wsm <= kWinSmemMax) {
+    static bool attr = false;
+    if (!attr) {
+      BCK(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemMax));
+      attr = true;
+    }
+    k_band_lu_win<<<1, 32, wsm, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
+  } else {
+    k_band_lu_glob<<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
+  }
+  BCK(cudaGetLastError());
+  int fail = 0;
+  BCK(cudaMemcpyAsync(&fail, dint, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
+  const bool svd_ok = !(a.flags & ASOLVE_NO_APPROX) && n <= 1024;
+  if (fail) {
+    BCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)(n * nrhs), st));
+    BCK(cudaStreamSynchronize(st));
+    return info->status = svd_ok ? ASOLVE_PENDING : ASOLVE_E_SINGULAR;
+  }
+  BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
+  switch (R) {
+    case 1: k_band_solve<1><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+    case 2: k_band_solve<2><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+    case 4: k_band_solve<4><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+    case 8: k_band_solve<8><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+    default: k_band_solve_glob<<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+  }
+  BCK(cudaGetLastError());
+  double rc = NAN;
+  if (!no_rcond) {
+    switch (R) {
+      case 1: k_band_est<1, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+      case 2: k_band_est<2, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+      case 4: k_band_est<4, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+      case 8: k_band_est<8, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+      default: k_band_est<1, true><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+    }
+    BCK(cudaGetLastError());
+    double est = NAN;
+    BCK(cudaMemcpyAsync(&est, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    rc = rcond_from_est(norm1, est);
+  }
+  info->rcond = no_rcond ? NAN : rc;
+  if (a.flags & ASOLVE_BERR) {
+    BCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    dim3 g((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
+    k_band_berr<<<g, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, a.B, a.X, (int)nrhs, colmax);
+    BCK(cudaGetLastError());
+    unsigned long long hm[3 * 256];
+    BCK(cudaMemcpyAsync(hm, colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    BCK(cudaStreamSynchronize(st));
+    double be = 0.0;
+    for (int64_t c = 0; c < nrhs; ++c) {
+      double rm, xm, bm;
+      memcpy(&rm, &hm[c], 8);
+      memcpy(&xm, &hm[nrhs + c], 8);
+      memcpy(&bm, &hm[2 * nrhs + c], 8);
+      const double den = norminf * xm + bm;
+      const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+      if (!(b1 <= be)) be = b1;
+    }
+    info->berr = be;
+  } else {
+    BCK(cudaStreamSynchronize(st));
+  }
+  const bool poor = !no_rcond && !(rc >= a.rcond_threshold);
+  if (!poor) return info->status = ASOLVE_OK;
+  if (a.flags & ASOLVE_NO_APPROX) return info->status = ASOLVE_W_ILLCOND;
+  return info->status = svd_ok ? ASOLVE_PENDING : ASOLVE_W_ILLCOND;
+}
+
+// Dense copy of a band-stored matrix (for the SVD fallback of small n).
+int band_to_dense(const double* AB, int64_t ldab, int64_t kld, int64_t kud, int64_t n, double* A, cudaStream_t st) {
+  k_band_to_dense<<<4 * 152, 256, 0, st>>>(AB, ldab, (int)kld, (int)kud, n, A);
+  BCK(cudaGetLastError());
+  return ASOLVE_OK;
+}
+
+}  // namespace asv

@@ -176,6 +176,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int r = m0 + 32 * w + lane;
 #pragma unroll 1
     for (int c0 = 0; c0 < kTcN; c0 += 32) {
+      // the 32 loads of C go out together, before the accumulator read
+      float cv[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = n0 + c0 + j;
+        cv[j] = (r < M && c < N) ? C[(size_t)c * ldc + r] : 0.f;
+      }
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(32 * w) << 16) + (uint32_t)c0;
       asm volatile(
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int c = n0 + c0 + j;
-          if (c < N) C[(size_t)c * ldc + r] -= __uint_as_float(v[j]);
+          if (c < N) C[(size_t)c * ldc + r] = cv[j] - __uint_as_float(v[j]);
         }
       }
     }

@@ -78,78 +78,76 @@ __global__ void __launch_bounds__(kThreads) k_chol_diag(T* W, int ldw, int k0, i
   if (f && threadIdx.x == 0) *fail = k0 + f;
 }
 
-// --------------------------------------- inverse of a triangular block
-// Dinv (kLB x kLB, column-major) = inverse of the kb x kb diagonal block at
-// (k0, k0) of W (lower or upper, unit or not), identity past kb.  Thread j
-// forms column j by substitution; the block is staged in shared memory.
+// ------------------------------------------------- panel TRSM by substitution
+// With L11 the kb x kb lower block of W at (k0, k0) (unit diagonal if
+// `unit`), solve L11 x = v in place for 64 vectors per CTA:
+//   side 0: the columns c in [lo, hi) of W's rows k0..k0+kb-1 (U12 of LU);
+//   side 1: the rows r in [lo, hi) of W's columns k0..k0+kb-1, i.e.
+//           x L11^T = a (L21 of Cholesky).
+// L11 and the 64 vectors sit in shared memory; four threads share each
+// vector (the dot product of step i is split four ways and combined with
+// two shuffles), so the 128 steps of forward substitution need no block
+// barrier.
+constexpr int kTrsmXP = kLB + 4;  // vector stride: 4 consecutive k of 8 vectors hit distinct banks
+
 template <typename T>
-__global__ void __launch_bounds__(kLB) k_tri_block_inv(const T* __restrict__ W, int ldw, int k0, int kb, int lower,
-                                                       int unit, T* __restrict__ Dinv) {
+__global__ void __launch_bounds__(kThreads) k_trsm_sub(T* __restrict__ W, int ldw, int k0, int kb, int lo, int hi,
+                                                      int side, int unit) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T* S = reinterpret_cast<T*>(smem);  // kLB x (kLB + 1), row-major: S[i * (kLB+1) + k] = D(i, k)
-  const int j = threadIdx.x;
-  for (int k = 0; k < kb; ++k)
-    if (j < kb) S[j * (kLB + 1) + k] = W[(size_t)(k0 + k) * ldw + k0 + j];
-  __syncthreads();
-  T* x = Dinv + (size_t)j * kLB;
-  if (lower) {
-    for (int i = 0; i < kLB; ++i) {
-      T s = (i == j) ? T(1) : T(0);
-      if (i < kb) {
-        for (int k = j; k < i; ++k) s -= S[i * (kLB + 1) + k] * x[k];
-        if (!unit) s /= S[i * (kLB + 1) + i];
-      }
-      x[i] = s;
+  T(*Ms)[kLB + 1] = reinterpret_cast<T(*)[kLB + 1]>(smem);  // Ms[i][k] = L11(i, k)
+  T* X = reinterpret_cast<T*>(smem + sizeof(T) * kLB * (kLB + 1));
+  T* rinv = X + 64 * kTrsmXP;
+  const int base = lo + blockIdx.x * 64;
+  if (base >= hi) return;
+  const int cnt = min(64, hi - base);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kLB * kLB; e += kThreads) {
+    const int i = e & (kLB - 1), k = e >> 7;
+    Ms[i][k] = (i < kb && k <= i) ? W[(size_t)(k0 + k) * ldw + k0 + i] : T(0);
+  }
+  if (side == 0) {
+    for (int e = tid; e < kLB * 64; e += kThreads) {
+      const int k = e & (kLB - 1), q = e >> 7;
+      X[q * kTrsmXP + k] = (k < kb && q < cnt) ? W[(size_t)(base + q) * ldw + k0 + k] : T(0);
     }
   } else {
-    for (int i = kLB - 1; i >= 0; --i) {
-      T s = (i == j) ? T(1) : T(0);
-      if (i < kb) {
-        for (int k = i + 1; k <= min(j, kb - 1); ++k) s -= S[i * (kLB + 1) + k] * x[k];
-        if (!unit) s /= S[i * (kLB + 1) + i];
-      }
-      x[i] = s;
+    for (int e = tid; e < kLB * 64; e += kThreads) {
+      const int q = e & 63, k = e >> 6;
+      X[q * kTrsmXP + k] = (k < kb && q < cnt) ? W[(size_t)(k0 + k) * ldw + base + q] : T(0);
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < kLB; i += kThreads) rinv[i] = (unit || i >= kb) ? T(1) : T(1) / Ms[i][i];
+  __syncthreads();
+  const int q = tid >> 2, t = tid & 3;
+  T* xq = X + q * kTrsmXP;
+  for (int i = 0; i < kb; ++i) {
+    T part = T(0);
+    for (int k = t; k < i; k += 4) part += Ms[i][k] * xq[k];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    const T xi = (xq[i] - part) * rinv[i];
+    __syncwarp();
+    if (t == 0) xq[i] = xi;
+    __syncwarp();
+  }
+  __syncthreads();
+  if (side == 0) {
+    for (int e = tid; e < kLB * 64; e += kThreads) {
+      const int k = e & (kLB - 1), qq = e >> 7;
+      if (k < kb && qq < cnt) W[(size_t)(base + qq) * ldw + k0 + k] = X[qq * kTrsmXP + k];
+    }
+  } else {
+    for (int e = tid; e < kLB * 64; e += kThreads) {
+      const int qq = e & 63, k = e >> 6;
+      if (k < kb && qq < cnt) W[(size_t)(k0 + k) * ldw + base + qq] = X[qq * kTrsmXP + k];
     }
   }
 }
 
-// ------------------------------------------------- TRSM with an inverse
-// side 0 (left):   W[k0:k0+kb, c] = Dinv * W[k0:k0+kb, c]      for c in [lo, hi)
-// side 1 (right):  W[r, k0:k0+kb] = W[r, k0:k0+kb] * Dinv^T    for r in [lo, hi)
-// One CTA per 64 columns (left) or 64 rows (right).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_trsm_inv(T* __restrict__ W, int ldw, int k0, int kb, int lo, int hi,
-                                                      const T* __restrict__ Dinv, int side) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  T* D = reinterpret_cast<T*>(smem);  // kLB x kLB, column-major, ld kLB + 1
-  T* Tl = D + kLB * (kLB + 1);         // 128 x 64 tile, ld 129 (left: [k][c]; right: [k][r])
-  const int base = lo + blockIdx.x * 64;
-  if (base >= hi) return;
-  const int cnt = min(64, hi - base);
-  for (int e = threadIdx.x; e < kLB * kLB; e += kThreads) D[(e / kLB) * (kLB + 1) + (e % kLB)] = Dinv[e];
-  if (side == 0) {
-    for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
-      const int k = e & (kLB - 1), c = e >> 7;
-      Tl[c * (kLB + 1) + k] = (k < kb && c < cnt) ? W[(size_t)(base + c) * ldw + k0 + k] : T(0);
-    }
-  } else {
-    for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
-      const int r = e & 63, k = e >> 6;
-      Tl[r * (kLB + 1) + k] = (k < kb && r < cnt) ? W[(size_t)(k0 + k) * ldw + base + r] : T(0);
-    }
-  }
-  __syncthreads();
-  // output (i, c): left = sum_k D(i,k) T(k,c); right (r, j) = sum_k T(r,k) D(j,k)
-  for (int e = threadIdx.x; e < kLB * 64; e += kThreads) {
-    const int i = e & (kLB - 1), c = e >> 7;
-    if (i >= kb || c >= cnt) continue;
-    T acc = T(0);
-    const T* trow = Tl + c * (kLB + 1);
-#pragma unroll 8
-    for (int k = 0; k < kLB; ++k) acc += D[k * (kLB + 1) + i] * trow[k];
-    if (side == 0) W[(size_t)(base + c) * ldw + k0 + i] = acc;
-    else W[(size_t)(k0 + i) * ldw + base + c] = acc;
-  }
+constexpr size_t trsm_smem() {
+  return sizeof(T) * ((size_t)kLB * (kLB + 1) + 64 * kTrsmXP + kLB);
 }
 
 // ------------------------------------------------- LU panel (cooperative)
@@ -283,13 +281,18 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
     }
     __syncthreads();
     const T inv = T(1) / s_pv;
-    for (int i = tid; i < nr; i += kThreads) {
-      if (rlo + i <= c) continue;
-      T* row = S + i * (kLB + 1);
-      const T l = row[c] * inv;
-      row[c] = l;
-      for (int k = c + 1; k < kb; ++k) row[k] -= l * prow[k];
-    }
+    // multipliers of the rows below the pivot, then the rank-1 update spread
+    // over (row, column) pairs so that every thread has independent work
+    const int i0 = max(0, c + 1 - rlo);
+    for (int i = i0 + tid; i < nr; i += kThreads) S[i * (kLB + 1) + c] *= inv;
+    __syncthreads();
+    const int ncol = kb - c - 1, nrow = nr - i0;
+    if (ncol > 0 && nrow > 0)
+      for (int e = tid; e < nrow * ncol; e += kThreads) {
+        const int i = i0 + e / ncol, k = c + 1 + e % ncol;
+        T* row = S + i * (kLB + 1);
+        row[k] -= row[c] * prow[k];
+      }
     __syncthreads();
   }
   for (int c = w; c < kb; c += kWarps)
@@ -357,81 +360,220 @@ __global__ void __launch_bounds__(kThreads) k_gemm_dmma(double* __restrict__ C, 
     }
     __syncthreads();
   }
+  // epilogue: all 16 loads of C first, then the stores
+  double cv[2][4][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a) {
-    const int r = m0 + wr + a * 8 + g;
-    if (r >= M) continue;
+  for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int c = n0 + wc + q * 8 + 2 * t + h;
-        if (c < N) C[(size_t)c * ldc + r] -= acc[a][q][h];
+        const int r = m0 + wr + a * 8 + g, c = n0 + wc + q * 8 + 2 * t + h;
+        cv[a][q][h] = (r < M && c < N) ? C[(size_t)c * ldc + r] : 0.0;
       }
-  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = m0 + wr + a * 8 + g, c = n0 + wc + q * 8 + 2 * t + h;
+        if (r < M && c < N) C[(size_t)c * ldc + r] = cv[a][q][h] - acc[a][q][h];
+      }
 }
 
-// --------------------------------------- blocked triangular solve steps
-// Diagonal block: x[b0:b0+bs, cols] <- inv(E_bb) x, E = trans ? M^T : M, by
-// substitution (cta_tri_solve) on an 8-column chunk per CTA.
-template <typename T, typename V>
-__global__ void __launch_bounds__(kThreads) k_tri_diag(const T* __restrict__ M, int ldm, int b0, int bs, int lower,
-                                                      int trans, int unit, V* x, int ldx, int nrhs) {
-  __shared__ V xs[kLB * 8];
-  const int c0 = blockIdx.x * 8, nc = min(8, nrhs - c0);
-  if (nc <= 0) return;
-  for (int e = threadIdx.x; e < kLB * 8; e += kThreads) {
-    const int r = e & (kLB - 1), c = e >> 7;
-    xs[e] = (r < bs && c < nc) ? x[(size_t)(c0 + c) * ldx + b0 + r] : V(0);
-  }
-  __syncthreads();
-  cta_tri_solve<T, V>(M + (size_t)b0 * ldm + b0, ldm, bs, lower != 0, trans != 0, unit != 0, xs, kLB, nc);
-  for (int e = threadIdx.x; e < kLB * 8; e += kThreads) {
-    const int r = e & (kLB - 1), c = e >> 7;
-    if (r < bs && c < nc) x[(size_t)(c0 + c) * ldx + b0 + r] = xs[e];
-  }
-}
+// ------------------------------------------- wavefront triangular solve
+// op(T) x = b for a triangular T (Sec. 2.2, Eq. 3 by BW-row blocks), one
+// launch for the whole solve.  Work items are (right-hand-side chunk of 8,
+// block row in solve order); CTA c takes items c, c+G, ... in order.  The
+// item for block row o accumulates -op(T)(o, p) x_p for every earlier block
+// p as soon as p's flag is set, then solves its diagonal block by warp
+// substitution (no inverse: FP64-stable), stores x_o and sets its flag.
+// The tiles of T do not depend on any flag: each is copied into shared
+// memory with cp.async one pair ahead (double buffer), so only x_p waits.
+// Every CTA is co-resident (cooperative launch) and an item waits only on
+// items of lower index, so the lowest unfinished item can always proceed.
+// Waits are bounded: on expiry the kernel sets *err and returns.
+constexpr int kWaveNR = 8;
 
-// Update: x[r, c] -= sum_{j < bs} E(r, b0 + j) x[b0 + j, c] for r in [rlo, rhi).
-// CTA tile: 64 rows x 16 right-hand sides; E tile and x block in shared memory.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_el(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// block width of the solve: 128 rows for FP32 factors, 64 for FP64 (two
+// tiles of BW x (BW+1) elements in shared memory either way)
+template <typename T>
+struct WaveBW {
+  static constexpr int value = sizeof(T) == 4 ? 128 : 64;
+};
+
 template <typename T, typename V>
-__global__ void __launch_bounds__(kThreads) k_tri_update(const T* __restrict__ M, int ldm, int b0, int bs, int rlo,
-                                                        int rhi, int trans, V* x, int ldx, int nrhs) {
+__global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__ M, int ldm, int n, int lower, int trans,
+                                                       int unit, V* x, int ldx, int nrhs, int* flags, int* err) {
+  constexpr int BW = WaveBW<T>::value;
+  constexpr int P = kThreads / BW;          // thread parts per row
+  constexpr int NQ = kWaveNR / P;           // right-hand sides per thread (multi mode)
   extern __shared__ __align__(16) unsigned char smem[];
-  V(*Es)[kLB + 1] = reinterpret_cast<V(*)[kLB + 1]>(smem);                         // [64][kLB+1]
-  V(*xb)[kLB + 1] = reinterpret_cast<V(*)[kLB + 1]>(smem + sizeof(V) * 64 * (kLB + 1));  // [16][kLB+1]
-  const int r0 = rlo + blockIdx.x * 64, c0 = blockIdx.y * 16;
-  if (r0 >= rhi) return;
-  const int nrow = min(64, rhi - r0), nc = min(16, nrhs - c0);
-  if (!trans) {  // E(r, j) = M[j * ldm + r]: lanes over r
-    for (int e = threadIdx.x; e < 64 * kLB; e += kThreads) {
-      const int r = e & 63, j = e >> 6;
-      Es[r][j] = (r < nrow && j < bs) ? (V)M[(size_t)(b0 + j) * ldm + r0 + r] : V(0);
-    }
-  } else {  // E(r, j) = M[r * ldm + j]: lanes over j
-    for (int e = threadIdx.x; e < 64 * kLB; e += kThreads) {
-      const int j = e & (kLB - 1), r = e >> 7;
-      Es[r][j] = (r < nrow && j < bs) ? (V)M[(size_t)(r0 + r) * ldm + b0 + j] : V(0);
-    }
-  }
-  for (int e = threadIdx.x; e < 16 * kLB; e += kThreads) {
-    const int j = e & (kLB - 1), c = e >> 7;
-    xb[c][j] = (j < bs && c < nc) ? x[(size_t)(c0 + c) * ldx + b0 + j] : V(0);
-  }
+  T(*tile)[BW][BW + 1] = reinterpret_cast<T(*)[BW][BW + 1]>(smem);  // [2][col][row]
+  V(*xs)[BW] = reinterpret_cast<V(*)[BW]>(smem + sizeof(T) * 2 * BW * (BW + 1));  // [NR][BW]
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const bool elower = (lower != 0) != (trans != 0);
+  const int nblk = (n + BW - 1) / BW;
+  const int nchunk = (nrhs + kWaveNR - 1) / kWaveNR;
+  const int items = nblk * nchunk;
+  const int r = tid % BW, part = tid / BW;
+  if (tid == 0) s_ok = 1;
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 16; e += kThreads) {
-    const int r = e & 63, c = e >> 6;
-    if (r >= nrow || c >= nc) continue;
-    V acc = V(0);
+  // copy the tile of M holding op(T)(block bi, block bj) into buffer buf
+  auto issue = [&](int buf, int bi, int bj) {
+    const int col0 = (trans ? bi : bj) * BW, row0 = (trans ? bj : bi) * BW;
+    const int nc_ = min(BW, n - col0), nr_ = min(BW, n - row0);
+    for (int e = tid; e < BW * BW; e += kThreads) {
+      const int c = e / BW, rr = e % BW;
+      T* dst = &tile[buf][c][rr];
+      if (c < nc_ && rr < nr_) cp_async_el<sizeof(T)>(dst, M + (size_t)(col0 + c) * ldm + row0 + rr);
+      else *dst = T(0);
+    }
+    cp_async_commit();
+  };
+  // element (i, j) of op(T)(bi, bj) in buffer buf
+  auto E = [&](int buf, int i, int j) -> V { return trans ? (V)tile[buf][i][j] : (V)tile[buf][j][i]; };
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int chunk = it / nblk, o = it - chunk * nblk;
+    const int c0 = chunk * kWaveNR, nc = min(kWaveNR, nrhs - c0);
+    const bool single = nc == 1;
+    const int bo = elower ? o : nblk - 1 - o;
+    const int r0 = bo * BW, bs = min(BW, n - r0);
+    V acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int c = part + P * q;
+      const bool on = single ? (q == 0 && part == 0) : (c < nc);
+      acc[q] = (on && r < bs) ? x[(size_t)(c0 + (single ? 0 : c)) * ldx + r0 + r] : V(0);
+    }
+    // first tile: pair (o, 0), or the diagonal block when o == 0
+    issue(0, bo, o > 0 ? (elower ? 0 : nblk - 1) : bo);
+    for (int p = 0; p < o; ++p) {
+      const int bp = elower ? p : nblk - 1 - p;
+      const int buf = p & 1;
+      // prefetch the next pair's tile (or the diagonal block) meanwhile
+      if (p + 1 < o) issue(buf ^ 1, bo, elower ? p + 1 : nblk - 2 - p);
+      else issue(buf ^ 1, bo, bo);
+      if (tid == 0) {
+        const int* f = flags + chunk * nblk + p;
+        long long spins = 0;
+        while (ld_acquire(f) == 0) {
+          if (++spins > 100000000ll) {
+            s_ok = 0;
+            atomicExch(err, 1);
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      if (!s_ok) {
+        cp_async_wait0();
+        return;
+      }
+      const int p0 = bp * BW, ps = min(BW, n - p0);
+      for (int e = tid; e < kWaveNR * BW; e += kThreads) {
+        const int j = e % BW, c = e / BW;
+        xs[c][j] = (j < ps && c < nc) ? __ldcg(x + (size_t)(c0 + c) * ldx + p0 + j) : V(0);
+      }
+      cp_async_wait1();
+      __syncthreads();
+      if (single) {  // one right-hand side: the parts split the j range
+        const int j0 = part * (BW / P);
 #pragma unroll 8
-    for (int j = 0; j < kLB; ++j) acc += Es[r][j] * xb[c][j];
-    x[(size_t)(c0 + c) * ldx + r0 + r] -= acc;
+        for (int j = j0; j < j0 + BW / P; ++j) acc[0] -= E(buf, r, j) * xs[0][j];
+      } else {
+#pragma unroll 4
+        for (int j = 0; j < BW; ++j) {
+          const V e = E(buf, r, j);
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) acc[q] -= e * xs[part + P * q][j];
+        }
+      }
+      __syncthreads();
+    }
+    cp_async_wait0();
+    __syncthreads();  // every thread's copies of the diagonal tile have landed
+    const int dbuf = o & 1;
+    // right-hand side of the diagonal block into xs
+    if (single) {
+      xs[part][r] = acc[0];
+      __syncthreads();
+      if (part == 0) {
+        V t = xs[0][r];
+#pragma unroll
+        for (int k = 1; k < P; ++k) t += xs[k][r];
+        xs[0][r] = t;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) xs[part + P * q][r] = acc[q];
+    }
+    // reciprocals of the diagonal (one division per row, off the chain)
+    __shared__ V s_rinv[BW];
+    for (int i = tid; i < BW; i += kThreads) s_rinv[i] = (unit || i >= bs) ? V(1) : V(1) / E(dbuf, i, i);
+    __syncthreads();
+    // diagonal block: warp w substitutes for right-hand side w
+    if (w < nc) {
+      constexpr int NV = (BW + 31) / 32;
+      V v[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) v[k] = (k * 32 + lane < BW) ? xs[w][k * 32 + lane] : V(0);
+      // register kk of the lanes holds rows 32kk..32kk+31: the outer loop
+      // index names the register statically
+#pragma unroll
+      for (int kq = 0; kq < NV; ++kq) {
+        const int kk = elower ? kq : NV - 1 - kq;
+        for (int jq = 0; jq < 32; ++jq) {
+          const int jj = elower ? jq : 31 - jq;
+          const int j = kk * 32 + jj;
+          if (j >= bs) continue;
+          const V vk = elower ? v[kq] : v[NV - 1 - kq];  // static register either way
+          const V vj = __shfl_sync(0xffffffffu, vk, jj) * s_rinv[j];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            const int i = k * 32 + lane;
+            const bool below = elower ? i > j : i < j;
+            const V upd = v[k] - E(dbuf, i < BW ? i : 0, j) * vj;
+            v[k] = (i == j) ? vj : ((i < bs && below) ? upd : v[k]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        const int i = k * 32 + lane;
+        if (i < bs) x[(size_t)(c0 + w) * ldx + r0 + i] = v[k];
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release(flags + it, 1);
   }
 }
 
 // ------------------------------------------------------ FP64 residual
-// R = B - A X (FP64), one warp per 8-row group, all right-hand sides in
-// chunks of 8 on mma.sync f64 (A fragment loaded once per chunk set).
+// R = B - A X (FP64), one warp per 8-row group (two warps per CTA, so the
+// row groups spread over every SM), all right-hand sides in chunks of 8 on
+// mma.sync f64 (A fragment loaded once per chunk set).
 // rmax[c] (as bits of a non-negative double) <- max |R(:, c)|.
 __global__ void __launch_bounds__(kThreads) k_residual_large(const double* __restrict__ A, int n,
                                                             const double* __restrict__ B, const double* __restrict__ X,
@@ -440,7 +582,8 @@ __global__ void __launch_bounds__(kThreads) k_residual_large(const double* __res
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
   const int nchunk = (nrhs + 7) / 8;
-  for (int r0 = (blockIdx.x * kWarps + w) * 8; r0 < n; r0 += gridDim.x * kWarps * 8) {
+  const int nw = blockDim.x >> 5;
+  for (int r0 = (blockIdx.x * nw + w) * 8; r0 < n; r0 += gridDim.x * nw * 8) {
     for (int cc = 0; cc < nchunk; cc += 8) {  // up to 64 right-hand sides per pass
       double acc[8][2];
 #pragma unroll
@@ -620,6 +763,20 @@ struct Arena {
     if (_e != cudaSuccess) return ASOLVE_E_CUDA;    \
   } while (0)
 
+// Scratch of the wavefront triangular solve: one flag per work item.
+struct WaveBuf {
+  int* flags;
+  int* err;
+  int cap;  // flags available
+  int grid; // co-resident CTAs
+};
+
+template <typename T, typename V>
+constexpr size_t wave_smem() {
+  return sizeof(T) * 2 * (size_t)WaveBW<T>::value * (WaveBW<T>::value + 1) +
+         sizeof(V) * (size_t)kWaveNR * WaveBW<T>::value;
+}
+
 template <typename T>
 struct Fac {  // a factorisation of the large path and its scratch
   T* W;
@@ -630,36 +787,33 @@ struct Fac {  // a factorisation of the large path and its scratch
   int* fail;     // device
   PanelBuf pb;
   size_t panel_smem;
+  WaveBuf wb;
 };
 
 template <typename T>
 int tri_solve_large(const T* M, int ldm, int n, bool lower, bool trans, bool unit, void* xv, int nrhs,
-                    bool vfloat, cudaStream_t st) {
-  const bool elower = (lower != trans);
-  const int nblk = (n + kLB - 1) / kLB;
-  for (int bi = 0; bi < nblk; ++bi) {
-    const int blk = elower ? bi : nblk - 1 - bi;
-    const int b0 = blk * kLB, bs = std::min(kLB, n - b0);
-    const int rlo = elower ? b0 + bs : 0, rhi = elower ? n : b0;
-    if (vfloat) {
-      float* x = static_cast<float*>(xv);
-      k_tri_diag<T, float><<<(nrhs + 7) / 8, kThreads, 0, st>>>(M, ldm, b0, bs, lower, trans, unit, x, n, nrhs);
-      if (rhi > rlo) {
-        dim3 g((rhi - rlo + 63) / 64, (nrhs + 15) / 16);
-        k_tri_update<T, float><<<g, kThreads, sizeof(float) * 80 * (kLB + 1), st>>>(M, ldm, b0, bs, rlo, rhi, trans, x,
-                                                                                   n, nrhs);
-      }
-    } else {
-      double* x = static_cast<double*>(xv);
-      k_tri_diag<T, double><<<(nrhs + 7) / 8, kThreads, 0, st>>>(M, ldm, b0, bs, lower, trans, unit, x, n, nrhs);
-      if (rhi > rlo) {
-        dim3 g((rhi - rlo + 63) / 64, (nrhs + 15) / 16);
-        k_tri_update<T, double><<<g, kThreads, sizeof(double) * 80 * (kLB + 1), st>>>(M, ldm, b0, bs, rlo, rhi, trans,
-                                                                                     x, n, nrhs);
-      }
-    }
+                    bool vfloat, const WaveBuf& wb, cudaStream_t st) {
+  const int nblk = (n + WaveBW<T>::value - 1) / WaveBW<T>::value;
+  const int items = nblk * ((nrhs + kWaveNR - 1) / kWaveNR);
+  if (items > wb.cap) return ASOLVE_E_NOMEM;
+  LCK(cudaMemsetAsync(wb.flags, 0, sizeof(int) * (size_t)items, st));
+  int G = std::min(wb.grid, items);
+  int lw = lower, tw = trans, uw = unit, ld = ldm, nn = n, nr = nrhs, ldx = n;
+  int* fl = wb.flags;
+  int* er = wb.err;
+  const T* Mp = M;
+  if (vfloat) {
+    float* x = static_cast<float*>(xv);
+    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er};
+    LCK(cudaLaunchCooperativeKernel((void*)k_trsv_wave<T, float>, dim3(G), dim3(kThreads), args,
+                                    wave_smem<T, float>(), st));
+  } else {
+    double* x = static_cast<double*>(xv);
+    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er};
+    LCK(cudaLaunchCooperativeKernel((void*)k_trsv_wave<T, double>, dim3(G), dim3(kThreads), args,
+                                    wave_smem<T, double>(), st));
   }
-  return cudaGetLastError() == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
+  return ASOLVE_OK;
 }
 
 template <typename T, typename V>
@@ -670,21 +824,21 @@ int apply_large(const Fac<T>& f, bool lu, int n, V* x, int nrhs, bool trans, V* 
     if (!trans) {
       k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 0);
       LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
-      int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, true, x, nrhs, vf, st);
+      int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, true, x, nrhs, vf, f.wb, st);
       if (rc) return rc;
-      return tri_solve_large<T>(f.W, f.ldw, n, false, false, false, x, nrhs, vf, st);
+      return tri_solve_large<T>(f.W, f.ldw, n, false, false, false, x, nrhs, vf, f.wb, st);
     }
-    int rc = tri_solve_large<T>(f.W, f.ldw, n, false, true, false, x, nrhs, vf, st);
+    int rc = tri_solve_large<T>(f.W, f.ldw, n, false, true, false, x, nrhs, vf, f.wb, st);
     if (rc) return rc;
-    rc = tri_solve_large<T>(f.W, f.ldw, n, true, true, true, x, nrhs, vf, st);
+    rc = tri_solve_large<T>(f.W, f.ldw, n, true, true, true, x, nrhs, vf, f.wb, st);
     if (rc) return rc;
     k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 1);
     LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
     return ASOLVE_OK;
   }
-  int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, false, x, nrhs, vf, st);
+  int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, false, x, nrhs, vf, f.wb, st);
   if (rc) return rc;
-  return tri_solve_large<T>(f.W, f.ldw, n, true, true, false, x, nrhs, vf, st);
+  return tri_solve_large<T>(f.W, f.ldw, n, true, true, false, x, nrhs, vf, f.wb, st);
 }
 
 template <typename T>
@@ -710,16 +864,13 @@ template <typename T>
 int set_large_attrs() {
   static bool done = false;
   if (done) return ASOLVE_OK;
-  LCK(cudaFuncSetAttribute(k_tri_block_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(T) * kLB * (kLB + 1))));
-  LCK(cudaFuncSetAttribute(k_trsm_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(T) * (kLB + 64) * (kLB + 1))));
+  LCK(cudaFuncSetAttribute(k_trsm_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
   // the panel kernel also has a little static shared memory
   LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
-  LCK(cudaFuncSetAttribute(k_tri_update<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(float) * 80 * (kLB + 1))));
-  LCK(cudaFuncSetAttribute(k_tri_update<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * 80 * (kLB + 1))));
+  LCK(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)wave_smem<T, float>()));
+  LCK(cudaFuncSetAttribute(k_trsv_wave<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)wave_smem<T, double>()));
   LCK(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
   done = true;
   return ASOLVE_OK;
@@ -736,9 +887,7 @@ int chol_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     k_chol_diag<T><<<1, kThreads, dsm, st>>>(f.W, f.ldw, k0, kb, nb, f.fail);
     const int rest = n - k0 - kb;
     if (rest > 0) {
-      k_tri_block_inv<T><<<1, kLB, sizeof(T) * kLB * (kLB + 1), st>>>(f.W, f.ldw, k0, kb, 1, 0, f.Dtmp);
-      k_trsm_inv<T><<<(rest + 63) / 64, kThreads, sizeof(T) * (kLB + 64) * (kLB + 1), st>>>(
-          f.W, f.ldw, k0, kb, k0 + kb, n, f.Dtmp, 1);
+      k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 1, 0);
       T* L21 = f.W + (size_t)k0 * f.ldw + k0 + kb;
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, L21, f.ldw, L21, f.ldw, rest, rest, kb,
                          true, true, f.fail + 1, st));
@@ -773,9 +922,7 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     k_swap_rows<T><<<(n + 255) / 256, 256, 0, st>>>(f.W, f.ldw, n, k0, kb, f.piv);
     const int rest = n - k0 - kb;
     if (rest > 0) {
-      k_tri_block_inv<T><<<1, kLB, sizeof(T) * kLB * (kLB + 1), st>>>(f.W, f.ldw, k0, kb, 1, 1, f.Dtmp);
-      k_trsm_inv<T><<<(rest + 63) / 64, kThreads, sizeof(T) * (kLB + 64) * (kLB + 1), st>>>(
-          f.W, f.ldw, k0, kb, k0 + kb, n, f.Dtmp, 0);
+      k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 0, 1);
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, f.W + (size_t)k0 * f.ldw + k0 + kb,
                          f.ldw, f.W + (size_t)(k0 + kb) * f.ldw + k0, f.ldw, rest, rest, kb, false, false,
                          f.fail + 1, st));
@@ -874,6 +1021,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += 4 * sizeof(double) * (size_t)n + 512;           // estimator vectors
   b += 2 * sizeof(double) * 1024 * (kLB + 4) + 2 * sizeof(double) * kLB + 1024;  // panel buffers (G <= 1024)
   b += scan_large_workspace(n) + 4096;
+  b += sizeof(int) * (size_t)(((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR)) + 1024;  // wave flags
   return b + (1 << 20);
 }
 
@@ -892,7 +1040,19 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   ScanRes* dsr = static_cast<ScanRes*>(ar.take(sizeof(ScanRes)));
   double* dscal = static_cast<double*>(ar.take(sizeof(double) * 8));
   int* dint = static_cast<int*>(ar.take(sizeof(int) * 8));
-  if (!sws || !dsr || !dscal || !dint) return ASOLVE_E_NOMEM;
+  const int wcap = ((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR);
+  int* wflags = static_cast<int*>(ar.take(sizeof(int) * (size_t)wcap));
+  int* werr = static_cast<int*>(ar.take(sizeof(int) * 4));
+  if (!sws || !dsr || !dscal || !dint || !wflags || !werr) return ASOLVE_E_NOMEM;
+  LCK(cudaMemsetAsync(werr, 0, sizeof(int) * 4, st));
+  const WaveBuf wb{wflags, werr, wcap, a.num_sms};
+  // a device-side wait of a triangular solve gave up: the result is not valid
+  auto wave_failed = [&]() -> bool {
+    int h = 0;
+    if (cudaMemcpyAsync(&h, werr, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return true;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return true;
+    return h != 0;
+  };
   LCK(launch_scan_large(a.A, n, a.B, (int64_t)n * nrhs, a.band_frac, a.sympd_tol, sws, dsr, a.num_sms, st));
   ScanRes sr;
   LCK(cudaMemcpyAsync(&sr, dsr, sizeof(sr), cudaMemcpyDeviceToHost, st));
@@ -903,7 +1063,25 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (sr.flags & (SF_NONFINITE | SF_B_NONFINITE)) return info->status = ASOLVE_E_NONFINITE;
   if (a.flags & ASOLVE_FORCE_SVD) return info->status = ASOLVE_E_UNSUPPORTED;
   int cls = (a.flags & ASOLVE_FORCE_LU) ? ASOLVE_CLS_GENERAL : sr.cls;
-  if (cls == ASOLVE_CLS_BANDED) return info->status = ASOLVE_E_UNSUPPORTED;  // dense input, band route: n <= 1024
+  bool band_as_dense = false;
+  if (cls == ASOLVE_CLS_BANDED) {
+    // Sec. 2.1 banded route.  Bandwidths beyond the band kernels' windows run
+    // the dense LU below, which makes the same pivot choices (the entries
+    // outside the band stay exactly zero), and report the banded route.
+    if (band_window_fits(sr.kl, sr.ku)) {
+      const size_t need = band_ws_bytes(n, sr.kl, sr.ku, nrhs);
+      void* bws = ar.take(need);
+      if (!bws) return info->status = ASOLVE_E_NOMEM;
+      BandArgs ba{nullptr, 0, 0, 0, a.A, a.B, a.X, n, nrhs, a.flags, a.rcond_threshold, sr.kl, sr.ku,
+                  sr.norm1, sr.norminf, st};
+      const int brc = band_solve(ba, bws, need, info);
+      // no SVD fallback above n = 1024
+      if (brc == ASOLVE_PENDING) info->status = ASOLVE_E_UNSUPPORTED;
+      return info->status;
+    }
+    band_as_dense = true;
+    cls = ASOLVE_CLS_GENERAL;
+  }
   // dynamic shared memory limits of every kernel below (the triangular
   // route uses the FP64 kernels even in mixed precision)
   int arc = set_large_attrs<float>();
@@ -938,12 +1116,12 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         }
     }
     LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
-    int rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, st);
+    int rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, wb, st);
     if (rc) return rc;
     double rc_val = NAN;
     if (!no_rcond) {
       double est;
-      auto apply = [&](double* v, bool tr) { return tri_solve_large<double>(a.A, n, n, lower, tr, false, v, 1, false, st); };
+      auto apply = [&](double* v, bool tr) { return tri_solve_large<double>(a.A, n, n, lower, tr, false, v, 1, false, wb, st); };
       rc = est_large<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est);
       if (rc) return rc;
       rc_val = rcond_of(sr.norm1, est);
@@ -951,7 +1129,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     info->rcond = rc_val;
     if (a.flags & ASOLVE_BERR) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-      k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
       std::vector<unsigned long long> hm((size_t)3 * nrhs);
@@ -969,6 +1147,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       }
       info->berr = be;
     }
+    if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
     const bool poor = !no_rcond && !(rc_val >= a.rcond_threshold);
     info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
     return info->status;
@@ -994,7 +1173,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   // ---- mixed precision: FP32 factors, FP64 refinement
   if (a.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
-    Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0};
+    Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool try_chol = chol && attempt == 0;
       if (!chol && attempt == 1) break;
@@ -1040,7 +1219,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       bool ok = false;
       for (int it = 0;; ++it) {
         LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
-        k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+        k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
         k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
         LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
         LCK(cudaStreamSynchronize(st));
@@ -1067,11 +1246,13 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       LCK(cudaStreamSynchronize(st));
       if (ok) {
         info->route = try_chol ? ASOLVE_ROUTE_CHOL : (chol ? ASOLVE_ROUTE_CHOL_FAIL_LU : ASOLVE_ROUTE_LU);
+        if (band_as_dense) info->route = ASOLVE_ROUTE_BAND_LU;
         info->rcond = rcv;
         info->berr = berr;
         info->ir_iters = iters;
         info->precision = ASOLVE_PREC_MIXED;
         info->detail = detail;
+        if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
         return info->status = ASOLVE_OK;
       }
       detail |= 2;
@@ -1080,7 +1261,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   }
   // ---- FP64 path
   if ((rc = set_large_attrs<double>())) return rc;
-  Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0};
+  Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0, wb};
   info->precision = ASOLVE_PREC_FP64;
   info->detail = detail;
   bool lu = !chol;
@@ -1098,6 +1279,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     fcol = 0;
     if ((rc = lu_large<double>(f, n, a.num_sms, &fcol, st))) return rc;
   }
+  if (band_as_dense) info->route = ASOLVE_ROUTE_BAND_LU;
   if (fcol) {
     LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
     LCK(cudaStreamSynchronize(st));
@@ -1115,7 +1297,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   info->rcond = rcv;
   if (a.flags & ASOLVE_BERR) {
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-    k_residual_large<<<(n + 63) / 64, kThreads, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+    k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
     std::vector<unsigned long long> hm((size_t)3 * nrhs);
@@ -1134,6 +1316,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     info->berr = be;
   }
   LCK(cudaStreamSynchronize(st));
+  if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
   const bool poor = !no_rcond && !(rcv >= a.rcond_threshold);
   return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
 }
