@@ -56,6 +56,7 @@ UNIT = "solves/s"
 WORKLOAD = "batched-10000: n~U[16,512], nrhs~U[1,8], mix 40% general/25% spd/15% banded/15% tri/5% ill"
 BERR_BAR = 1e-13
 COUNT = 10000  # systems per GPU per step (--count overrides, for small profiling runs)
+TUNING = os.path.join(ROOT, "paper_2007_11208_gb300", "tuning.json")  # autotuner output, if present
 SEED = 1
 
 
@@ -274,7 +275,7 @@ def ours(args):
     flags = asolve.BERR
 
     def arm(precision, steps, warmup, profile=False):
-        ctx = asolve.Context(precision=precision)
+        ctx = asolve.Context(precision=precision, tuning=TUNING if os.path.exists(TUNING) else None)
         stream = torch.cuda.ExternalStream(ctx.stream)
         run_steps(ctx, pk, X, infos, flags, warmup, stream)
         if profile:
@@ -311,7 +312,8 @@ def ours(args):
         "data": "synthetic (seeded; shapes and distributions of the batched configuration)",
         "config": {"workload": WORKLOAD, "systems_per_gpu": COUNT, "global_batch": COUNT * world,
                    "parallelism": f"replicas x{world}", "l2": "inputs (7.2 GB/GPU) larger than L2",
-                   "precision": "mixed"},
+                   "precision": "mixed",
+                   "panel_widths": "autotuned (tuning.json)" if os.path.exists(TUNING) else "built-in rule"},
         "verified_per_step": ok, "verified_fraction": ok / COUNT,
         "fp64_path": {"value": fp64_value, "unit": UNIT, "ms_per_step": statistics.mean(t64),
                       "verified_per_step": ok64},

@@ -79,6 +79,10 @@ extern "C" {
 #define ASOLVE_SYNC          0x10u  /* synchronise the stream before returning */
 #define ASOLVE_HOST_BUFFERS  0x20u  /* A, B, X (and batched arrays) are host memory */
 #define ASOLVE_BERR          0x40u  /* FP64 path: also compute the backward error */
+#define ASOLVE_RESIDENT      0x80u  /* request server: keep A and its factorisation on the device;
+                                       a later resident request with the same A pointer (A
+                                       unchanged) solves with them (systems above n = 1024 or
+                                       8 right-hand sides) */
 
 typedef struct asolve_ctx asolve_ctx;
 
@@ -111,7 +115,8 @@ typedef struct {           /* 64 bytes, one per system */
   int64_t svd_rank;        /* singular values kept by the SVD solve; -1 if not used */
   int32_t precision;       /* ASOLVE_PREC_* the final answer came from */
   int32_t detail;          /* bit 0: FP32 factor rejected by the rcond gate,
-                              bit 1: refinement stalled, bit 2: FP32 Cholesky failed */
+                              bit 1: refinement stalled, bit 2: FP32 Cholesky failed,
+                              bit 3: factorisation reused from an earlier resident request */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */
@@ -137,13 +142,13 @@ typedef struct {           /* request-server counters (asolve_get_serve_stats) *
   int64_t failed;          /* finished with an error status (< 0) */
   int64_t rejected;        /* refused at submission: alone over the HBM budget */
   int64_t queued;          /* waiting for admission now */
-  int64_t rounds;          /* server rounds run */
+  int64_t rounds;          /* lane rounds: batches plus large solves */
   int64_t batches;         /* batched launches of small requests */
   int64_t large_solves;    /* large systems solved */
   size_t  budget;          /* the context's hbm_budget */
   size_t  charged_bytes;   /* bytes admitted and not yet released */
   size_t  peak_charged_bytes;
-  double  busy_ms;         /* host wall time the server spent inside rounds */
+  double  busy_ms;         /* wall time with at least one lane at work */
   double  wall_ms;         /* first submission to last completion */
 } asolve_serve_stats;
 
@@ -212,21 +217,25 @@ int asolve_solve_batched_ptrs(asolve_ctx* ctx, int64_t count, const int64_t* n,
 
 /* Request server with continuous batching (the paper has no counterpart:
  * it serves many asolve_solve calls, Sec. 2 per request, from one context).
- * asolve_submit queues one request and returns at once with a ticket; a
- * server thread, started by the first submission, admits queued requests in
- * arrival order while the device bytes they hold fit cfg.hbm_budget, solves
- * the admitted small ones (n <= 1024, nrhs <= 8, same solver flags) as one
- * class-routed batch and at most one larger one per round, and records each
- * result.  A, B, X: device pointers, or host pointers with
+ * asolve_submit queues one request and returns at once with a ticket.  The
+ * first submission starts two server lanes, each a host thread with its own
+ * stream: the batch lane solves all queued small requests (n <= 1024,
+ * nrhs <= 8, same solver flags) as one class-routed batch, the large lane
+ * the oldest larger request; the two overlap on the device, and requests
+ * that arrive meanwhile join the next batch.  A request is admitted only
+ * while the device bytes it holds fit cfg.hbm_budget with everything in
+ * flight.  A, B, X: device pointers, or host pointers with
  * ASOLVE_HOST_BUFFERS (the server stages them in device memory it charges
  * to the budget); they must stay valid, and A and B unchanged, until the
  * request completes.  Allowed flags: NO_APPROX, FORCE_LU, FORCE_SVD,
- * NO_RCOND, BERR, HOST_BUFFERS.  Errors: E_INVALID, E_UNSUPPORTED
+ * NO_RCOND, BERR, HOST_BUFFERS, RESIDENT (one large request's device block
+ * is kept, charged to the budget, until another resident request replaces
+ * it or the budget needs it).  Errors: E_INVALID, E_UNSUPPORTED
  * (n > 32768 or nrhs > 256), E_NOMEM (the request alone needs more than the
  * budget; no ticket is issued), E_CUDA.  n = 0 completes at once.
- * The server runs on its own stream and workspaces: synchronous calls on the
- * same context may run meanwhile.  asolve_destroy waits for every submitted
- * request to complete. */
+ * The server runs on its own streams and workspaces: synchronous calls on
+ * the same context may run meanwhile.  asolve_destroy waits for every
+ * submitted request to complete. */
 int asolve_submit(asolve_ctx* ctx, const double* A, const double* B, int64_t n, int64_t nrhs,
                   uint32_t flags, double* X, uint64_t* ticket);
 /* Wait up to wait_us microseconds (< 0: without limit, 0: do not wait) for
@@ -268,6 +277,16 @@ int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, voi
  * set to 1 if a device-side wait gave up.  Asynchronous on `stream`. */
 int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
                     int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream);
+
+/* Panel widths of the batched dense factorisations, one per size bucket
+ * (bucket i holds n in [32 i + 1, 32 i + 32]), as chosen by the autotuner
+ * (paper_2007_11208_gb300/autotune.py; the paper has no counterpart: it is
+ * a tuning knob of this implementation).  kind: 0 LU FP32, 1 Cholesky FP32,
+ * 2 LU FP64, 3 Cholesky FP64.  Each value is 0 (built-in rule) or 4, 8, 16,
+ * 32; a value wider than what fits the kernel's shared memory is narrowed.
+ * Buckets past `count` revert to the built-in rule.  Applies to calls made
+ * after it returns.  Errors: E_INVALID. */
+int asolve_set_panel_widths(asolve_ctx* ctx, int kind, const int32_t* nb, int count);
 
 /* Per-kernel timing with CUDA events on the context stream (off by default). */
 int asolve_set_profiling(asolve_ctx* ctx, int on);

@@ -23,8 +23,8 @@ CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
 (ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
  ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD) = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
-NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND, SYNC, HOST_BUFFERS, BERR = (
-    0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40)
+NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND, SYNC, HOST_BUFFERS, BERR, RESIDENT = (
+    0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80)
 
 
 class Config(C.Structure):
@@ -77,7 +77,7 @@ EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve
            "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
            "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc",
            "asolve_gemm_sub", "asolve_solve_batched_ptrs", "asolve_submit", "asolve_poll",
-           "asolve_get_serve_stats")
+           "asolve_get_serve_stats", "asolve_set_panel_widths")
 
 
 def lib():
@@ -111,6 +111,7 @@ def lib():
     L.asolve_submit.argtypes = [vp, vp, vp, i64, i64, u32, vp, P(C.c_uint64)]
     L.asolve_poll.argtypes = [vp, C.c_uint64, i64, P(Info), P(C.c_double)]
     L.asolve_get_serve_stats.argtypes = [vp, P(ServeStats)]
+    L.asolve_set_panel_widths.argtypes = [vp, i32, vp, i32]
     for f in EXPORTS:
         if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
             getattr(L, f).restype = i32
@@ -153,12 +154,29 @@ def infos_from_tensor(t: torch.Tensor) -> list:
 class Context:
     """Owns an asolve_ctx (one CUDA stream, workspaces, captured graphs)."""
 
-    def __init__(self, **cfg):
+    def __init__(self, tuning=None, **cfg):
+        """tuning: path of a panel-width table written by autotune.py (optional)."""
         self._h = C.c_void_p()
         c = default_config(**cfg)
         rc = lib().asolve_create(C.byref(self._h), C.byref(c))
         if rc != OK:
             raise RuntimeError(f"asolve_create: {strerror(rc)}")
+        if tuning is not None:
+            self.load_tuning(tuning)
+
+    def set_panel_widths(self, kind: int, widths) -> int:
+        arr = (C.c_int32 * len(widths))(*[int(x) for x in widths])
+        return lib().asolve_set_panel_widths(self._h, kind, C.cast(arr, C.c_void_p), len(widths))
+
+    def load_tuning(self, path: str):
+        import json
+        with open(path) as f:
+            t = json.load(f)
+        for kind, key in enumerate(("lu32", "chol32", "lu64", "chol64")):
+            if key in t.get("nb", {}):
+                rc = self.set_panel_widths(kind, t["nb"][key])
+                if rc != OK:
+                    raise RuntimeError(f"asolve_set_panel_widths: {strerror(rc)}")
 
     def close(self):
         if self._h:

@@ -29,20 +29,6 @@ cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64
                               double tol, void* ws, ScanRes* out, int num_sms, cudaStream_t st);
 cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
                            int K, int passes, int* err, cudaStream_t st, bool trans_b, bool lower);
-struct LargeArgs {
-  const double* A;
-  const double* B;
-  double* X;
-  int64_t n, nrhs;
-  uint32_t flags;
-  int precision;
-  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
-  int ir_max_iter;
-  int num_sms;
-  cudaStream_t st;
-};
-size_t large_ws_bytes(int64_t n, int64_t nrhs);
-int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
 void serve_shutdown(asolve_ctx* c);
 }  // namespace asv
 
@@ -102,6 +88,7 @@ struct asolve_ctx {
   DevBuf large;        // large-system / banded workspace
   DevBuf bandDense;    // dense copy of a band-stored matrix (SVD fallback)
   ScanRes* h_scan = nullptr;  // pinned
+  int8_t nb_tab[4][32] = {};  // tuned panel widths (0: built-in rule)
   // request server (created by the first asolve_submit)
   void* serve = nullptr;
   // profiling
@@ -301,6 +288,7 @@ static void fill_desc(asolve_ctx* c, BatchDesc* h, int64_t count, const int64_t*
   h->slot_base = (char*)c->slots.p;
   h->slot_bytes = (int64_t)c->slot_bytes;
   h->slot_count = c->slot_count;
+  memcpy(h->nb_tab, c->nb_tab, sizeof(h->nb_tab));
 }
 
 // Enqueue the pipeline kernels (used both for capture and for profiling).
@@ -480,7 +468,7 @@ extern "C" int asolve_solve(asolve_ctx* c, const double* A, const double* B, int
     CK(c->large.ensure(wsb));
     LargeArgs la{dA, dB, dX, n, nrhs, flags, c->cfg.precision, c->cfg.rcond_threshold, c->cfg.sympd_tol,
                  c->cfg.band_frac, c->cfg.ir_target_berr, c->cfg.ir_kappa_limit, c->cfg.ir_max_iter,
-                 c->num_sms, st};
+                 c->num_sms, st, nullptr};
     asolve_info li;
     const int rc = large_solve(la, c->large.p, c->large.bytes, &li);
     if (rc < 0 && rc != li.status) {  // an error before the solve produced a status
@@ -627,6 +615,14 @@ extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t ld
   cudaError_t e = launch_gemm_tc(C, (int)ldc, A, (int)lda, B, (int)ldb, (int)M, (int)N, (int)K, passes, err,
                                  (cudaStream_t)stream, false, false);
   return e == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
+}
+
+extern "C" int asolve_set_panel_widths(asolve_ctx* c, int kind, const int32_t* nb, int count) {
+  if (!c || kind < 0 || kind > 3 || count < 0 || count > 32 || (count > 0 && !nb)) return ASOLVE_E_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (!(nb[i] == 0 || nb[i] == 4 || nb[i] == 8 || nb[i] == 16 || nb[i] == 32)) return ASOLVE_E_INVALID;
+  for (int i = 0; i < 32; ++i) c->nb_tab[kind][i] = (int8_t)(i < count ? nb[i] : 0);
+  return ASOLVE_OK;
 }
 
 extern "C" int asolve_set_profiling(asolve_ctx* c, int on) {

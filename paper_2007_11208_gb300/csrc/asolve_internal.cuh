@@ -73,7 +73,42 @@ struct BatchDesc {
   int32_t slot_count;
   int32_t pad1;
   int32_t* err_flag;       // device-side error (e.g. a scratch slot too small)
+  // panel widths of the dense class kernels chosen by the autotuner:
+  // [LU FP32, Cholesky FP32, LU FP64, Cholesky FP64][(n - 1) / 32];
+  // 0 keeps the built-in rule
+  int8_t nb_tab[4][32];
 };
+
+// A dense route's factorisation kept for later solves with the same A
+// (request server, ASOLVE_RESIDENT).  Filled by large_solve after a dense
+// route succeeded; a later call with the same key solves with the kept
+// factor (which stays in the workspace it was computed in).
+struct LargeReuse {
+  int valid;
+  const double* A;       // key: the caller's A, its order and routing flags
+  int64_t n;
+  uint32_t flags;
+  int cls, route, precision, lu, detail;
+  int64_t kl, ku;
+  double rcond, norm1, norminf;
+};
+
+// One large dense system (large.cu).
+struct LargeArgs {
+  const double* A;
+  const double* B;
+  double* X;
+  int64_t n, nrhs;
+  uint32_t flags;
+  int precision;
+  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
+  int ir_max_iter;
+  int num_sms;
+  cudaStream_t st;
+  LargeReuse* reuse;       // optional
+};
+size_t large_ws_bytes(int64_t n, int64_t nrhs);
+int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
 
 // One system for the banded route (band_large.cu): band storage input
 // (AB, ldab, declared kld/kud) or a dense matrix A with its scan results.

@@ -180,12 +180,16 @@ __device__ __forceinline__ int next_item(const BatchDesc& d, int ctr, int* s_ite
 constexpr int kDenseSmem = 110 * 1024;
 
 // Panel width: the n x nb panel plus the 32 x 33 inverse and two 32 x 64
-// tiles must fit in kDenseSmem.
+// tiles must fit in kDenseSmem; within that, the autotuner's table may
+// choose a narrower panel per size bucket.
 template <typename T>
-__device__ __forceinline__ int pick_nb(int n) {
+__device__ __forceinline__ int pick_nb(int n, const BatchDesc& d, int kind) {
   const size_t extra = (32 * 33 + 8 + 32 * 65 + 8 + 32 * 64) * sizeof(T) + 64;
   int nb = 32;
   while (nb > 4 && (size_t)n * nb * sizeof(T) + extra > (size_t)kDenseSmem) nb >>= 1;
+  // a tuned width (a power of two) may only narrow the panel
+  const int t = d.nb_tab[kind + (sizeof(T) == 8 ? 2 : 0)][(n - 1) >> 5];
+  if (t >= 4 && t < nb) nb = t >= 16 ? 16 : (t >= 8 ? 8 : 4);
   return nb;
 }
 
@@ -327,7 +331,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   if (d.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
     float* W = reinterpret_cast<float*>(sl.W);
     copy_to_work<float>(A, n, W, ldw);
-    const int nb = pick_nb<float>(n);
+    const int nb = pick_nb<float>(n, d, KIND);
     int f = KIND == 0 ? cta_lu_factor<float>(W, ldw, n, sl.piv, reinterpret_cast<float*>(smem), nb)
                       : cta_chol_factor<float>(W, ldw, n, reinterpret_cast<float*>(smem), nb);
     if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);
@@ -386,7 +390,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   // ---- FP64 path
   double* W = reinterpret_cast<double*>(sl.W);
   copy_to_work<double>(A, n, W, ldw);
-  const int nb = pick_nb<double>(n);
+  const int nb = pick_nb<double>(n, d, KIND);
   int f = KIND == 0 ? cta_lu_factor<double>(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), nb)
                     : cta_chol_factor<double>(W, ldw, n, reinterpret_cast<double*>(smem), nb);
   if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);

@@ -152,17 +152,25 @@ __device__ __noinline__ void tile_gemm_sub<double>(double* C, int ldc, const dou
   const int kb4 = (kb + 3) & ~3;
   const int istart = lower_only ? (col_off / 64) * 64 : 0;
   for (int i0 = istart; i0 < m; i0 += 64) {
+    // the C tile is the accumulator's initial value: its 16 loads go out
+    // together, and the products are accumulated negated
     double acc[2][4][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b][0] = acc[a][b][1] = 0.0;
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = i0 + wr + a * 8 + g, c = wc + b * 8 + 2 * t + q;
+          acc[a][b][q] = (r < m && c < nc) ? C[(size_t)c * ldc + r] : 0.0;
+        }
+#pragma unroll 2
     for (int k = 0; k < kb4; k += 4) {
       double af[2], bf[4];
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int r = i0 + wr + a * 8 + g;
-        af[a] = (r < m && k + t < kb) ? As[(size_t)(k + t) * lda + r] : 0.0;
+        af[a] = (r < m && k + t < kb) ? -As[(size_t)(k + t) * lda + r] : 0.0;
       }
 #pragma unroll
       for (int b = 0; b < 4; ++b) bf[b] = (k + t < kb) ? Bt[(k + t) * 64 + wc + b * 8 + g] : 0.0;
@@ -180,7 +188,7 @@ __device__ __noinline__ void tile_gemm_sub<double>(double* C, int ldc, const dou
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int c = wc + b * 8 + 2 * t + q;
-          if (c < nc) C[(size_t)c * ldc + r] -= acc[a][b][q];
+          if (c < nc) C[(size_t)c * ldc + r] = acc[a][b][q];
         }
     }
   }
@@ -567,6 +575,8 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
         V acc[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = V(0);
+        // unrolled so that the loads of M (global memory) are in flight together
+#pragma unroll 8
         for (int j = 0; j < bs; ++j) {
           const V m = (V)M[(size_t)(b0 + j) * ldm + r];
 #pragma unroll
@@ -735,6 +745,7 @@ __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda,
     const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kRows; ++q) acc[q][0] = acc[q][1] = 0.0;
+#pragma unroll 4
     for (int j = 0; j < n; ++j) {
       const double x0 = Xs[j], x1 = (nrhs > 1) ? Xs[(size_t)n + j] : 0.0;
 #pragma unroll

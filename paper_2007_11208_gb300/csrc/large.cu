@@ -17,6 +17,7 @@
 // residual on mma.sync f64), the 1-norm condition estimate and the
 // per-column backward error are driven from the host.
 #include <cuda_runtime.h>
+#include <float.h>
 #include <math.h>
 #include <string.h>
 
@@ -286,13 +287,12 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
     const int i0 = max(0, c + 1 - rlo);
     for (int i = i0 + tid; i < nr; i += kThreads) S[i * (kLB + 1) + c] *= inv;
     __syncthreads();
-    const int ncol = kb - c - 1, nrow = nr - i0;
-    if (ncol > 0 && nrow > 0)
-      for (int e = tid; e < nrow * ncol; e += kThreads) {
-        const int i = i0 + e / ncol, k = c + 1 + e % ncol;
-        T* row = S + i * (kLB + 1);
-        row[k] -= row[c] * prow[k];
-      }
+    // one warp per row, lanes over the columns
+    for (int i = i0 + w; i < nr; i += kWarps) {
+      T* row = S + i * (kLB + 1);
+      const T l = row[c];
+      for (int k = c + 1 + lane; k < kb; k += 32) row[k] -= l * prow[k];
+    }
     __syncthreads();
   }
   for (int c = w; c < kb; c += kWarps)
@@ -315,55 +315,90 @@ __global__ void k_swap_rows(T* W, int ldw, int n, int k0, int kb, const int* __r
   }
 }
 
+template <int BYTES>
+__device__ __forceinline__ void cp_async_el(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+
 // ------------------------------------------- FP64 GEMM (mma.sync f64)
 // C (M x N) -= A (M x K) * B (K x N) (B transposed when TB); LO skips tiles
-// strictly above the diagonal.  64 x 64 tiles, K chunks of 16.
+// strictly above the diagonal.  CTA tile 128 x 64, eight warps of 32 x 32
+// (4 x 4 m8n8k4 tiles each), K steps of 16 double-buffered in shared memory
+// with cp.async so the global loads of step k+1 overlap the MMAs of step k.
+constexpr int kDmM = 128, kDmN = 64, kDmK = 16;
+constexpr int kDmPA = kDmM + 8, kDmPB = kDmN + 8;  // padded rows: the 4 k of a fragment hit other banks
+constexpr size_t kDmSmem = sizeof(double) * 2 * kDmK * (kDmPA + kDmPB);
+
 template <bool TB, bool LO>
 __global__ void __launch_bounds__(kThreads) k_gemm_dmma(double* __restrict__ C, int ldc, const double* __restrict__ A,
                                                        int lda, const double* __restrict__ B, int ldb, int M, int N,
                                                        int K) {
-  if (LO && blockIdx.y > blockIdx.x) return;
-  __shared__ double As[16][64 + 1];
-  __shared__ double Bs[16][64 + 1];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m0 = blockIdx.x * kDmM, n0 = blockIdx.y * kDmN;
+  if (LO && n0 >= m0 + kDmM) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double(*As)[kDmK][kDmPA] = reinterpret_cast<double(*)[kDmK][kDmPA]>(smem);
+  double(*Bs)[kDmK][kDmPB] = reinterpret_cast<double(*)[kDmK][kDmPB]>(smem + sizeof(double) * 2 * kDmK * kDmPA);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int wr = (w & 3) * 16, wc = (w >> 2) * 32;
-  const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
-  double acc[2][4][2];
+  const int wr = (w & 3) * 32, wc = (w >> 2) * 32;
+  auto load = [&](int buf, int k0) {
+    for (int e = tid; e < kDmK * kDmM; e += kThreads) {
+      const int r = e & (kDmM - 1), k = e >> 7;
+      double* dst = &As[buf][k][r];
+      if (m0 + r < M && k0 + k < K) cp_async_el<8>(dst, A + (size_t)(k0 + k) * lda + m0 + r);
+      else *dst = 0.0;
+    }
+    for (int e = tid; e < kDmK * kDmN; e += kThreads) {
+      int k, c;
+      if (TB) { c = e & (kDmN - 1); k = e >> 6; }
+      else { k = e & (kDmK - 1); c = e >> 4; }
+      double* dst = &Bs[buf][k][c];
+      if (n0 + c < N && k0 + k < K)
+        cp_async_el<8>(dst, TB ? B + (size_t)(k0 + k) * ldb + n0 + c : B + (size_t)(n0 + c) * ldb + k0 + k);
+      else *dst = 0.0;
+    }
+    cp_async_commit();
+  };
+  double acc[4][4][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[a][q][0] = acc[a][q][1] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
-      const int r = e & 63, k = e >> 6;
-      As[k][r] = (m0 + r < M && k0 + k < K) ? A[(size_t)(k0 + k) * lda + m0 + r] : 0.0;
-      if (TB) Bs[k][r] = (n0 + r < N && k0 + k < K) ? B[(size_t)(k0 + k) * ldb + n0 + r] : 0.0;
+  const int nk = (K + kDmK - 1) / kDmK;
+  if (nk > 0) load(0, 0);
+  for (int ks = 0; ks < nk; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < nk) {
+      load(buf ^ 1, (ks + 1) * kDmK);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
     }
-    if (!TB)
-      for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
-        const int k = e & 15, c = e >> 4;
-        Bs[k][c] = (n0 + c < N && k0 + k < K) ? B[(size_t)(n0 + c) * ldb + k0 + k] : 0.0;
-      }
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; kk += 4) {
-      double af[2], bf[4];
+    for (int kk = 0; kk < kDmK; kk += 4) {
+      double af[4], bf[4];
 #pragma unroll
-      for (int a = 0; a < 2; ++a) af[a] = As[kk + t][wr + a * 8 + g];
+      for (int a = 0; a < 4; ++a) af[a] = As[buf][kk + t][wr + a * 8 + g];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) bf[q] = Bs[kk + t][wc + q * 8 + g];
+      for (int q = 0; q < 4; ++q) bf[q] = Bs[buf][kk + t][wc + q * 8 + g];
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) dmma_8x8x4(acc[a][q][0], acc[a][q][1], af[a], bf[q]);
     }
     __syncthreads();
   }
-  // epilogue: all 16 loads of C first, then the stores
-  double cv[2][4][2];
+  // epilogue: all loads of C first, then the stores
+  double cv[4][4][2];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -372,7 +407,7 @@ __global__ void __launch_bounds__(kThreads) k_gemm_dmma(double* __restrict__ C, 
         cv[a][q][h] = (r < M && c < N) ? C[(size_t)c * ldc + r] : 0.0;
       }
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -404,16 +439,6 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-template <int BYTES>
-__device__ __forceinline__ void cp_async_el(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (BYTES == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // block width of the solve: 128 rows for FP32 factors, 64 for FP64 (two
 // tiles of BW x (BW+1) elements in shared memory either way)
 template <typename T>
@@ -731,18 +756,6 @@ size_t scan_large_workspace(int64_t n);
 cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64_t nb, double band_frac,
                               double tol, void* ws, ScanRes* out, int num_sms, cudaStream_t st);
 
-struct LargeArgs {
-  const double* A;
-  const double* B;
-  double* X;
-  int64_t n, nrhs;
-  uint32_t flags;
-  int precision;
-  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
-  int ir_max_iter;
-  int num_sms;
-  cudaStream_t st;
-};
 
 namespace {
 
@@ -852,11 +865,11 @@ cudaError_t gemm_update<float>(float* C, int ldc, const float* A, int lda, const
 template <>
 cudaError_t gemm_update<double>(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N,
                                 int K, bool tb, bool lower, int* err, cudaStream_t st) {
-  dim3 g((M + 63) / 64, (N + 63) / 64);
-  if (tb && lower) k_gemm_dmma<true, true><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
-  else if (tb) k_gemm_dmma<true, false><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
-  else if (lower) k_gemm_dmma<false, true><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
-  else k_gemm_dmma<false, false><<<g, kThreads, 0, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  dim3 g((M + kDmM - 1) / kDmM, (N + kDmN - 1) / kDmN);
+  if (tb && lower) k_gemm_dmma<true, true><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else if (tb) k_gemm_dmma<true, false><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else if (lower) k_gemm_dmma<false, true><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
+  else k_gemm_dmma<false, false><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
   return cudaGetLastError();
 }
 
@@ -865,6 +878,10 @@ int set_large_attrs() {
   static bool done = false;
   if (done) return ASOLVE_OK;
   LCK(cudaFuncSetAttribute(k_trsm_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
+  LCK(cudaFuncSetAttribute(k_gemm_dmma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  LCK(cudaFuncSetAttribute(k_gemm_dmma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  LCK(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  LCK(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   // the panel kernel also has a little static shared memory
   LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   LCK(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -905,9 +922,9 @@ int chol_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
 template <typename T>
 int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
   LCK(cudaMemsetAsync(f.fail, 0, sizeof(int) * 2, st));
-  const int G = num_sms;
   for (int k0 = 0; k0 < n; k0 += kLB) {
     const int kb = std::min(kLB, n - k0), m = n - k0;
+    const int G = num_sms;
     const int R = (m + G - 1) / G;
     const size_t psmem = sizeof(T) * ((size_t)R * (kLB + 1) + kLB) + 64;
     if (psmem > 226 * 1024) return ASOLVE_E_UNSUPPORTED;
@@ -1035,6 +1052,18 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   info->rcond = NAN;
   info->berr = NAN;
   info->svd_rank = -1;
+  // the factor block comes first, at offsets that depend on n only, so that a
+  // kept factorisation is found again by a later call with another nrhs
+  const int ldw = (n + 3) & ~3;
+  void* Wv = ar.take(sizeof(double) * (size_t)ldw * n);
+  int* piv = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
+  int* perm = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
+  if (!Wv || !piv || !perm) return ASOLVE_E_NOMEM;
+  LargeReuse* kept = a.reuse;
+  constexpr uint32_t kRouteFlags = ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_NO_APPROX;
+  const bool reuse_hit = kept && kept->valid && kept->A == a.A && kept->n == a.n &&
+                         kept->flags == (a.flags & kRouteFlags) && kept->precision >= 0;
+  if (kept && !reuse_hit) kept->valid = 0;
   // ---- scan (Sec. 2.1, 2.2, Fig. 4)
   void* sws = ar.take(scan_large_workspace(n));
   ScanRes* dsr = static_cast<ScanRes*>(ar.take(sizeof(ScanRes)));
@@ -1053,16 +1082,24 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if (cudaStreamSynchronize(st) != cudaSuccess) return true;
     return h != 0;
   };
-  LCK(launch_scan_large(a.A, n, a.B, (int64_t)n * nrhs, a.band_frac, a.sympd_tol, sws, dsr, a.num_sms, st));
-  ScanRes sr;
-  LCK(cudaMemcpyAsync(&sr, dsr, sizeof(sr), cudaMemcpyDeviceToHost, st));
-  LCK(cudaStreamSynchronize(st));
+  ScanRes sr{};
+  if (reuse_hit) {  // A is unchanged: its scan results come with the kept factor
+    sr.kl = (int)kept->kl;
+    sr.ku = (int)kept->ku;
+    sr.cls = ASOLVE_CLS_GENERAL;  // a dense route follows
+    sr.norm1 = kept->norm1;
+    sr.norminf = kept->norminf;
+  } else {
+    LCK(launch_scan_large(a.A, n, a.B, (int64_t)n * nrhs, a.band_frac, a.sympd_tol, sws, dsr, a.num_sms, st));
+    LCK(cudaMemcpyAsync(&sr, dsr, sizeof(sr), cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+  }
   info->cls = sr.cls;
   info->kl = sr.kl;
   info->ku = sr.ku;
   if (sr.flags & (SF_NONFINITE | SF_B_NONFINITE)) return info->status = ASOLVE_E_NONFINITE;
   if (a.flags & ASOLVE_FORCE_SVD) return info->status = ASOLVE_E_UNSUPPORTED;
-  int cls = (a.flags & ASOLVE_FORCE_LU) ? ASOLVE_CLS_GENERAL : sr.cls;
+  int cls = (a.flags & ASOLVE_FORCE_LU || reuse_hit) ? ASOLVE_CLS_GENERAL : sr.cls;
   bool band_as_dense = false;
   if (cls == ASOLVE_CLS_BANDED) {
     // Sec. 2.1 banded route.  Bandwidths beyond the band kernels' windows run
@@ -1088,7 +1125,6 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (!arc) arc = set_large_attrs<double>();
   if (arc) return info->status = arc;
   const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
-  const int ldw = (n + 3) & ~3;
   double* R = static_cast<double*>(ar.take(sizeof(double) * (size_t)n * nrhs));
   void* xs = ar.take(sizeof(double) * (size_t)n * nrhs);
   void* tmp = ar.take(sizeof(double) * (size_t)n * nrhs);
@@ -1153,8 +1189,6 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     return info->status;
   }
   // ---- dense routes: Cholesky (Sec. 2.3) or LU (Sec. 2.4)
-  int* piv = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
-  int* perm = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
   int* fail = static_cast<int*>(ar.take(sizeof(int) * 4));
   void* Dtmp = ar.take(sizeof(double) * kLB * kLB);
   void* pcand = ar.take(sizeof(double) * 2 * a.num_sms * 4);
@@ -1162,14 +1196,143 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   void* pdiag = ar.take(sizeof(double) * 2 * kLB);
   unsigned* pbar = static_cast<unsigned*>(ar.take(sizeof(unsigned) * 4));
   int* perr = static_cast<int*>(ar.take(sizeof(int) * 4));
-  void* Wv = ar.take(sizeof(double) * (size_t)ldw * n);
-  if (!piv || !perm || !fail || !Dtmp || !pcand || !prows || !pdiag || !pbar || !perr || !Wv) return ASOLVE_E_NOMEM;
+  if (!fail || !Dtmp || !pcand || !prows || !pdiag || !pbar || !perr) return ASOLVE_E_NOMEM;
   LCK(cudaMemsetAsync(perr, 0, sizeof(int) * 4, st));
   PanelBuf pb{pcand, prows, pdiag, pbar, perr};
   bool chol = (cls == ASOLVE_CLS_SYMPD);
   info->route = chol ? ASOLVE_ROUTE_CHOL : ASOLVE_ROUTE_LU;
   int detail = 0;
   int rc;
+  // refinement with FP32 factors: x0 = inv(A32) b; loop r = b - A x (FP64),
+  // x += inv(A32) r.  Returns 1 converged, 0 stalled, < 0 error.
+  auto mixed_ir = [&](Fac<float>& f, bool lu, int& iters, double& berr) -> int {
+    std::vector<unsigned long long> hm((size_t)3 * nrhs);
+    std::vector<double> scale((size_t)nrhs);
+    double* dscale = static_cast<double*>(ev);  // reuse (n >= nrhs)
+    LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+    LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    std::vector<double> bmax((size_t)nrhs);
+    for (int c = 0; c < nrhs; ++c) {
+      memcpy(&bmax[c], &hm[2 * nrhs + c], 8);
+      if (!(bmax[c] <= DBL_MAX)) return ASOLVE_E_NONFINITE;
+      scale[c] = bmax[c] > 0.0 ? bmax[c] : 1.0;
+    }
+    LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+    k_scale_down<float><<<1024, 256, 0, st>>>(a.B, n, nrhs, dscale, (float*)xs);
+    int r2 = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st);
+    if (r2) return r2;
+    k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 1);
+    double berr_prev = INFINITY;
+    berr = INFINITY;
+    iters = 0;
+    int ok = 0;
+    for (int it = 0;; ++it) {
+      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
+      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+      LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      berr = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        double rm, xm;
+        memcpy(&rm, &hm[c], 8);
+        memcpy(&xm, &hm[nrhs + c], 8);
+        const double den = sr.norminf * xm + bmax[c];
+        const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+        if (!(b1 <= berr)) berr = b1;
+        scale[c] = rm > 0.0 ? rm : 1.0;
+      }
+      const bool conv = berr <= a.ir_target_berr;
+      if (!conv && (it >= a.ir_max_iter || !(berr < 0.5 * berr_prev))) break;
+      berr_prev = berr;
+      LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
+      k_scale_down<float><<<1024, 256, 0, st>>>(R, n, nrhs, dscale, (float*)xs);
+      if ((r2 = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st))) return r2;
+      k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 0);
+      ++iters;
+      if (conv) { ok = 1; break; }
+    }
+    LCK(cudaStreamSynchronize(st));
+    return ok;
+  };
+  // the kept factorisation fills the fields of a later call's info
+  auto keep = [&](int precision, bool lu) {
+    if (!kept) return;
+    kept->valid = 1;
+    kept->A = a.A;
+    kept->n = a.n;
+    kept->flags = a.flags & kRouteFlags;
+    kept->cls = info->cls;
+    kept->route = info->route;
+    kept->precision = precision;
+    kept->lu = lu ? 1 : 0;
+    kept->detail = info->detail;
+    kept->kl = info->kl;
+    kept->ku = info->ku;
+    kept->rcond = info->rcond;
+    kept->norm1 = sr.norm1;
+    kept->norminf = sr.norminf;
+  };
+  if (reuse_hit) {
+    info->cls = kept->cls;
+    info->route = kept->route;
+    info->rcond = kept->rcond;
+    info->precision = kept->precision;
+    info->detail = kept->detail | 8;
+    if (kept->precision == ASOLVE_PREC_MIXED) {
+      if ((rc = set_large_attrs<float>())) return rc;
+      Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
+      int iters = 0;
+      double berr = NAN;
+      const int ok = mixed_ir(f, kept->lu != 0, iters, berr);
+      if (ok < 0) return info->status = ok;
+      if (ok == 1) {
+        info->berr = berr;
+        info->ir_iters = iters;
+        if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
+        return info->status = ASOLVE_OK;
+      }
+      kept->valid = 0;  // the kept factor does not refine this right-hand side: start over
+      return large_solve(a, ws, ws_bytes, info);
+    }
+    Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0, wb};
+    LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+    std::vector<unsigned long long> hb((size_t)3 * nrhs);
+    LCK(cudaMemcpyAsync(hb.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    for (int c = 0; c < nrhs; ++c) {
+      double bm;
+      memcpy(&bm, &hb[2 * nrhs + c], 8);
+      if (!(bm <= DBL_MAX)) return info->status = ASOLVE_E_NONFINITE;
+    }
+    LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+    if ((rc = apply_large<double, double>(f, kept->lu != 0, n, a.X, nrhs, false, (double*)tmp, st))) return rc;
+    if (a.flags & ASOLVE_BERR) {
+      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
+      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+      LCK(cudaMemcpyAsync(hb.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      double be = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        double rm, xm, bm;
+        memcpy(&rm, &hb[c], 8);
+        memcpy(&xm, &hb[nrhs + c], 8);
+        memcpy(&bm, &hb[2 * nrhs + c], 8);
+        const double den = sr.norminf * xm + bm;
+        const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+        if (!(b1 <= be)) be = b1;
+      }
+      info->berr = be;
+    }
+    LCK(cudaStreamSynchronize(st));
+    if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
+    const bool poor = !no_rcond && !(kept->rcond >= a.rcond_threshold);
+    return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
+  }
   // ---- mixed precision: FP32 factors, FP64 refinement
   if (a.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
@@ -1197,53 +1360,11 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         gate_ok = rcv >= 1.0 / a.ir_kappa_limit;
       }
       if (!gate_ok) { detail |= 1; break; }
-      // refinement: x0 = inv(A32) b; loop r = b - A x (FP64), x += inv(A32) r
-      std::vector<unsigned long long> hm((size_t)3 * nrhs);
-      std::vector<double> scale((size_t)nrhs);
-      double* dscale = static_cast<double*>(ev);  // reuse (n >= nrhs)
-      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
-      LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
-      LCK(cudaStreamSynchronize(st));
-      std::vector<double> bmax((size_t)nrhs);
-      for (int c = 0; c < nrhs; ++c) {
-        memcpy(&bmax[c], &hm[2 * nrhs + c], 8);
-        scale[c] = bmax[c] > 0.0 ? bmax[c] : 1.0;
-      }
-      LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-      k_scale_down<float><<<1024, 256, 0, st>>>(a.B, n, nrhs, dscale, (float*)xs);
-      if ((rc = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st))) return rc;
-      k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 1);
-      double berr_prev = INFINITY, berr = INFINITY;
       int iters = 0;
-      bool ok = false;
-      for (int it = 0;; ++it) {
-        LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
-        k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
-        k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
-        LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
-        LCK(cudaStreamSynchronize(st));
-        berr = 0.0;
-        for (int c = 0; c < nrhs; ++c) {
-          double rm, xm;
-          memcpy(&rm, &hm[c], 8);
-          memcpy(&xm, &hm[nrhs + c], 8);
-          const double den = sr.norminf * xm + bmax[c];
-          const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
-          if (!(b1 <= berr)) berr = b1;
-          scale[c] = rm > 0.0 ? rm : 1.0;
-        }
-        const bool conv = berr <= a.ir_target_berr;
-        if (!conv && (it >= a.ir_max_iter || !(berr < 0.5 * berr_prev))) break;
-        berr_prev = berr;
-        LCK(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, st));
-        k_scale_down<float><<<1024, 256, 0, st>>>(R, n, nrhs, dscale, (float*)xs);
-        if ((rc = apply_large<float, float>(f, lu, n, (float*)xs, nrhs, false, (float*)tmp, st))) return rc;
-        k_scale_add<float><<<1024, 256, 0, st>>>(a.X, n, nrhs, dscale, (float*)xs, 0);
-        ++iters;
-        if (conv) { ok = true; break; }
-      }
-      LCK(cudaStreamSynchronize(st));
+      double berr = NAN;
+      const int okc = mixed_ir(f, lu, iters, berr);
+      if (okc < 0) return info->status = okc;
+      const bool ok = okc == 1;
       if (ok) {
         info->route = try_chol ? ASOLVE_ROUTE_CHOL : (chol ? ASOLVE_ROUTE_CHOL_FAIL_LU : ASOLVE_ROUTE_LU);
         if (band_as_dense) info->route = ASOLVE_ROUTE_BAND_LU;
@@ -1253,6 +1374,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         info->precision = ASOLVE_PREC_MIXED;
         info->detail = detail;
         if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
+        keep(ASOLVE_PREC_MIXED, lu);
         return info->status = ASOLVE_OK;
       }
       detail |= 2;
@@ -1318,6 +1440,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   LCK(cudaStreamSynchronize(st));
   if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
   const bool poor = !no_rcond && !(rcv >= a.rcond_threshold);
+  keep(ASOLVE_PREC_FP64, lu);
   return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
 }
 

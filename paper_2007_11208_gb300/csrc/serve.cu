@@ -3,24 +3,27 @@
 //
 // The paper solves one system per call.  A server takes a stream of such
 // calls from many producers and keeps the GPU busy with them: requests wait
-// in a FIFO queue, and one server thread repeatedly
-//   1. admits requests in arrival order while the bytes they pin on the
-//      device fit the context's HBM budget (staging of host buffers plus the
-//      workspace of a large system; a request that alone exceeds the budget
-//      is refused at submission with ASOLVE_E_NOMEM),
-//   2. solves every admitted small request (n <= 1024, nrhs <= 8) with the
-//      same solver flags as one class-routed batch (scan, device routing,
-//      one persistent launch per class, replayed from a CUDA graph), and at
-//      most one large request on the blocked whole-GPU path,
-//   3. publishes each request's status, asolve_info and latency (submission
-//      to completion, host steady clock) for asolve_poll.
-// Requests that arrive while a round runs join the next round: a batch is
-// never waited for, it is whatever is queued when the GPU frees up.  Large
-// requests run one per round so that small requests behind them wait for at
-// most one large solve.
+// in a FIFO queue and two lanes, each a host thread with its own CUDA
+// stream, take work from it as soon as they are free:
+//   * the batch lane takes every queued small request (n <= 1024,
+//     nrhs <= 8) with the same solver flags, in arrival order, and solves
+//     them as one class-routed batch (scan, device routing, one persistent
+//     launch per class, replayed from a CUDA graph);
+//   * the large lane takes the oldest larger request and runs the blocked
+//     whole-GPU path.
+// The lanes overlap on the device: small requests that arrive while a large
+// system is being factored are solved meanwhile.  Admission is by HBM
+// budget: a request is admitted only while the bytes it holds on the device
+// (staging of host buffers, the workspace of a large system) fit the
+// context's budget together with everything in flight; a large request that
+// does not fit yet reserves its bytes so that small ones cannot starve it,
+// and one that alone exceeds the budget is refused at submission with
+// ASOLVE_E_NOMEM.  Each request's status, asolve_info and latency
+// (submission to completion, host steady clock) are published for
+// asolve_poll.
 //
-// The server owns a second asolve context (its own stream and workspaces),
-// so synchronous calls on the owner context may go on meanwhile.  Staging
+// The server owns a second asolve context (its streams and workspaces), so
+// synchronous calls on the owner context may go on meanwhile.  Staging
 // memory and large-system workspaces come from a stream-ordered memory pool
 // private to the server.
 #include <cuda_runtime.h>
@@ -42,20 +45,6 @@ const asolve_config* ctx_config(asolve_ctx* c);
 int ctx_device(asolve_ctx* c);
 int ctx_num_sms(asolve_ctx* c);
 void** ctx_serve_slot(asolve_ctx* c);
-struct LargeArgs {
-  const double* A;
-  const double* B;
-  double* X;
-  int64_t n, nrhs;
-  uint32_t flags;
-  int precision;
-  double rcond_threshold, sympd_tol, band_frac, ir_target_berr, ir_kappa_limit;
-  int ir_max_iter;
-  int num_sms;
-  cudaStream_t st;
-};
-size_t large_ws_bytes(int64_t n, int64_t nrhs);
-int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
 void serve_shutdown(asolve_ctx* c);
 }  // namespace asv
 
@@ -121,7 +110,21 @@ struct Server {
   std::unordered_map<uint64_t, Done> done;
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread th;
+  std::thread th_small, th_large;
+  // one kept large request (ASOLVE_RESIDENT): its device block holds the
+  // workspace with the factorisation and, for host buffers, the staged A
+  void* kept_blk = nullptr;
+  size_t kept_bytes = 0, kept_ws = 0;
+  const double* kept_key = nullptr;  // the caller's A pointer
+  int64_t kept_n = 0, kept_nrhs = 0;
+  bool kept_host = false;
+  LargeReuse kept{};
+  bool evict_pending = false;
+  void evict_kept();  // large-lane thread only
+  cudaStream_t stl = nullptr;  // stream of the large lane
+  size_t reserved = 0;         // held for a large request waiting for budget
+  int active = 0;              // lanes busy on the device
+  Clock::time_point busy_since;
 
   // statistics (under mu)
   asolve_serve_stats stats = {};
@@ -132,7 +135,13 @@ struct Server {
   char* h_meta = nullptr;
   size_t h_meta_bytes = 0;
 
-  void run();
+  void lane_small();
+  void lane_large();
+  bool pick_small(std::vector<Request>& batch);
+  bool pick_large(Request& r);
+  bool any_queued(bool large) const;
+  void begin_busy();
+  void end_busy();
   void solve_small(std::vector<Request>& batch);
   void solve_large(Request& r);
   void complete(const Request& r, int status, const asolve_info* info);
@@ -165,6 +174,7 @@ void Server::complete(const Request& r, int status, const asolve_info* info) {
   stats.charged_bytes -= r.charge;
   t_last_done = t;
   cv_done.notify_all();
+  cv_work.notify_all();  // budget freed
 }
 
 void Server::fail_all(std::vector<Request>& rs, int status) {
@@ -269,16 +279,38 @@ void Server::solve_small(std::vector<Request>& b) {
 }
 
 // One large system on the blocked whole-GPU path.
+void Server::evict_kept() {
+  if (!kept_blk) return;
+  cudaFreeAsync(kept_blk, stl);
+  cudaStreamSynchronize(stl);
+  kept_blk = nullptr;
+  kept.valid = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  stats.charged_bytes -= kept_bytes;
+  kept_bytes = 0;
+  cv_work.notify_all();
+}
+
+// One large system on the blocked whole-GPU path.  With ASOLVE_RESIDENT the
+// request's device block is kept afterwards, and a later resident request
+// with the same A (same pointer, unchanged contents) solves with the kept
+// factorisation (and, for host buffers, the A already staged).
 void Server::solve_large(Request& r) {
   const bool hm = host_mode(r);
-  const size_t ws = round256(large_ws_bytes(r.n, r.nrhs));
-  const size_t total = ws + (hm ? staging_bytes(r.n, r.nrhs) : 0);
-  void* dblk = nullptr;
-  cudaError_t e = cudaMallocFromPoolAsync(&dblk, total, pool, st);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    complete(r, cuda_code(e), nullptr);
-    return;
+  const bool resident = (r.flags & ASOLVE_RESIDENT) != 0;
+  const bool hit = resident && kept_blk && kept.valid && kept_key == r.A && kept_n == r.n && kept_host == hm &&
+                   r.nrhs <= kept_nrhs;
+  if (resident && !hit) evict_kept();
+  const size_t ws = hit ? kept_ws : round256(large_ws_bytes(r.n, r.nrhs));
+  const size_t total = ws + (hm ? staging_bytes(r.n, hit ? kept_nrhs : r.nrhs) : 0);
+  void* dblk = hit ? kept_blk : nullptr;
+  if (!hit) {
+    cudaError_t e = cudaMallocFromPoolAsync(&dblk, total, pool, stl);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      complete(r, cuda_code(e), nullptr);
+      return;
+    }
   }
   const double* A = r.A;
   const double* B = r.B;
@@ -287,11 +319,12 @@ void Server::solve_large(Request& r) {
   if (hm) {
     char* stage = static_cast<char*>(dblk) + ws;
     const size_t ba = sizeof(double) * (size_t)(r.n * r.n), bb = sizeof(double) * (size_t)(r.n * r.nrhs);
+    const size_t bcap = sizeof(double) * (size_t)(r.n * (hit ? kept_nrhs : r.nrhs));
     double* sA = reinterpret_cast<double*>(stage);
     double* sB = reinterpret_cast<double*>(stage + round256(ba));
-    double* sX = reinterpret_cast<double*>(stage + round256(ba) + round256(bb));
-    ok = cudaMemcpyAsync(sA, r.A, ba, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaMemcpyAsync(sB, r.B, bb, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    double* sX = reinterpret_cast<double*>(stage + round256(ba) + round256(bcap));
+    if (!hit) ok = cudaMemcpyAsync(sA, r.A, ba, cudaMemcpyHostToDevice, stl) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(sB, r.B, bb, cudaMemcpyHostToDevice, stl) == cudaSuccess;
     A = sA;
     B = sB;
     X = sX;
@@ -302,15 +335,37 @@ void Server::solve_large(Request& r) {
   if (ok) {
     LargeArgs la{A, B, X, r.n, r.nrhs, r.flags & kSolverFlags, cfg.precision, cfg.rcond_threshold,
                  cfg.sympd_tol, cfg.band_frac, cfg.ir_target_berr, cfg.ir_kappa_limit, cfg.ir_max_iter,
-                 num_sms, st};
+                 num_sms, stl, resident ? &kept : nullptr};
     rc = large_solve(la, dblk, ws, &info);
     if (rc < 0 && rc != info.status) info.status = rc;
     if (hm && info.status >= 0)
-      ok = cudaMemcpyAsync(r.X, X, sizeof(double) * (size_t)(r.n * r.nrhs), cudaMemcpyDeviceToHost, st) ==
+      ok = cudaMemcpyAsync(r.X, X, sizeof(double) * (size_t)(r.n * r.nrhs), cudaMemcpyDeviceToHost, stl) ==
            cudaSuccess;
   }
-  cudaFreeAsync(dblk, st);
-  const bool synced = cudaStreamSynchronize(st) == cudaSuccess;
+  const bool keep = resident && ok && info.status >= 0 && kept.valid;
+  if (!keep) {
+    if (hit) {
+      kept_blk = nullptr;  // the kept block goes with this request
+      kept.valid = 0;
+      std::lock_guard<std::mutex> lk(mu);
+      stats.charged_bytes -= kept_bytes;
+      kept_bytes = 0;
+    }
+    cudaFreeAsync(dblk, stl);
+  }
+  const bool synced = cudaStreamSynchronize(stl) == cudaSuccess;
+  if (keep && !hit) {
+    kept_blk = dblk;
+    kept_bytes = total;
+    kept_ws = ws;
+    kept_key = r.A;
+    kept_n = r.n;
+    kept_nrhs = r.nrhs;
+    kept_host = hm;
+    std::lock_guard<std::mutex> lk(mu);
+    stats.charged_bytes += kept_bytes;
+    if (stats.charged_bytes > stats.peak_charged_bytes) stats.peak_charged_bytes = stats.charged_bytes;
+  }
   if (!ok || !synced) {
     cudaGetLastError();
     complete(r, ASOLVE_E_CUDA, nullptr);
@@ -323,61 +378,132 @@ void Server::solve_large(Request& r) {
   complete(r, info.status, &info);
 }
 
-void Server::run() {
+// Admission (mu held).  Small requests with the solver flags of the oldest
+// one, in arrival order, while the budget allows (minus what a waiting large
+// request has reserved).
+bool Server::pick_small(std::vector<Request>& batch) {
+  size_t used = 0;
+  uint32_t f0 = 0;
+  bool have = false;
+  for (auto it = queue.begin(); it != queue.end();) {
+    if (it->large) {
+      ++it;
+      continue;
+    }
+    const uint32_t f = it->flags & kSolverFlags;
+    if (have && f != f0) {
+      ++it;
+      continue;
+    }
+    if (stats.charged_bytes + reserved + used + it->charge > budget) break;
+    if ((int64_t)batch.size() >= kServeMaxBatch) break;
+    f0 = f;
+    have = true;
+    used += it->charge;
+    batch.push_back(*it);
+    it = queue.erase(it);
+  }
+  if (batch.empty()) return false;
+  stats.charged_bytes += used;
+  if (stats.charged_bytes > stats.peak_charged_bytes) stats.peak_charged_bytes = stats.charged_bytes;
+  stats.queued = (int64_t)queue.size();
+  return true;
+}
+
+// The oldest large request, if it fits; otherwise its bytes are reserved.
+bool Server::pick_large(Request& r) {
+  for (auto it = queue.begin(); it != queue.end(); ++it) {
+    if (!it->large) continue;
+    if (stats.charged_bytes + it->charge > budget) {
+      if (kept_blk && (stats.charged_bytes - kept_bytes) + it->charge <= budget) {
+        // the kept factorisation gives way (freed by the caller, outside the lock)
+        evict_pending = true;
+        return false;
+      }
+      reserved = it->charge;
+      return false;
+    }
+    reserved = 0;
+    r = *it;
+    queue.erase(it);
+    stats.charged_bytes += r.charge;
+    if (stats.charged_bytes > stats.peak_charged_bytes) stats.peak_charged_bytes = stats.charged_bytes;
+    stats.queued = (int64_t)queue.size();
+    return true;
+  }
+  reserved = 0;
+  return false;
+}
+
+bool Server::any_queued(bool large) const {
+  for (const Request& q : queue)
+    if (q.large == large) return true;
+  return false;
+}
+
+void Server::begin_busy() {
+  if (active++ == 0) busy_since = Clock::now();
+}
+void Server::end_busy() {
+  if (--active == 0) stats.busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - busy_since).count();
+  stats.rounds += 1;
+}
+
+void Server::lane_small() {
   cudaSetDevice(device);
   for (;;) {
-    std::vector<Request> small;
-    Request large{};
-    bool have_large = false;
+    std::vector<Request> batch;
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !queue.empty(); });
-      if (queue.empty()) break;  // stop requested and nothing left
-      // admission in arrival order: stop at the first request that does not
-      // fit the budget, so that a big request is not overtaken forever
-      size_t used = 0;
-      uint32_t batch_flags = 0;
-      bool have_flags = false;
-      for (auto it = queue.begin(); it != queue.end();) {
-        if (used + it->charge > budget) break;
-        if (it->large) {
-          if (have_large) {
-            ++it;
-            continue;
-          }
-          large = *it;
-          have_large = true;
-        } else {
-          const uint32_t f = it->flags & kSolverFlags;
-          if ((have_flags && f != batch_flags) || (int64_t)small.size() >= kServeMaxBatch) {
-            ++it;
-            continue;
-          }
-          batch_flags = f;
-          have_flags = true;
-          small.push_back(*it);
-        }
-        used += it->charge;
-        it = queue.erase(it);
+      for (;;) {
+        if (pick_small(batch)) break;
+        if (stop && !any_queued(false)) return;
+        cv_work.wait(lk);
       }
-      stats.charged_bytes += used;
-      if (stats.charged_bytes > stats.peak_charged_bytes) stats.peak_charged_bytes = stats.charged_bytes;
-      stats.queued = (int64_t)queue.size();
+      begin_busy();
     }
-    const Clock::time_point t0 = Clock::now();
-    if (!small.empty()) solve_small(small);
-    if (have_large) solve_large(large);
-    const double ms = std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+    solve_small(batch);
     std::lock_guard<std::mutex> lk(mu);
-    stats.busy_ms += ms;
-    stats.rounds += 1;
+    end_busy();
+    cv_work.notify_all();
+  }
+}
+
+void Server::lane_large() {
+  cudaSetDevice(device);
+  for (;;) {
+    Request r{};
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      for (;;) {
+        if (pick_large(r)) break;
+        if (evict_pending) {
+          evict_pending = false;
+          lk.unlock();
+          evict_kept();
+          lk.lock();
+          continue;
+        }
+        if (stop && !any_queued(true)) return;
+        cv_work.wait(lk);
+      }
+      begin_busy();
+    }
+    solve_large(r);
+    std::lock_guard<std::mutex> lk(mu);
+    end_busy();
+    cv_work.notify_all();
   }
 }
 
 Server* server_of(asolve_ctx* c) { return static_cast<Server*>(*ctx_serve_slot(c)); }
 
+// Guards the creation of servers (first submissions may race).
+std::mutex g_create_mu;
+
 // Create the server of context c on first use.
 int ensure_server(asolve_ctx* c, Server** out) {
+  std::lock_guard<std::mutex> create_lk(g_create_mu);
   Server* s = server_of(c);
   if (s) {
     *out = s;
@@ -413,7 +539,15 @@ int ensure_server(asolve_ctx* c, Server** out) {
   // keep freed blocks for the next rounds instead of returning them
   uint64_t keep = s->budget;
   cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
-  s->th = std::thread([s] { s->run(); });
+  if (cudaStreamCreateWithFlags(&s->stl, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaMemPoolDestroy(s->pool);
+    asolve_destroy(s->w);
+    delete s;
+    return ASOLVE_E_CUDA;
+  }
+  s->th_small = std::thread([s] { s->lane_small(); });
+  s->th_large = std::thread([s] { s->lane_large(); });
   *ctx_serve_slot(c) = s;
   *out = s;
   return ASOLVE_OK;
@@ -430,9 +564,19 @@ void serve_shutdown(asolve_ctx* c) {
     s->stop = true;
   }
   s->cv_work.notify_all();
-  if (s->th.joinable()) s->th.join();
+  if (s->th_small.joinable()) s->th_small.join();
+  if (s->th_large.joinable()) s->th_large.join();
+  if (s->kept_blk) {
+    cudaSetDevice(s->device);
+    cudaFreeAsync(s->kept_blk, s->stl);
+    s->kept_blk = nullptr;
+  }
   cudaSetDevice(s->device);
   if (s->st) cudaStreamSynchronize(s->st);
+  if (s->stl) {
+    cudaStreamSynchronize(s->stl);
+    cudaStreamDestroy(s->stl);
+  }
   if (s->pool) cudaMemPoolDestroy(s->pool);
   if (s->h_meta) cudaFreeHost(s->h_meta);
   asolve_destroy(s->w);
@@ -445,7 +589,7 @@ extern "C" int asolve_submit(asolve_ctx* c, const double* A, const double* B, in
                              uint32_t flags, double* X, uint64_t* ticket) {
   if (!c || !ticket || n < 0 || nrhs < 1) return ASOLVE_E_INVALID;
   if (n > 0 && (!A || !B || !X)) return ASOLVE_E_INVALID;
-  if (flags & ~(kSolverFlags | ASOLVE_HOST_BUFFERS | ASOLVE_SYNC)) return ASOLVE_E_INVALID;
+  if (flags & ~(kSolverFlags | ASOLVE_HOST_BUFFERS | ASOLVE_SYNC | ASOLVE_RESIDENT)) return ASOLVE_E_INVALID;
   if (n > kLargeNMax || nrhs > kLargeRhsMax) return ASOLVE_E_UNSUPPORTED;
   Server* s = nullptr;
   int rc = ensure_server(c, &s);
@@ -488,7 +632,7 @@ extern "C" int asolve_submit(asolve_ctx* c, const double* A, const double* B, in
   s->queue.push_back(r);
   s->stats.queued = (int64_t)s->queue.size();
   lk.unlock();
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();  // both lanes wait on this condition
   return ASOLVE_OK;
 }
 

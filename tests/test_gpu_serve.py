@@ -264,3 +264,95 @@ def test_concurrent_producers(lib_ready):
         dA, dB, dX, n, r = dev[i]
         assert np.array_equal(host_from_dev(dX, n, r), alone[i][2])
     ctx.close()
+
+
+def test_lanes_overlap(lib_ready):
+    """Small requests submitted right after a large one are not held behind
+    it: the batch lane solves them while the large lane factors."""
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(31)
+    ctx = asolve.Context()
+    nL = 4096
+    AL = _mat("general", nL, rng)
+    bL = rng.standard_normal((nL, 1))
+    dAL = dev_colmajor(AL)
+    dBL, _ = dev_rhs(bL, nL)
+    dXL = torch.zeros_like(dBL)
+    small = []
+    for i in range(16):
+        n = 64 + 8 * i
+        A = _mat(KINDS[i % 5], n, rng)
+        B = rng.standard_normal((n, 1))
+        dB, _ = dev_rhs(B, n)
+        small.append((dev_colmajor(A), dB, torch.zeros_like(dB), n))
+    torch.cuda.synchronize()
+    rc, tL = ctx.submit(dAL, dBL, nL, 1, dXL)
+    assert rc == asolve.OK
+    ts = []
+    for dA, dB, dX, n in small:
+        rc, t = ctx.submit(dA, dB, n, 1, dX)
+        assert rc == asolve.OK
+        ts.append(t)
+    lat_small = []
+    for t in ts:
+        st, info, lat = ctx.poll(t, -1)
+        assert st == asolve.OK
+        lat_small.append(lat)
+    st, info, lat_large = ctx.poll(tL, -1)
+    assert st == asolve.OK
+    # every small request finished before the large one
+    assert max(lat_small) < lat_large, (max(lat_small), lat_large)
+    stats = ctx.serve_stats()
+    assert stats["large_solves"] == 1 and stats["batches"] >= 1
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,host", [("mixed", False), ("mixed", True), ("fp64", False)])
+def test_resident_reuse(lib_ready, prec, host):
+    """A resident large request keeps its factorisation: a later resident
+    request with the same A solves with it (detail bit 3) and gives the same
+    answer, bit for bit, as a fresh solve."""
+    from paper_2007_11208_gb300 import asolve
+    p = asolve.PREC_MIXED if prec == "mixed" else asolve.PREC_FP64
+    rng = np.random.default_rng(41)
+    n = 1500
+    A = _mat("spd" if host else "general", n, rng)
+    Bs = [rng.standard_normal((n, r)) for r in (2, 1, 2)]
+    ref = asolve.Context(precision=p)
+    alone = [_alone(ref, A, B) for B in Bs]
+    ref.close()
+    ctx = asolve.Context(precision=p)
+    flags = asolve.RESIDENT | (asolve.HOST_BUFFERS if host else 0)
+    if host:
+        hA = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+        Aptr = hA.data_ptr()
+    else:
+        dA = dev_colmajor(A)
+        Aptr = dA
+    outs = []
+    for B in Bs:
+        r = B.shape[1]
+        if host:
+            hB = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory()
+            hX = torch.zeros((r, n), dtype=torch.float64).pin_memory()
+            rc, t = ctx.submit(Aptr, hB.data_ptr(), n, r, hX.data_ptr(), flags)
+            keep = (hB, hX)
+        else:
+            dB, _ = dev_rhs(B, n)
+            dX = torch.zeros_like(dB)
+            torch.cuda.synchronize()
+            rc, t = ctx.submit(Aptr, dB, n, r, dX, flags)
+            keep = (dB, dX)
+        assert rc == asolve.OK
+        st, info, _ = ctx.poll(t, -1)
+        X = keep[1].numpy().reshape(r, n).T if host else host_from_dev(keep[1], n, r)
+        outs.append((st, info, X))
+    for k, ((st, info, X), (rc0, info0, X0)) in enumerate(zip(outs, alone)):
+        assert st == rc0 == asolve.OK
+        assert bool(info["detail"] & 8) == (k > 0), (k, info["detail"])
+        assert (info["route"], info["cls"], info["ir_iters"]) == (info0["route"], info0["cls"], info0["ir_iters"])
+        assert info["rcond"] == info0["rcond"]
+        assert np.array_equal(X, X0)
+    stats = ctx.serve_stats()
+    assert stats["charged_bytes"] > 0  # the kept block stays charged
+    ctx.close()
