@@ -55,6 +55,11 @@ METRIC = "solves/s at backward err <=1e-13 (batched adaptive solve)"
 UNIT = "solves/s"
 WORKLOAD = "batched-10000: n~U[16,512], nrhs~U[1,8], mix 40% general/25% spd/15% banded/15% tri/5% ill"
 BERR_BAR = 1e-13
+# arithmetic peaks of one GB300 (FP32 from the unit counts and the maximum
+# SM clock; the FP64 rates measured with a microbenchmark on this machine)
+PEAK_FP32 = 152 * 128 * 2 * 2.07e9
+PEAK_DFMA = 1.0e12
+PEAK_DMMA = 4.1e12
 COUNT = 10000  # systems per GPU per step (--count overrides, for small profiling runs)
 TUNING = os.path.join(ROOT, "paper_2007_11208_gb300", "tuning.json")  # autotuner output, if present
 SEED = 1
@@ -164,23 +169,35 @@ def verified_count(infos_list):
 
 
 def flops_model(specs, infos_list):
-    """Algorithmic work of the dominant class kernels, per step."""
+    """Algorithmic work of the dominant class kernels, per step, and the
+    minimum time the kernels' arithmetic needs on the pipes it runs on."""
     lu32 = chol32 = lu64 = chol64 = res64 = 0.0
+    t_min = {"k_lu_class": 0.0, "k_chol_class": 0.0}
     for (kind, n, r, *_), inf in zip(specs, infos_list):
         route, prec, it = inf["route"], inf["precision"], inf["ir_iters"]
-        if route in (6, 5):  # LU
-            if prec == 1:
-                lu32 += 2.0 / 3.0 * n ** 3
-                res64 += 2.0 * n * n * r * (it + 1)
+        kern = "k_lu_class" if route in (6, 5) else ("k_chol_class" if route == 4 else None)
+        if kern is None:
+            continue
+        f = (2.0 / 3.0 if kern == "k_lu_class" else 1.0 / 3.0) * n ** 3
+        if prec == 1:
+            res = 2.0 * n * n * r * (it + 1)
+            res64 += res
+            # FP64 residual: DFMA for one or two right-hand sides, else
+            # mma.sync f64 with the columns padded to 8
+            res_rate = PEAK_DFMA if r <= 2 else PEAK_DMMA * r / 8.0
+            t_min[kern] += f / PEAK_FP32 + res / res_rate
+            if kern == "k_lu_class":
+                lu32 += f
             else:
-                lu64 += 2.0 / 3.0 * n ** 3
-        elif route == 4:
-            if prec == 1:
-                chol32 += 1.0 / 3.0 * n ** 3
-                res64 += 2.0 * n * n * r * (it + 1)
+                chol32 += f
+        else:
+            t_min[kern] += f / PEAK_DMMA
+            if kern == "k_lu_class":
+                lu64 += f
             else:
-                chol64 += 1.0 / 3.0 * n ** 3
-    return dict(lu32=lu32, chol32=chol32, lu64=lu64, chol64=chol64, res64=res64)
+                chol64 += f
+    return dict(lu32=lu32, chol32=chol32, lu64=lu64, chol64=chol64, res64=res64,
+                t_min_ms={k: v * 1e3 for k, v in t_min.items()})
 
 
 def load_peaks():
@@ -341,11 +358,17 @@ def ours(args):
             key32 = "lu32" if dom == "k_lu_class" else "chol32"
             fl = fm[key32]
             ach = fl / (per[dom] / 1e3) / 1e12
+            t_min = fm["t_min_ms"].get(dom, 0.0)
             result["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
                                   "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
                                   "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
                                   "note": "FP32 factor flops only; the FP64 refinement of the same "
-                                          "kernel is not counted"}
+                                          "kernel is not counted",
+                                  "alu_time_model": {
+                                      "min_ms": t_min, "measured_ms": per[dom], "frac": t_min / per[dom],
+                                      "note": "FP32 factor flops at the FP32 peak + FP64 factor flops at "
+                                              "the mma.sync f64 rate (4.1 TFLOP/s) + FP64 residual flops at "
+                                              "the DFMA (1.0) or mma.sync f64 rate, per system"}}
         result["flops_model"] = fm
     if rank == 0 and args.cpu_baseline:
         result["cpu_baseline"] = oracle_sample(pk, budget_s=args.cpu_seconds)

@@ -29,8 +29,6 @@ namespace asv {
 
 namespace {
 
-constexpr int kD = 4;           // cp.async prefetch distance (column steps)
-constexpr int kMaxR = 8;        // register-window width: kl+ku+1 <= 32 * kMaxR
 constexpr size_t kWinSmemMax = 200 * 1024;
 constexpr size_t kTailBytes = 16384;  // scan record, scalars and per-column maxima (nrhs <= 256)
 
@@ -42,21 +40,6 @@ constexpr size_t kTailBytes = 16384;  // scan record, scalars and per-column max
       return _e == cudaErrorMemoryAllocation ? ASOLVE_E_NOMEM : ASOLVE_E_CUDA; \
     }                                                 \
   } while (0)
-
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ------------------------------------------------------------ scan / pack
 struct BandScan {
@@ -226,257 +209,6 @@ __global__ void __launch_bounds__(32) k_band_lu_glob(double* F, int ldf, int n, 
   b.ldf = ldf;
   const int f = warp_band_lu(b);
   if ((threadIdx.x & 31) == 0 && f) *fail = f;
-}
-
-// ------------------------------------------------------------ sweeps
-// The vector window: element e sits in register e >> 5 of lane e & 31.
-template <int R>
-struct Win {
-  double w[R];
-  // (selects on shuffled copies keep every w[r] in a register)
-  __device__ __forceinline__ double get(int e) const {
-    const int re = e >> 5, le = e & 31;
-    double v = __shfl_sync(0xffffffffu, w[0], le);
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      const double t = __shfl_sync(0xffffffffu, w[r], le);
-      v = (r == re) ? t : v;
-    }
-    return v;
-  }
-  __device__ __forceinline__ void set(int e, double v) {
-    const int lane = threadIdx.x & 31;
-    const bool mine = lane == (e & 31);
-#pragma unroll
-    for (int r = 0; r < R; ++r) w[r] = (mine && r == (e >> 5)) ? v : w[r];
-  }
-  // element e <- element e+1; the top element becomes 0
-  __device__ __forceinline__ void shift_down() {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const double nxt = (r + 1 < R) ? __shfl_sync(0xffffffffu, w[(r + 1 < R) ? r + 1 : r], 0) : 0.0;
-      w[r] = __shfl_down_sync(0xffffffffu, w[r], 1);
-      if (lane == 31) w[r] = nxt;
-    }
-  }
-  // element e <- element e-1; element 0 becomes v0
-  __device__ __forceinline__ void shift_up(double v0) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = R - 1; r >= 0; --r) {
-      const double prv = (r > 0) ? __shfl_sync(0xffffffffu, w[r > 0 ? r - 1 : 0], 31) : v0;
-      w[r] = __shfl_up_sync(0xffffffffu, w[r], 1);
-      if (lane == 0) w[r] = prv;
-    }
-  }
-};
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// x <- inv(A) x with the band factors (Sec. 2.1 solve), one warp, one vector.
-// ring: kD * (kv + 2) doubles + kD ints of shared memory.
-template <int R>
-__device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl, int ku, const int* __restrict__ piv,
-                           double* x, double* ring, int* pring) {
-  const int lane = threadIdx.x & 31;
-  const int kv = kl + ku, SL = kv + 2;
-  Win<R> W;
-  // ---- forward: apply P_j then L_j, j = 0..n-1; element t = x[j+t], t <= kl
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int t = r * 32 + lane;
-    W.w[r] = (t <= kl && t < n) ? x[t] : 0.0;
-  }
-  __syncwarp();
-  auto pre_f = [&](int c) {
-    if (c < n) {
-      double* sl = ring + (size_t)(c % kD) * SL;
-      const int kmc = min(kl, n - 1 - c);
-      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)c * ldf);
-      if (lane == 0) {
-        if (c + kl + 1 < n) cp_async8(sl + kl, x + c + kl + 1);
-        cp_async4(pring + c % kD, piv + c);
-      }
-    }
-    cp_commit();
-  };
-  for (int c = 0; c < kD; ++c) pre_f(c);
-  for (int j = 0; j < n; ++j) {
-    cp_wait<kD - 1>();
-    __syncwarp();
-    const double* sl = ring + (size_t)(j % kD) * SL;
-    const int km = min(kl, n - 1 - j);
-    const int d = pring[j % kD] - j;
-    const double e0 = W.get(0);
-    const double ed = W.get(d);
-    if (d) {
-      W.set(0, ed);
-      W.set(d, e0);
-    }
-    const double xj = d ? ed : e0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int t = r * 32 + lane;
-      if (t >= 1 && t <= km) W.w[r] = fma(-sl[t - 1], xj, W.w[r]);
-    }
-    if (lane == 0) x[j] = xj;
-    const double inc = (j + kl + 1 < n) ? sl[kl] : 0.0;
-    W.shift_down();
-    W.set(kl, inc);
-    __syncwarp();
-    pre_f(j + kD);
-  }
-  cp_wait_all();
-  __syncwarp();
-  __threadfence();
-  // ---- backward: U x = y, i = n-1..0; element s = y[i-s], s <= kv
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int s = r * 32 + lane;
-    W.w[r] = (s <= kv && n - 1 - s >= 0) ? x[n - 1 - s] : 0.0;
-  }
-  __syncwarp();
-  auto pre_b = [&](int q) {
-    const int i = n - 1 - q;
-    if (i >= 0) {
-      double* sl = ring + (size_t)(q % kD) * SL;
-      for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)i * ldf);
-      if (lane == 0 && i - kv - 1 >= 0) cp_async8(sl + kv + 1, x + i - kv - 1);
-    }
-    cp_commit();
-  };
-  for (int q = 0; q < kD; ++q) pre_b(q);
-  for (int q = 0; q < n; ++q) {
-    const int i = n - 1 - q;
-    cp_wait<kD - 1>();
-    __syncwarp();
-    const double* sl = ring + (size_t)(q % kD) * SL;
-    const double xi = W.get(0) / sl[kv];
-    if (lane == 0) x[i] = xi;
-    const int lim = min(kv, i);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int s = r * 32 + lane;
-      if (s >= 1 && s <= lim) W.w[r] = fma(-sl[kv - s], xi, W.w[r]);
-    }
-    const double inc = (i - kv - 1 >= 0) ? sl[kv + 1] : 0.0;
-    W.shift_down();
-    W.set(kv, inc);
-    __syncwarp();
-    pre_b(q + kD);
-  }
-  cp_wait_all();
-  __syncwarp();
-  __threadfence();
-}
-
-// x <- inv(A)^T x: U^T z = x forward, then L_j^T and P_j backward.
-template <int R>
-__device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int kl, int ku,
-                             const int* __restrict__ piv, double* x, double* ring, int* pring) {
-  const int lane = threadIdx.x & 31;
-  const int kv = kl + ku, SL = kv + 2;
-  Win<R> W;
-  // ---- U^T z = b, i = 0..n-1: element 0 = b_i, element s = z_{i-s}
-#pragma unroll
-  for (int r = 0; r < R; ++r) W.w[r] = (r == 0 && lane == 0) ? x[0] : 0.0;
-  __syncwarp();
-  auto pre_u = [&](int c) {
-    if (c < n) {
-      double* sl = ring + (size_t)(c % kD) * SL;
-      for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)c * ldf);
-      if (lane == 0 && c + 1 < n) cp_async8(sl + kv + 1, x + c + 1);
-    }
-    cp_commit();
-  };
-  for (int c = 0; c < kD; ++c) pre_u(c);
-  for (int i = 0; i < n; ++i) {
-    cp_wait<kD - 1>();
-    __syncwarp();
-    const double* sl = ring + (size_t)(i % kD) * SL;
-    const int lim = min(kv, i);
-    double acc = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int s = r * 32 + lane;
-      if (s >= 1 && s <= lim) acc = fma(sl[kv - s], W.w[r], acc);
-    }
-    acc = warp_sum_d(acc);
-    const double zi = (W.get(0) - acc) / sl[kv];
-    if (lane == 0) x[i] = zi;
-    W.set(0, zi);
-    const double inc = (i + 1 < n) ? sl[kv + 1] : 0.0;
-    W.shift_up(inc);
-    __syncwarp();
-    pre_u(i + kD);
-  }
-  cp_wait_all();
-  __syncwarp();
-  __threadfence();
-  // ---- L^T with interchanges, j = n-1..0: element t = x[j+t], t <= kl
-#pragma unroll
-  for (int r = 0; r < R; ++r) W.w[r] = (r == 0 && lane == 0) ? x[n - 1] : 0.0;
-  __syncwarp();
-  auto pre_l = [&](int q) {
-    const int j = n - 1 - q;
-    if (j >= 0) {
-      double* sl = ring + (size_t)(q % kD) * SL;
-      const int kmc = min(kl, n - 1 - j);
-      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)j * ldf);
-      if (lane == 0) {
-        if (j - 1 >= 0) cp_async8(sl + kl, x + j - 1);
-        cp_async4(pring + q % kD, piv + j);
-      }
-    }
-    cp_commit();
-  };
-  for (int q = 0; q < kD; ++q) pre_l(q);
-  for (int q = 0; q < n; ++q) {
-    const int j = n - 1 - q;
-    cp_wait<kD - 1>();
-    __syncwarp();
-    const double* sl = ring + (size_t)(q % kD) * SL;
-    const int km = min(kl, n - 1 - j);
-    double acc = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int t = r * 32 + lane;
-      if (t >= 1 && t <= km) acc = fma(sl[t - 1], W.w[r], acc);
-    }
-    acc = warp_sum_d(acc);
-    const double v = W.get(0) - acc;
-    const int d = pring[q % kD] - j;
-    if (d) {
-      const double ed = W.get(d);
-      W.set(0, ed);
-      W.set(d, v);
-    } else {
-      W.set(0, v);
-    }
-    if (j == 0) break;
-    // element kl (x[j+kl]) is final: no later step reads or swaps it
-    const double ek = W.get(kl);
-    if (lane == 0 && j + kl < n) x[j + kl] = ek;
-    const double inc = sl[kl];
-    W.shift_up(inc);
-    __syncwarp();
-    pre_l(q + kD);
-  }
-  cp_wait_all();
-  __syncwarp();
-  // flush the window: elements 0..kl are x[0..kl]
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int t = r * 32 + lane;
-    if (t <= kl && t < n) x[t] = W.w[r];
-  }
-  __syncwarp();
-  __threadfence();
 }
 
 template <int R>

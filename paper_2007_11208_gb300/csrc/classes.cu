@@ -232,18 +232,24 @@ template <typename ApplyF>
 __device__ bool refine(const BatchDesc& d, const double* __restrict__ A, const double* __restrict__ B,
                        int n, int nrhs, double norminf, double* xd, float* xs, double* R,
                        ApplyF apply32, double& berr_out, int& iters, CtaRed& red) {
-  __shared__ double s_scale[8], s_rmax[8];
-  // x0 = inv(A32) b, with each column scaled to unit max-norm first
+  // column scales are powers of two (exact to apply and to undo); the
+  // reciprocal is kept so the per-element scaling is one multiplication
+  __shared__ double s_scale[8], s_iscale[8], s_rmax[8];
+  // x0 = inv(A32) b, with each column scaled to max-norm in [1, 2) first
   for (int c = 0; c < nrhs; ++c) {
     double m = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(B[(size_t)c * n + i]));
     m = cta_max(m, red);
-    if (threadIdx.x == 0) s_scale[c] = m > 0.0 ? m : 1.0;
+    if (threadIdx.x == 0) {
+      const int k = m > 0.0 ? ilogb(m) : 0;
+      s_scale[c] = ldexp(1.0, k);
+      s_iscale[c] = ldexp(1.0, -k);
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
     int c = e / n;
-    xs[e] = (float)(B[e] / s_scale[c]);
+    xs[e] = (float)(B[e] * s_iscale[c]);
   }
   apply32(xs);
   for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = (double)xs[e] * s_scale[e / n];
@@ -270,16 +276,21 @@ __device__ bool refine(const BatchDesc& d, const double* __restrict__ A, const d
     const bool conv = berr <= d.ir_target_berr;
     if (!conv && (it >= d.ir_max_iter || !(berr < 0.5 * berr_prev))) break;  // stalled
     berr_prev = berr;
+    if (threadIdx.x < nrhs) {
+      const double m = s_rmax[threadIdx.x];
+      const int k = m > 0.0 ? ilogb(m) : 0;
+      s_scale[threadIdx.x] = ldexp(1.0, k);
+      s_iscale[threadIdx.x] = ldexp(1.0, -k);
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
       int c = e / n;
-      double sc = s_rmax[c] > 0.0 ? s_rmax[c] : 1.0;
-      xs[e] = (float)(R[e] / sc);
+      xs[e] = (float)(R[e] * s_iscale[c]);
     }
     apply32(xs);
     for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) {
       int c = e / n;
-      double sc = s_rmax[c] > 0.0 ? s_rmax[c] : 1.0;
-      xd[e] += (double)xs[e] * sc;
+      xd[e] += (double)xs[e] * s_scale[c];
     }
     __syncthreads();
     ++iters;
@@ -518,15 +529,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
 }
 
 // ------------------------------------------------------------------ banded
-// Band storage, warp_band_lu and warp_band_apply live in band_warp.cuh.
+// Band storage, warp_band_lu and the sweeps live in band_warp.cuh.  The
+// batched band kernel gives every warp a ring for register windows of up
+// to kBandR registers (kl + ku < 32 kBandR); wider bands use the
+// global-memory sweep.
+constexpr int kBandR = 2;
+constexpr int kBandRingBytes = band_ring_doubles(kBandR) * 8 + 64;  // ring + pivot ring, per warp
 
 // Warp-scope estimator (same iteration as cta_est_inv_norm1).
-__device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
+__device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi, double* ring, int* pring) {
   const int lane = threadIdx.x & 31;
   const int n = b.n;
   for (int i = lane; i < n; i += 32) v[i] = 1.0 / (double)n;
   __syncwarp();
-  warp_band_apply(b, v, false);
+  band_sweep_any(b, v, false, ring, pring, kBandR);
   if (n == 1) return fabs(v[0]);
   auto sum_abs = [&]() {
     double s = 0.0;
@@ -550,7 +566,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
     v[i] = sg;
   }
   __syncwarp();
-  warp_band_apply(b, v, true);
+  band_sweep_any(b, v, true, ring, pring, kBandR);
   int k = 2;
   for (;;) {
     const int j = argmax();
@@ -558,7 +574,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
     __syncwarp();
     for (int i = lane; i < n; i += 32) v[i] = (i == j) ? 1.0 : 0.0;
     __syncwarp();
-    warp_band_apply(b, v, false);
+    band_sweep_any(b, v, false, ring, pring, kBandR);
     const double estold = est;
     est = sum_abs();
     bool same = true;
@@ -572,7 +588,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
       v[i] = sg;
     }
     __syncwarp();
-    warp_band_apply(b, v, true);
+    band_sweep_any(b, v, true, ring, pring, kBandR);
     const int jn = argmax();
     ++k;
     if (jn < 0 || jn >= n) return __longlong_as_double(0x7ff8000000000000ll);
@@ -583,7 +599,7 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
   __syncwarp();
   for (int i = lane; i < n; i += 32) v[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
   __syncwarp();
-  warp_band_apply(b, v, false);
+  band_sweep_any(b, v, false, ring, pring, kBandR);
   double temp = 2.0 * sum_abs() / (double)(3 * n);
   return temp > est ? temp : est;
 }
@@ -592,8 +608,11 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi) {
 // system whose band storage does not fit there is left for the second
 // phase, where warp 0 of a CTA uses the whole slot.
 __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __restrict__ dp) {
+  extern __shared__ __align__(16) unsigned char band_smem[];
   const BatchDesc& d = *dp;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* ring = reinterpret_cast<double*>(band_smem + (size_t)w * kBandRingBytes);
+  int* pring = reinterpret_cast<int*>(band_smem + (size_t)w * kBandRingBytes + band_ring_doubles(kBandR) * 8);
   const int len = d.list_len[L_BAND];
   const size_t sub = (size_t)d.slot_bytes / kWarps;
   for (int phase = 0; phase < 2; ++phase) {
@@ -645,11 +664,11 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
         for (int c = 0; c < nrhs; ++c) {
           for (int i = lane; i < n; i += 32) xv[i] = B[(size_t)c * n + i];
           __syncwarp();
-          warp_band_apply(b, xv, false);
+          band_sweep_any(b, xv, false, ring, pring, kBandR);
           for (int i = lane; i < n; i += 32) X[(size_t)c * n + i] = xv[i];
           __syncwarp();
         }
-        if (!(d.flags & ASOLVE_NO_RCOND)) rc = rcond_from(sr.norm1, warp_est_inv_norm1(b, v, xi));
+        if (!(d.flags & ASOLVE_NO_RCOND)) rc = rcond_from(sr.norm1, warp_est_inv_norm1(b, v, xi, ring, pring));
         if (d.flags & ASOLVE_BERR) {
           // FP64 backward error over the band: r = b - A x, A read in band form
           double berr = 0.0;
@@ -915,7 +934,7 @@ cudaError_t launch_route(const BatchDesc* d, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t launch_band(const BatchDesc* d, int grid, cudaStream_t st) {
-  k_band_class<<<grid, kThreads, 0, st>>>(d);
+  k_band_class<<<grid, kThreads, kWarps * kBandRingBytes, st>>>(d);
   return cudaGetLastError();
 }
 cudaError_t launch_tri(const BatchDesc* d, int grid, cudaStream_t st) {

@@ -55,12 +55,19 @@ struct ScanShared {
 
 // Fig. 4 predicates for the pair (a = A_ij below the diagonal, b = A_ji).
 // Returns true when the pair violates one of them.
+// e_min: a biased exponent at which the symmetry test is decided without
+// FP64 arithmetic: when the exponents of a and b differ by 2 or more, the
+// larger magnitude m has |a - b| > m/2 > tol m, and when m's exponent is at
+// least e_min also m/2 > tol — the pair fails exactly when the FP64 test
+// would say so.
 __device__ __forceinline__ bool pair_fails(double a, double b, double di, double dj,
-                                           uint64_t hmd, double tol) {
+                                           uint64_t hmd, double tol, int e_min) {
   const uint64_t kAbs = 0x7fffffffffffffffull;
   uint64_t ab = dbits(a), bb = dbits(b);
   uint64_t ha = ab & kAbs, hb = bb & kAbs;
   if (ab != bb) {  // symmetry within tol, absolute and relative
+    const int ea = (int)(ha >> 52), eb = (int)(hb >> 52);
+    if (abs(ea - eb) >= 2 && max(ea, eb) >= e_min) return true;
     double delta = fabs(__dadd_rn(a, -b));
     double mx = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
     if (delta > tol && delta > __dmul_rn(tol, mx)) return true;
@@ -85,6 +92,7 @@ __device__ void scan_pairs(const double* __restrict__ A, int n, const double* di
   const int T = (n + 31) / 32;
   const int64_t npairs = (int64_t)T * (T + 1) / 2;
   double* ts = sh.tile[warp];
+  const int e_min = tol <= 0.0 ? 0 : (tol < 0.25 ? ilogb(tol) + 1025 : 0x7fffffff);
   for (int64_t p = first; p < npairs; p += step) {
     // invert p = P(P+1)/2 + Q
     int64_t P = (int64_t)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
@@ -109,7 +117,10 @@ __device__ void scan_pairs(const double* __restrict__ A, int n, const double* di
     float v2[32];
     if (P == Q) {
       const int jc = i0 + lane;  // this lane's column (and row) index
+      bool chk = check_sym;
       for (int k = 0; k < 32; ++k) {
+        // once a pair of this warp failed, the predicate is decided
+        if ((k & 7) == 0) chk = chk && !__any_sync(0xffffffffu, symfail_l);
         const int ir = i0 + k;
         double a = ts[lane * kTileLd + k];  // A(ir, jc)
         uint64_t ab = dbits(a);
@@ -120,9 +131,9 @@ __device__ void scan_pairs(const double* __restrict__ A, int n, const double* di
             if (k < lane) ku_l = max(ku_l, lane - k);
           }
           cs1 += abs_f32_trunc(ab, range_bad_l);
-          if (check_sym && k > lane) {
+          if (chk && k > lane) {
             double b = ts[k * kTileLd + lane];  // A(jc, ir)
-            if (pair_fails(a, b, diag[ir], diag[jc], hmd, tol)) symfail_l = true;
+            if (pair_fails(a, b, diag[ir], diag[jc], hmd, tol, e_min)) symfail_l = true;
           }
         }
         double at = ts[k * kTileLd + lane];  // A(i0+lane, i0+k): row sums
@@ -142,8 +153,10 @@ __device__ void scan_pairs(const double* __restrict__ A, int n, const double* di
         const int ic = i0 + k;
         bv[k] = (jr < n && ic < n) ? __ldg(A + (size_t)ic * n + jr) : 0.0;
       }
+      bool chk = check_sym;
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
+        if ((k & 7) == 0) chk = chk && !__any_sync(0xffffffffu, symfail_l);
         const int ir = i0 + k;
         const bool valid = (ir < n) && (jr < n);
         double a = ts[lane * kTileLd + k];  // A(ir, jr): below the diagonal
@@ -156,7 +169,7 @@ __device__ void scan_pairs(const double* __restrict__ A, int n, const double* di
           if (is_nonzero_bits(bb)) ku_l = max(ku_l, ir - jr);
           fa = abs_f32_trunc(ab, range_bad_l);
           fb = abs_f32_trunc(bb, range_bad_l);
-          if (check_sym && pair_fails(a, b, diag[ir], diag[jr], hmd, tol)) symfail_l = true;
+          if (chk && pair_fails(a, b, diag[ir], diag[jr], hmd, tol, e_min)) symfail_l = true;
         }
         cs1 += fa;   // column jr of tile (P,Q)
         rs2 += fb;   // row jr of tile (Q,P)
