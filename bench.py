@@ -480,8 +480,11 @@ def large_workload(args):
             for kind in kinds:
                 for kappa in kappas:
                     g = synth.gen(int(n + 17 * kappa) % 100003, dev)
-                    A = synth.spectrum_fast(n, g, kappa, spd=(kind == "spd"), device=dev)
-                    B64 = synth.rhs(n, 64, g, dev)
+                    if kind == "lower":  # TRSM: diagonally dominant lower triangle (kappa not imposed)
+                        A = synth.tri_dd(n, g, lower=True, device=dev)
+                    else:
+                        A = synth.spectrum_fast(n, g, kappa, spd=(kind == "spd"), device=dev)
+                    B64 = synth.rhs(n, max(nrhs_list), g, dev)
                     for nrhs in nrhs_list:
                         B = B64[:nrhs].contiguous()
                         X = torch.zeros_like(B)
@@ -505,8 +508,8 @@ def large_workload(args):
                                          "precision": info["precision"], "ir_iters": info["ir_iters"],
                                          "berr": info["berr"], "rcond": info["rcond"],
                                          "detail": info["detail"],
-                                         "flops_per_s": (2.0 / 3.0 if kind == "general" else 1.0 / 3.0)
-                                         * n ** 3 / (ms * 1e-3)}
+                                         "flops_per_s": ({"general": 2.0 / 3.0 * n ** 3, "spd": 1.0 / 3.0 * n ** 3,
+                                                          "lower": float(n) * n * nrhs}[kind]) / (ms * 1e-3)}
                             log(n, kind, f"{kappa:.0e}", nrhs, name, f"{ms:.2f} ms", info["route"],
                                 info["precision"], info["ir_iters"], f"{info['berr']:.2e}")
                         if "fp64" in row and "mixed" in row:
@@ -724,7 +727,7 @@ def main():
     ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve", "plain"])
     ap.add_argument("--reps", type=int, default=1000, help="plain: repetitions per system")
     ap.add_argument("--sizes", default="8192,16384", help="large: matrix sizes")
-    ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds")
+    ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds (general, spd, lower)")
     ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
     ap.add_argument("--nrhs-list", default="1,64", help="large: right-hand-side counts")
     ap.add_argument("--precs", default="mixed,fp64", help="large: precisions")

@@ -139,6 +139,16 @@ def _ptr(t):
     return C.c_void_p(t)
 
 
+def _need(t, count: int, name: str):
+    """A tensor argument must hold at least `count` FP64 elements and be
+    contiguous (the library reads and writes exactly that extent)."""
+    if isinstance(t, torch.Tensor):
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous float64 tensor")
+        if t.numel() < count:
+            raise ValueError(f"{name}: {t.numel()} elements, the call needs {count}")
+
+
 def info_dict(i: Info) -> dict:
     return {k: getattr(i, k) for k, _ in Info._fields_}
 
@@ -206,11 +216,17 @@ class Context:
 
     def solve(self, A, B, n: int, nrhs: int, X, flags: int = 0):
         """A, B, X: CUDA tensors (or host pointers with HOST_BUFFERS)."""
+        _need(A, n * n, "A")
+        _need(B, n * nrhs, "B")
+        _need(X, n * nrhs, "X")
         inf = Info()
         rc = lib().asolve_solve(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(inf))
         return rc, info_dict(inf)
 
     def solve_band(self, AB, ldab: int, kl: int, ku: int, B, n: int, nrhs: int, X, flags: int = 0):
+        _need(AB, ldab * n, "AB")
+        _need(B, n * nrhs, "B")
+        _need(X, n * nrhs, "X")
         inf = Info()
         rc = lib().asolve_solve_band(self._h, _ptr(AB), ldab, kl, ku, _ptr(B), n, nrhs, flags,
                                      _ptr(X), C.byref(inf))
@@ -228,6 +244,9 @@ class Context:
 
     def submit(self, A, B, n: int, nrhs: int, X, flags: int = 0):
         """Queue one request; returns (rc, ticket).  The buffers must outlive it."""
+        _need(A, n * n, "A")
+        _need(B, n * nrhs, "B")
+        _need(X, n * nrhs, "X")
         t = C.c_uint64(0)
         rc = lib().asolve_submit(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(t))
         return rc, t.value

@@ -165,6 +165,7 @@ struct PanelBuf {
   void* diag;      // [2][kLB] of T
   unsigned* bar;   // grid barrier (zeroed before the launch)
   int* err;
+  unsigned long long* key;  // [3] FP32 panels: (|v| bits << 32) | ~row, by atomicMax
 };
 
 template <typename T>
@@ -214,11 +215,21 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
       int ii = s_idx[0];
       for (int k = 1; k < kWarps; ++k)
         if (s_best[k] > bb || (s_best[k] == bb && s_idx[k] < ii)) { bb = s_best[k]; ii = s_idx[k]; bv = s_val[k]; }
-      T* cd = candT + ((size_t)buf * G + b) * 4;
-      cd[0] = bb;
-      cd[1] = (T)ii;
-      cd[2] = bv;
-      cd[3] = (ii != 0x7fffffff && bb >= T(0)) ? T(1) : T(0);
+      if constexpr (sizeof(T) == 4) {
+        // one atomic per CTA: the largest key is the largest |v|, then the
+        // smallest row (first index on ties)
+        if (ii != 0x7fffffff && bb >= T(0))
+          atomicMax(pb.key + c % 3,
+                    ((unsigned long long)__float_as_uint((float)bb) << 32) | (0xffffffffull - (unsigned)ii));
+        // the next column's key was last read after barrier c-2: reset it now
+        if (b == 0) pb.key[(c + 1) % 3] = 0ull;
+      } else {
+        T* cd = candT + ((size_t)buf * G + b) * 4;
+        cd[0] = bb;
+        cd[1] = (T)ii;
+        cd[2] = bv;
+        cd[3] = (ii != 0x7fffffff && bb >= T(0)) ? T(1) : T(0);
+      }
       s_p = ii;
     }
     __syncthreads();
@@ -232,6 +243,21 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
     }
     __threadfence();
     if (!grid_barrier(pb.bar, (unsigned)G, pb.err)) return;
+    if constexpr (sizeof(T) == 4) {
+      // the winner is the key; its row (owner: row / R) holds the pivot
+      if (tid == 0) {
+        const unsigned long long key = *(volatile unsigned long long*)(pb.key + c % 3);
+        const int ii = key ? (int)(0xffffffffull - (key & 0xffffffffull)) : 0x7fffffff;
+        const int wb = (ii != 0x7fffffff) ? ii / R : -1;
+        const T bv = (wb >= 0 && wb < G) ? ((volatile T*)rowsT)[((size_t)buf * G + wb) * kLB + c] : T(0);
+        s_p = ii;
+        s_wb = wb;
+        s_pv = bv;
+        s_stop = (wb < 0 || wb >= G || ii < c || ii >= m || bv == T(0) || bv != bv) ? 1 : 0;
+        if (s_stop && b == 0) *fail = k0 + c + 1;
+        if (!s_stop && b == 0) piv[k0 + c] = k0 + ii;
+      }
+    } else {
     // every CTA finds the same winner: the candidates are read in parallel
     // (one per thread) and reduced (largest |v|, then smallest row)
     {
@@ -268,6 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
         if (s_stop && b == 0) *fail = k0 + c + 1;
         if (!s_stop && b == 0) piv[k0 + c] = k0 + ii;
       }
+    }
     }
     __syncthreads();
     if (s_stop) return;  // uniform across the grid: every CTA saw the same candidates
@@ -929,6 +956,7 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     const size_t psmem = sizeof(T) * ((size_t)R * (kLB + 1) + kLB) + 64;
     if (psmem > 226 * 1024) return ASOLVE_E_UNSUPPORTED;
     LCK(cudaMemsetAsync(f.pb.bar, 0, sizeof(unsigned) * 2, st));
+    LCK(cudaMemsetAsync(f.pb.key, 0, sizeof(unsigned long long) * 3, st));
     T* W = f.W;
     int ldw = f.ldw;
     int* piv = f.piv;
@@ -1196,9 +1224,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   void* pdiag = ar.take(sizeof(double) * 2 * kLB);
   unsigned* pbar = static_cast<unsigned*>(ar.take(sizeof(unsigned) * 4));
   int* perr = static_cast<int*>(ar.take(sizeof(int) * 4));
-  if (!fail || !Dtmp || !pcand || !prows || !pdiag || !pbar || !perr) return ASOLVE_E_NOMEM;
+  unsigned long long* pkey = static_cast<unsigned long long*>(ar.take(sizeof(unsigned long long) * 4));
+  if (!fail || !Dtmp || !pcand || !prows || !pdiag || !pbar || !perr || !pkey) return ASOLVE_E_NOMEM;
   LCK(cudaMemsetAsync(perr, 0, sizeof(int) * 4, st));
-  PanelBuf pb{pcand, prows, pdiag, pbar, perr};
+  PanelBuf pb{pcand, prows, pdiag, pbar, perr, pkey};
   bool chol = (cls == ASOLVE_CLS_SYMPD);
   info->route = chol ? ASOLVE_ROUTE_CHOL : ASOLVE_ROUTE_LU;
   int detail = 0;

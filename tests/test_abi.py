@@ -60,3 +60,18 @@ def test_null_handles_rejected(lib):
     assert L.asolve_destroy(None) == lib.E_INVALID
     assert L.asolve_set_profiling(None, 1) == lib.E_INVALID
     assert L.asolve_create(None, None) == lib.E_INVALID
+
+
+def test_binding_refuses_undersized_tensors(lib):
+    """The binding checks tensor extents before a call reaches the library,
+    which reads n*n elements of A and n*nrhs of B and X."""
+    import torch
+    need = lib._need
+    need(torch.zeros(12, dtype=torch.float64), 12, "A")
+    with pytest.raises(ValueError):
+        need(torch.zeros(11, dtype=torch.float64), 12, "A")
+    with pytest.raises(ValueError):
+        need(torch.zeros(12, dtype=torch.float32), 12, "A")
+    with pytest.raises(ValueError):
+        need(torch.zeros(4, 6, dtype=torch.float64).t(), 12, "A")
+    need(12345, 10 ** 9, "A")  # raw addresses are the caller's responsibility

@@ -71,6 +71,24 @@ def spectrum(n, kappa, rng, spd=False):
     return (U * s) @ V.T
 
 
+@pytest.mark.parametrize("kind,n,nrhs", [("lower", 2048, 9), ("upper", 1100, 64), ("lower", 2048, 256),
+                                          ("general", 1100, 40), ("spd", 1411, 17)])
+def test_large_many_rhs(ctx, orc, kind, n, nrhs):
+    """Right-hand sides spanning several 8-column chunks of the wavefront
+    triangular solve and of the residual kernel, with a ragged last chunk."""
+    rng = np.random.default_rng(n + nrhs)
+    A = make(kind, n, rng)
+    B = rng.standard_normal((n, nrhs))
+    rc, info, X = solve_gpu(ctx, A, B)
+    Xo, io = orc.solve(A, B)
+    assert rc == io["status"] == 0 and info["route"] == io["route"], (rc, info, io)
+    ka = kappa_inf(A)
+    for j in range(nrhs):  # column by column: a wrong chunk shows which one
+        assert fwd_err(X[:, j], Xo[:, j]) <= 2.0 ** -52 * n * ka, (j, fwd_err(X[:, j], Xo[:, j]))
+    _, berr = orc.residual_dot2(A, X, B)
+    assert berr.max() <= 1e-13, (berr.max(), info)
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
 @pytest.mark.parametrize("spd", [False, True])
 def test_large_known_x_spectra(ctx, orc, kappa, spd):

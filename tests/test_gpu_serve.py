@@ -213,7 +213,10 @@ def test_tickets_and_flags(lib_ready):
     rc0, t0 = ctx.submit(None, None, 0, 1, None)
     assert rc1 == rc2 == rc0 == asolve.OK
     assert ctx.submit(dA, dB, -1, 1, X1)[0] == asolve.E_INVALID
-    assert ctx.submit(dA, dB, 40000, 1, X1)[0] == asolve.E_UNSUPPORTED
+    # raw addresses: the library itself rejects the order before touching memory
+    assert ctx.submit(dA.data_ptr(), dB.data_ptr(), 40000, 1, X1.data_ptr())[0] == asolve.E_UNSUPPORTED
+    with pytest.raises(ValueError):  # tensors too small for the order: refused by the binding
+        ctx.submit(dA, dB, 40000, 1, X1)
     assert ctx.submit(dA, dB, 64, 1, X1, 0x10000)[0] == asolve.E_INVALID
     assert ctx.poll(t0, 0)[0] == asolve.OK
     r1, i1, _ = ctx.poll(t1, -1)
