@@ -471,7 +471,8 @@ def large_workload(args):
     kappas = [float(x) for x in args.kappas.split(",")]
     kinds = args.kinds.split(",")
     nrhs_list = [int(x) for x in args.nrhs_list.split(",")]
-    precs = [(asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64")]
+    precs = [(asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64"), (asolve.PREC_BF16, "bf16"),
+             (asolve.PREC_FP16, "fp16")]
     precs = [p for p in precs if p[1] in args.precs.split(",")]
     ctxs = {p: asolve.Context(precision=p) for p, _ in precs}
     cases = []
@@ -730,7 +731,7 @@ def main():
     ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds (general, spd, lower)")
     ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
     ap.add_argument("--nrhs-list", default="1,64", help="large: right-hand-side counts")
-    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions")
+    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions (mixed, fp64, bf16, fp16)")
     ap.add_argument("--templates", type=int, default=40, help="serve: distinct request matrices")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests per load point")
     ap.add_argument("--load", default="0.25,0.5,0.8", help="serve: arrival rates as fractions of capacity")

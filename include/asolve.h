@@ -69,7 +69,16 @@ extern "C" {
 
 /* ---- precision of the dense factorisations --------------------------- */
 #define ASOLVE_PREC_FP64    0   /* FP64 factorisations (DMMA tensor path) */
-#define ASOLVE_PREC_MIXED   1   /* FP32 factors + FP64 iterative refinement */
+#define ASOLVE_PREC_MIXED   1   /* FP32 factors + FP64 iterative refinement; large dense
+                                   systems: trailing updates as 3xTF32 tensor products
+                                   (FP32-level accuracy) */
+#define ASOLVE_PREC_BF16    2   /* as MIXED, but the trailing updates of large dense systems
+                                   (n > 1024) are single BF16 tensor products with FP32
+                                   accumulation; the refinement gate is the kappa limit of
+                                   BF16 (ir_kappa_limit capped at 1e3).  Systems with
+                                   n <= 1024 factor in FP32 as with MIXED */
+#define ASOLVE_PREC_FP16    3   /* as BF16 with FP16 operands (per-tile power-of-two
+                                   scaling); gate ir_kappa_limit capped at 1e4 */
 
 /* ---- flags ----------------------------------------------------------- */
 #define ASOLVE_NO_APPROX     0x01u  /* disable the SVD fallback (Sec. 2.5 option) */
@@ -271,10 +280,18 @@ int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, voi
 /* The trailing-update GEMM of the large dense factorisations (Sec. 2.3/2.4
  * blocked Cholesky/LU updates), exposed so it can be verified on its own:
  *   C (M x N) -= A (M x K) * B (K x N), FP32, column-major, device pointers,
- * computed with tcgen05 kind::tf32 MMAs and FP32 accumulation; passes = 3
- * splits every operand into a TF32 head and remainder (three products,
- * FP32-level accuracy), passes = 1 is plain TF32.  err: optional device int
- * set to 1 if a device-side wait gave up.  Asynchronous on `stream`. */
+ * computed on the tcgen05 tensor cores with FP32 accumulation.  passes:
+ * ASOLVE_GEMM_TF32X3 (3) splits every operand into a TF32 head and
+ * remainder (three products, FP32-level accuracy), ASOLVE_GEMM_TF32 (1) is
+ * plain TF32, ASOLVE_GEMM_BF16 / ASOLVE_GEMM_FP16 round every operand once
+ * to the 16-bit type (FP16 tiles scaled by powers of two from each tile's
+ * largest magnitude).  err: optional device int set to 1 if a device-side
+ * wait gave up.  Asynchronous on `stream`.  Errors: E_INVALID for another
+ * `passes` value. */
+#define ASOLVE_GEMM_TF32    1
+#define ASOLVE_GEMM_TF32X3  3
+#define ASOLVE_GEMM_BF16    16
+#define ASOLVE_GEMM_FP16    17
 int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
                     int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream);
 

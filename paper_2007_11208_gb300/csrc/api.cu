@@ -160,7 +160,7 @@ extern "C" int asolve_create(asolve_ctx** out, const asolve_config* cfg) {
   if (!c) return ASOLVE_E_NOMEM;
   if (cfg) c->cfg = *cfg;
   else asolve_default_config(&c->cfg);
-  if (c->cfg.precision != ASOLVE_PREC_FP64 && c->cfg.precision != ASOLVE_PREC_MIXED) {
+  if (c->cfg.precision < ASOLVE_PREC_FP64 || c->cfg.precision > ASOLVE_PREC_FP16) {
     delete c;
     return ASOLVE_E_INVALID;
   }
@@ -607,7 +607,10 @@ extern "C" int asolve_solve_band(asolve_ctx* c, const double* AB, int64_t ldab, 
 
 extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
                                int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream) {
-  if (!C || !A || !B || M < 0 || N < 0 || K < 0 || (passes != 1 && passes != 3)) return ASOLVE_E_INVALID;
+  if (!C || !A || !B || M < 0 || N < 0 || K < 0 ||
+      (passes != ASOLVE_GEMM_TF32 && passes != ASOLVE_GEMM_TF32X3 && passes != ASOLVE_GEMM_BF16 &&
+       passes != ASOLVE_GEMM_FP16))
+    return ASOLVE_E_INVALID;
   if (ldc < (M > 0 ? M : 1) || lda < (M > 0 ? M : 1) || ldb < (K > 0 ? K : 1)) return ASOLVE_E_INVALID;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || ldc > INT32_MAX || lda > INT32_MAX || ldb > INT32_MAX)
     return ASOLVE_E_UNSUPPORTED;

@@ -16,6 +16,12 @@ constexpr int kBatchNMax = 1024;   // largest n handled by the per-CTA batched p
 constexpr int kBatchRhsMax = 8;    // largest nrhs handled by the per-CTA batched path
 constexpr int kCtaThreads = 256;   // threads of the per-system (class) kernels
 constexpr double kEps = 2.220446049250313080847e-16;  // 2^-52, machine epsilon
+constexpr int kGemmBf16 = ASOLVE_GEMM_BF16;  // operand modes of launch_gemm_tc
+constexpr int kGemmFp16 = ASOLVE_GEMM_FP16;
+// kappa limits of refinement with 16-bit trailing updates (unit roundoff
+// 2^-8 for BF16, 2^-11 for FP16, times a margin for the growth of |L||U|)
+constexpr double kKappaLimitBf16 = 1e3;
+constexpr double kKappaLimitFp16 = 1e4;
 
 // Scan flags (Sec. 2.1, 2.2, Fig. 4).
 enum : int32_t {

@@ -178,6 +178,10 @@ __device__ __forceinline__ int next_item(const BatchDesc& d, int ctr, int* s_ite
 
 // Dense-class dynamic shared memory: 110 KB (two blocks per SM).
 constexpr int kDenseSmem = 110 * 1024;
+// FP64 estimates: v and xi (2 x 1024 doubles) first, then the 8 warps'
+// 32 x 33 tiles of the transposed triangular updates.
+constexpr int kEstStageOff = 2 * 1024 * 8 + 64;
+static_assert(kEstStageOff + kWarps * 32 * 33 * 8 <= kDenseSmem, "estimate stage");
 
 // Panel width: the n x nb panel plus the 32 x 33 inverse and two 32 x 64
 // tiles must fit in kDenseSmem; within that, the autotuner's table may
@@ -219,7 +223,7 @@ __device__ __forceinline__ DenseSlot dense_slot(const BatchDesc& d, int n) {
 }
 
 template <typename T>
-__device__ void copy_to_work(const double* __restrict__ A, int n, T* W, int ldw) {
+__device__ __noinline__ void copy_to_work(const double* __restrict__ A, int n, T* W, int ldw) {
   cta_copy_block<T, double>(W, ldw, A, n, n, n);
   __syncthreads();
 }
@@ -339,7 +343,9 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   const bool no_rcond = (d.flags & ASOLVE_NO_RCOND) != 0;
   int detail = 0;
   // ---- mixed precision attempt (not when magnitudes leave the FP32 range)
-  if (d.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
+  // (the 16-bit modes differ only in the large path's tensor-core updates:
+  // here they factor in FP32 as MIXED does)
+  if (d.precision != ASOLVE_PREC_FP64 && !(sr.flags & SF_NORM_FP64)) {
     float* W = reinterpret_cast<float*>(sl.W);
     copy_to_work<float>(A, n, W, ldw);
     const int nb = pick_nb<float>(n, d, KIND);
@@ -431,9 +437,10 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
       // product with explicit block inverses would corrupt the estimate
       double* v = reinterpret_cast<double*>(smem);
       double* xi = v + n;
+      double* stage = reinterpret_cast<double*>(smem + kEstStageOff);
       auto apply_est = [&](double* x, bool tr) {
-        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, x, n, 1, tr, sl.tmp);
-        else cta_chol_apply<double, double>(W, ldw, n, x, n, 1);
+        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, x, n, 1, tr, sl.tmp, nullptr, nullptr, stage);
+        else cta_chol_apply<double, double>(W, ldw, n, x, n, 1, nullptr, stage);
       };
       double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
       rc = rcond_from(sr.norm1, est);
@@ -513,6 +520,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
         if (threadIdx.x == 0) d.info[s].berr = be;
       }
       if (!(d.flags & ASOLVE_NO_RCOND)) {
+        // (the transposed solves use warp-per-row sums here: A itself is
+        // the factor, mostly outside L2, and staging tiles measured slower)
         double* v = reinterpret_cast<double*>(smem);
         double* xi = v + n;
         auto apply_est = [&](double* x, bool tr) {

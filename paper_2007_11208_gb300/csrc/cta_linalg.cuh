@@ -298,12 +298,38 @@ __device__ __noinline__ void cta_chol_update(T* W, int ldw, int n, int k0, int k
   __syncthreads();
 }
 
-// 2-D copy of an m x nc column-major block (no integer division per element).
+// 2-D copy of an m x nc column-major block.  The block is cut into 32-row
+// pieces of columns; warp w takes pieces w, w + 8, ... and has eight of
+// them (eight loads per lane) in flight before it stores any.  The piece's
+// (column, row) position advances incrementally: no integer division.
 template <typename D, typename S>
 __device__ __forceinline__ void cta_copy_block(D* dst, int ldd, const S* src, int lds, int m, int nc) {
+  constexpr int U = 8;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int c = w; c < nc; c += kWarps)
-    for (int r = lane; r < m; r += 32) dst[(size_t)c * ldd + r] = (D)src[(size_t)c * lds + r];
+  const int chunks = (m + 31) >> 5;
+  int c = 0, k = w;  // piece w: column c, 32-row chunk k
+  while (k >= chunks && c < nc) {
+    k -= chunks;
+    ++c;
+  }
+  while (c < nc) {
+    S v[U];
+    int cc[U], rr[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      cc[q] = c;
+      rr[q] = 32 * k + lane;
+      v[q] = (c < nc && rr[q] < m) ? src[(size_t)c * lds + rr[q]] : S(0);
+      k += kWarps;
+      while (k >= chunks) {
+        k -= chunks;
+        ++c;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+      if (cc[q] < nc && rr[q] < m) dst[(size_t)cc[q] * ldd + rr[q]] = (D)v[q];
+  }
 }
 
 // Reduction record of the panel pivot search: magnitude, row, signed value.
@@ -576,7 +602,7 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = V(0);
         // unrolled so that the loads of M (global memory) are in flight together
-#pragma unroll 8
+#pragma unroll 16
         for (int j = 0; j < bs; ++j) {
           const V m = (V)M[(size_t)(b0 + j) * ldm + r];
 #pragma unroll
@@ -592,7 +618,7 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
       // with coalesced column loads, then lane i finishes row r0 + i
       T* tile = stage + (size_t)w * 32 * 33;
       for (int r0 = r_lo + 32 * w; r0 < r_hi; r0 += 32 * kWarps) {
-#pragma unroll 4
+#pragma unroll 8
         for (int i = 0; i < 32; ++i) {
           const int r = r0 + i;
           tile[i * 33 + lane] = (r < r_hi && lane < bs) ? M[(size_t)r * ldm + b0 + lane] : T(0);
@@ -701,8 +727,7 @@ __device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nr
 // R = B - A X in FP64 (A: n x n ld lda; X: n x nrhs ld n), writes R (ld n)
 // and the per-column max |r| to rmax_s[c].  For nrhs >= 3 the products run
 // on the FP64 tensor instruction (8 rows x 8 right-hand sides x 4 columns
-// per mma.sync, one warp per 8-row group); otherwise on DFMA, one thread
-// per row.
+// per mma.sync, a warp per 32 rows); otherwise on DFMA, one thread per row.
 __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
                                           const double* Xs, int nrhs, double* R, double* rmax_s, CtaRed& red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -710,33 +735,44 @@ __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda,
 #pragma unroll
   for (int c = 0; c < 8; ++c) mx[c] = 0.0;
   if (nrhs >= 3) {
+    // a warp pass covers 4 row groups (32 rows): four independent
+    // accumulator chains and four loads of A per lane per K step
+    constexpr int G = 4;
     const int g = lane >> 2, t = lane & 3;
-    for (int r0 = 8 * w; r0 < n; r0 += 8 * kWarps) {
-      double c0 = 0.0, c1 = 0.0;
-      const int ra = r0 + g;  // A fragment row
-      const bool xok = g < nrhs;
+    const bool xok = g < nrhs;
+    for (int r0 = 8 * G * w; r0 < n; r0 += 8 * G * kWarps) {
+      double c0[G], c1[G];
+#pragma unroll
+      for (int q = 0; q < G; ++q) c0[q] = c1[q] = 0.0;
 #pragma unroll 4
       for (int k = 0; k < n; k += 4) {
         const int ka = k + t;
-        const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * lda + ra) : 0.0;
         const double b = (xok && ka < n) ? Xs[(size_t)g * n + ka] : 0.0;
-        dmma_8x8x4(c0, c1, a, b);
-      }
-      // c0, c1 = (A X)(r0 + g, 2t), (A X)(r0 + g, 2t + 1)
-      const int r = r0 + g;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int c = 2 * t + q;
-        double v = 0.0;
-        if (r < n && c < nrhs) {
-          v = B[(size_t)c * n + r] - (q ? c1 : c0);
-          R[(size_t)c * n + r] = v;
+        for (int q = 0; q < G; ++q) {
+          const int ra = r0 + 8 * q + g;  // A fragment row
+          const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * lda + ra) : 0.0;
+          dmma_8x8x4(c0[q], c1[q], a, b);
         }
-        // lane holds column c = 2t + q: fold into mx via a per-lane max
-        const double av = fabs(v);
+      }
+      // c0[q], c1[q] = (A X)(r0 + 8q + g, 2t), (A X)(r0 + 8q + g, 2t + 1)
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc)
-          if (cc == c) mx[cc] = fmax(mx[cc], av);
+      for (int q = 0; q < G; ++q) {
+        const int r = r0 + 8 * q + g;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * t + h;
+          double v = 0.0;
+          if (r < n && c < nrhs) {
+            v = B[(size_t)c * n + r] - (h ? c1[q] : c0[q]);
+            R[(size_t)c * n + r] = v;
+          }
+          // lane holds column c = 2t + h: fold into mx via a per-lane max
+          const double av = fabs(v);
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc)
+            if (cc == c) mx[cc] = fmax(mx[cc], av);
+        }
       }
     }
   } else {
@@ -745,7 +781,7 @@ __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda,
     const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < kRows; ++q) acc[q][0] = acc[q][1] = 0.0;
-#pragma unroll 4
+#pragma unroll 8
     for (int j = 0; j < n; ++j) {
       const double x0 = Xs[j], x1 = (nrhs > 1) ? Xs[(size_t)n + j] : 0.0;
 #pragma unroll

@@ -34,28 +34,22 @@ constexpr int kLB = 128;  // panel / block width of the large path
 
 // ------------------------------------------------------------ utilities
 // Bounded grid-wide barrier for cooperatively launched kernels (all CTAs
-// co-resident).  bar[0] counts arrivals, bar[1] is the generation.
-__device__ bool grid_barrier(unsigned* bar, unsigned G, int* err) {
+// co-resident), on an arrival counter that only grows (zeroed before the
+// launch): the k-th barrier of a launch completes when the counter reaches
+// k * G.  One atomic per CTA and polling; no reset and no generation word.
+__device__ bool grid_barrier_count(unsigned* bar, unsigned target, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     s_ok = 1;
-    volatile unsigned* gen = bar + 1;
-    const unsigned my = *gen;
     __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == G) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long it = 0;
-      while (*gen == my) {
-        if (++it > 200000000ll) {
-          s_ok = 0;
-          atomicExch(err, 1);
-          break;
-        }
+    atomicAdd(bar, 1u);
+    long long it = 0;
+    while (*(volatile unsigned*)bar < target) {
+      if (++it > 200000000ll) {
+        s_ok = 0;
+        atomicExch(err, 1);
+        break;
       }
     }
     __threadfence();
@@ -158,14 +152,15 @@ constexpr size_t trsm_smem() {
 // row, and the whole panel row) and the owner of the diagonal row publishes
 // that row; after one grid barrier every CTA picks the same pivot (largest
 // |value|, first row on ties), swaps locally and updates its own rows.
-// Buffers are double-buffered by column parity.
+// Buffers are double-buffered by column parity.  This is the FP64 panel;
+// the FP32 panel (k_lu_panel32, below) elects the pivot with an atomic.
 struct PanelBuf {
   void* cand;      // [2][G][4] of T: |v|, row, v, valid
   void* rows;      // [2][G][kLB] of T
   void* diag;      // [2][kLB] of T
   unsigned* bar;   // grid barrier (zeroed before the launch)
   int* err;
-  unsigned long long* key;  // [3] FP32 panels: (|v| bits << 32) | ~row, by atomicMax
+  unsigned long long* key;  // [3] k_lu_panel32: (|v| bits << 32) | ~row, by atomicMax
 };
 
 template <typename T>
@@ -215,21 +210,11 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
       int ii = s_idx[0];
       for (int k = 1; k < kWarps; ++k)
         if (s_best[k] > bb || (s_best[k] == bb && s_idx[k] < ii)) { bb = s_best[k]; ii = s_idx[k]; bv = s_val[k]; }
-      if constexpr (sizeof(T) == 4) {
-        // one atomic per CTA: the largest key is the largest |v|, then the
-        // smallest row (first index on ties)
-        if (ii != 0x7fffffff && bb >= T(0))
-          atomicMax(pb.key + c % 3,
-                    ((unsigned long long)__float_as_uint((float)bb) << 32) | (0xffffffffull - (unsigned)ii));
-        // the next column's key was last read after barrier c-2: reset it now
-        if (b == 0) pb.key[(c + 1) % 3] = 0ull;
-      } else {
-        T* cd = candT + ((size_t)buf * G + b) * 4;
-        cd[0] = bb;
-        cd[1] = (T)ii;
-        cd[2] = bv;
-        cd[3] = (ii != 0x7fffffff && bb >= T(0)) ? T(1) : T(0);
-      }
+      T* cd = candT + ((size_t)buf * G + b) * 4;
+      cd[0] = bb;
+      cd[1] = (T)ii;
+      cd[2] = bv;
+      cd[3] = (ii != 0x7fffffff && bb >= T(0)) ? T(1) : T(0);
       s_p = ii;
     }
     __syncthreads();
@@ -242,22 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
         for (int k = tid; k < kb; k += kThreads) diagT[(size_t)buf * kLB + k] = S[(c - rlo) * (kLB + 1) + k];
     }
     __threadfence();
-    if (!grid_barrier(pb.bar, (unsigned)G, pb.err)) return;
-    if constexpr (sizeof(T) == 4) {
-      // the winner is the key; its row (owner: row / R) holds the pivot
-      if (tid == 0) {
-        const unsigned long long key = *(volatile unsigned long long*)(pb.key + c % 3);
-        const int ii = key ? (int)(0xffffffffull - (key & 0xffffffffull)) : 0x7fffffff;
-        const int wb = (ii != 0x7fffffff) ? ii / R : -1;
-        const T bv = (wb >= 0 && wb < G) ? ((volatile T*)rowsT)[((size_t)buf * G + wb) * kLB + c] : T(0);
-        s_p = ii;
-        s_wb = wb;
-        s_pv = bv;
-        s_stop = (wb < 0 || wb >= G || ii < c || ii >= m || bv == T(0) || bv != bv) ? 1 : 0;
-        if (s_stop && b == 0) *fail = k0 + c + 1;
-        if (!s_stop && b == 0) piv[k0 + c] = k0 + ii;
-      }
-    } else {
+    if (!grid_barrier_count(pb.bar, (unsigned)(c + 1) * (unsigned)G, pb.err)) return;
     // every CTA finds the same winner: the candidates are read in parallel
     // (one per thread) and reduced (largest |v|, then smallest row)
     {
@@ -295,7 +265,6 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
         if (!s_stop && b == 0) piv[k0 + c] = k0 + ii;
       }
     }
-    }
     __syncthreads();
     if (s_stop) return;  // uniform across the grid: every CTA saw the same candidates
     const int p = s_p;
@@ -320,6 +289,113 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
       const T l = row[c];
       for (int k = c + 1 + lane; k < kb; k += 32) row[k] -= l * prow[k];
     }
+    __syncthreads();
+  }
+  for (int c = w; c < kb; c += kWarps)
+    for (int i = lane; i < nr; i += 32) W[(size_t)(k0 + c) * ldw + k0 + rlo + i] = S[i * (kLB + 1) + c];
+}
+
+// FP32 panel with the pivot elected by one 64-bit atomicMax per CTA and
+// column: key = (|v| bits << 32) | ~row, so the largest key is the largest
+// |v| and, among equal magnitudes, the first row.  Per column:
+//   1. each warp finds its best row among the CTA's rows >= c; warp 0
+//      reduces the eight, posts the key and publishes that row; the owner
+//      of row c publishes it (the row a swap moves down);
+//   2. grid barrier;
+//   3. every thread reads the key, then its element of the winning row and
+//      of row c (the two loads in flight together);
+//   4. each warp takes rows below the pivot: multiplier l = a(i,c) / pivot,
+//      a(i,k) -= l * u(k) for k > c; the swapped-in row is taken from the
+//      copy of row c and the pivot row is written over row c, so the swap
+//      needs no barrier of its own.
+// Keys are triple-buffered (the buffer for column c + 1 is cleared while
+// column c is elected), rows double-buffered by column parity.
+__global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, int ldw, int n, int k0, int kb,
+                                                        int R, int* __restrict__ piv, PanelBuf pb, int* fail) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* S = reinterpret_cast<float*>(smem);  // R x (kLB + 1)
+  float* prow = S + (size_t)R * (kLB + 1);     // the pivot row
+  float* drow = prow + kLB;                    // the old row c
+  __shared__ float s_best[kWarps];
+  __shared__ int s_idx[kWarps];
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int m = n - k0;
+  const int rlo = b * R, rhi = min(m, rlo + R);
+  const int nr = max(0, rhi - rlo);
+  for (int c = w; c < kb; c += kWarps)
+    for (int i = lane; i < nr; i += 32) S[i * (kLB + 1) + c] = W[(size_t)(k0 + c) * ldw + k0 + rlo + i];
+  __syncthreads();
+  float* rowsT = reinterpret_cast<float*>(pb.rows);
+  float* diagT = reinterpret_cast<float*>(pb.diag);
+  for (int c = 0; c < kb; ++c) {
+    const int buf = c & 1;
+    float best = -1.f;
+    int bi = 0x7fffffff;
+    for (int i = max(0, c - rlo) + tid; i < nr; i += kThreads) {
+      const float a = fabsf(S[i * (kLB + 1) + c]);
+      if (a > best) { best = a; bi = rlo + i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { s_best[w] = best; s_idx[w] = bi; }
+    if (c >= rlo && c < rhi && w == kWarps - 1)  // row c, as it stands, for the swap
+      for (int k = lane; k < kb; k += 32) diagT[(size_t)buf * kLB + k] = S[(c - rlo) * (kLB + 1) + k];
+    __syncthreads();
+    if (w == 0) {
+      best = lane < kWarps ? s_best[lane] : -1.f;
+      bi = lane < kWarps ? s_idx[lane] : 0x7fffffff;
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      best = __shfl_sync(0xffffffffu, best, 0);
+      bi = __shfl_sync(0xffffffffu, bi, 0);
+      if (bi != 0x7fffffff) {
+        for (int k = lane; k < kb; k += 32) rowsT[((size_t)buf * G + b) * kLB + k] = S[(bi - rlo) * (kLB + 1) + k];
+        if (lane == 0 && best >= 0.f)
+          atomicMax(pb.key + c % 3, ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffull - (unsigned)bi));
+      }
+      // the next column's key was last read after barrier c - 2: clear it now
+      if (b == 0 && lane == 0) pb.key[(c + 1) % 3] = 0ull;
+    }
+    __threadfence();
+    if (!grid_barrier_count(pb.bar, (unsigned)(c + 1) * (unsigned)G, pb.err)) return;
+    const unsigned long long key = *(volatile unsigned long long*)(pb.key + c % 3);
+    const int p = key ? (int)(0xffffffffull - (key & 0xffffffffull)) : 0x7fffffff;
+    const int wb = (p != 0x7fffffff) ? p / R : -1;
+    const bool okw = wb >= 0 && wb < G;
+    if (tid < kb) {
+      prow[tid] = okw ? ((volatile float*)rowsT)[((size_t)buf * G + wb) * kLB + tid] : 0.f;
+      drow[tid] = ((volatile float*)diagT)[(size_t)buf * kLB + tid];
+    }
+    __syncthreads();
+    const float pv = prow[c];
+    const bool stop = !okw || p < c || p >= m || pv == 0.f || pv != pv;  // uniform: the same key everywhere
+    if (tid == 0 && b == 0) {
+      if (stop) *fail = k0 + c + 1;
+      else piv[k0 + c] = k0 + p;
+    }
+    if (stop) return;
+    const float inv = 1.f / pv;
+    const int pl = (p != c && p >= rlo && p < rhi) ? p - rlo : -1;  // the swapped-in row, if here
+    for (int i = max(0, c + 1 - rlo) + w; i < nr; i += kWarps) {
+      float* row = S + i * (kLB + 1);
+      const float* src = (i == pl) ? drow : row;
+      const float l = src[c] * inv;
+      if (i == pl)
+        for (int k = lane; k < c; k += 32) row[k] = drow[k];
+      for (int k = c + 1 + lane; k < kb; k += 32) row[k] = src[k] - l * prow[k];
+      __syncwarp();
+      if (lane == 0) row[c] = l;
+    }
+    if (p != c && c >= rlo && c < rhi)  // the pivot row moves up to row c
+      for (int k = tid; k < kb; k += kThreads) S[(c - rlo) * (kLB + 1) + k] = prow[k];
     __syncthreads();
   }
   for (int c = w; c < kb; c += kWarps)
@@ -828,6 +904,7 @@ struct Fac {  // a factorisation of the large path and its scratch
   PanelBuf pb;
   size_t panel_smem;
   WaveBuf wb;
+  int gemm_mode = 3;  // FP32 factors: operand mode of the trailing updates (launch_gemm_tc)
 };
 
 template <typename T>
@@ -883,15 +960,15 @@ int apply_large(const Fac<T>& f, bool lu, int n, V* x, int nrhs, bool trans, V* 
 
 template <typename T>
 cudaError_t gemm_update(T* C, int ldc, const T* A, int lda, const T* B, int ldb, int M, int N, int K, bool tb,
-                        bool lower, int* err, cudaStream_t st);
+                        bool lower, int* err, int mode, cudaStream_t st);
 template <>
 cudaError_t gemm_update<float>(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
-                               int K, bool tb, bool lower, int* err, cudaStream_t st) {
-  return launch_gemm_tc(C, ldc, A, lda, B, ldb, M, N, K, 3, err, st, tb, lower);
+                               int K, bool tb, bool lower, int* err, int mode, cudaStream_t st) {
+  return launch_gemm_tc(C, ldc, A, lda, B, ldb, M, N, K, mode, err, st, tb, lower);
 }
 template <>
 cudaError_t gemm_update<double>(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N,
-                                int K, bool tb, bool lower, int* err, cudaStream_t st) {
+                                int K, bool tb, bool lower, int* err, int, cudaStream_t st) {
   dim3 g((M + kDmM - 1) / kDmM, (N + kDmN - 1) / kDmN);
   if (tb && lower) k_gemm_dmma<true, true><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
   else if (tb) k_gemm_dmma<true, false><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
@@ -910,7 +987,10 @@ int set_large_attrs() {
   LCK(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   LCK(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   // the panel kernel also has a little static shared memory
-  LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  if constexpr (sizeof(T) == 4)
+    LCK(cudaFuncSetAttribute(k_lu_panel32, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  else
+    LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   LCK(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)wave_smem<T, float>()));
   LCK(cudaFuncSetAttribute(k_trsv_wave<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -934,7 +1014,7 @@ int chol_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
       k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 1, 0);
       T* L21 = f.W + (size_t)k0 * f.ldw + k0 + kb;
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, L21, f.ldw, L21, f.ldw, rest, rest, kb,
-                         true, true, f.fail + 1, st));
+                         true, true, f.fail + 1, f.gemm_mode, st));
     }
   }
   LCK(cudaGetLastError());
@@ -953,7 +1033,7 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     const int kb = std::min(kLB, n - k0), m = n - k0;
     const int G = num_sms;
     const int R = (m + G - 1) / G;
-    const size_t psmem = sizeof(T) * ((size_t)R * (kLB + 1) + kLB) + 64;
+    const size_t psmem = sizeof(T) * ((size_t)R * (kLB + 1) + 2 * kLB) + 64;
     if (psmem > 226 * 1024) return ASOLVE_E_UNSUPPORTED;
     LCK(cudaMemsetAsync(f.pb.bar, 0, sizeof(unsigned) * 2, st));
     LCK(cudaMemsetAsync(f.pb.key, 0, sizeof(unsigned long long) * 3, st));
@@ -963,14 +1043,17 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     PanelBuf pb = f.pb;
     int* fail = f.fail;
     void* args[] = {&W, &ldw, &n, &k0, (void*)&kb, (void*)&R, &piv, &pb, &fail};
-    LCK(cudaLaunchCooperativeKernel((void*)k_lu_panel<T>, dim3(G), dim3(kThreads), args, psmem, st));
+    const void* kern;
+    if constexpr (sizeof(T) == 4) kern = (const void*)k_lu_panel32;
+    else kern = (const void*)k_lu_panel<T>;
+    LCK(cudaLaunchCooperativeKernel(kern, dim3(G), dim3(kThreads), args, psmem, st));
     k_swap_rows<T><<<(n + 255) / 256, 256, 0, st>>>(f.W, f.ldw, n, k0, kb, f.piv);
     const int rest = n - k0 - kb;
     if (rest > 0) {
       k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 0, 1);
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, f.W + (size_t)k0 * f.ldw + k0 + kb,
                          f.ldw, f.W + (size_t)(k0 + kb) * f.ldw + k0, f.ldw, rest, rest, kb, false, false,
-                         f.fail + 1, st));
+                         f.fail + 1, f.gemm_mode, st));
     }
   }
   LCK(cudaGetLastError());
@@ -1310,7 +1393,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     info->rcond = kept->rcond;
     info->precision = kept->precision;
     info->detail = kept->detail | 8;
-    if (kept->precision == ASOLVE_PREC_MIXED) {
+    if (kept->precision != ASOLVE_PREC_FP64) {  // FP32-stored factors
       if ((rc = set_large_attrs<float>())) return rc;
       Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
       int iters = 0;
@@ -1362,10 +1445,17 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     const bool poor = !no_rcond && !(kept->rcond >= a.rcond_threshold);
     return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
   }
-  // ---- mixed precision: FP32 factors, FP64 refinement
-  if (a.precision == ASOLVE_PREC_MIXED && !(sr.flags & SF_NORM_FP64)) {
+  // ---- mixed precision: FP32 factors (trailing updates as 3xTF32, BF16 or
+  // FP16 tensor products), FP64 refinement
+  if (a.precision != ASOLVE_PREC_FP64 && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
     Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
+    f.gemm_mode = a.precision == ASOLVE_PREC_BF16 ? kGemmBf16 : (a.precision == ASOLVE_PREC_FP16 ? kGemmFp16 : 3);
+    // the refinement converges while kappa times the factors' relative
+    // error stays below one: the 16-bit updates lower the kappa limit
+    const double klim = a.precision == ASOLVE_PREC_BF16   ? fmin(a.ir_kappa_limit, kKappaLimitBf16)
+                        : a.precision == ASOLVE_PREC_FP16 ? fmin(a.ir_kappa_limit, kKappaLimitFp16)
+                                                          : a.ir_kappa_limit;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool try_chol = chol && attempt == 0;
       if (!chol && attempt == 1) break;
@@ -1386,7 +1476,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         rc = est_large<float>(n, (float*)ev, (float*)exi, dscal, dint, apply, st, &est);
         if (rc) return rc;
         rcv = rcond_of(sr.norm1, est);
-        gate_ok = rcv >= 1.0 / a.ir_kappa_limit;
+        gate_ok = rcv >= 1.0 / klim;
       }
       if (!gate_ok) { detail |= 1; break; }
       int iters = 0;
@@ -1400,10 +1490,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         info->rcond = rcv;
         info->berr = berr;
         info->ir_iters = iters;
-        info->precision = ASOLVE_PREC_MIXED;
+        info->precision = a.precision;
         info->detail = detail;
         if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
-        keep(ASOLVE_PREC_MIXED, lu);
+        keep(a.precision, lu);
         return info->status = ASOLVE_OK;
       }
       detail |= 2;

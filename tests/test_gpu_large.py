@@ -125,3 +125,32 @@ def test_large_chol_fail_to_lu(ctx, orc):
     assert info["route"] == 5 and rc == 0, info
     _, berr = orc.residual_dot2(A, X, B)
     assert berr.max() <= 1e-13
+
+
+@pytest.mark.parametrize("prec_name", ["bf16", "fp16"])
+@pytest.mark.parametrize("kind,n,kappa", [("general", 2048, None), ("spd", 1411, None), ("general", 1100, 1e2),
+                                          ("spd", 2304, 1e2), ("general", 1500, 1e6)])
+def test_large_16bit_updates(orc, prec_name, kind, n, kappa):
+    """Trailing updates as single 16-bit tensor products (BF16, or FP16 with
+    per-tile scaling), FP64 refinement: the answer meets the same bars as
+    the FP64 path; well-conditioned systems finish in the 16-bit mode, and
+    kappa above the mode's limit goes to the FP64 factorisation."""
+    from paper_2007_11208_gb300 import asolve, build
+    build.build()
+    prec = {"bf16": asolve.PREC_BF16, "fp16": asolve.PREC_FP16}[prec_name]
+    rng = np.random.default_rng(n + (0 if kappa is None else int(np.log10(kappa))))
+    A = make(kind, n, rng) if kappa is None else spectrum(n, kappa, rng, kind == "spd")
+    B = rng.standard_normal((n, 2))
+    c = asolve.Context(precision=prec)
+    rc, info, X = solve_gpu(c, A, B)
+    c.close()
+    Xo, io = orc.solve(A, B)
+    assert rc == io["status"] == 0, (rc, info)
+    assert (info["cls"], info["route"]) == (io["cls"], io["route"]), (info, io)
+    _, berr = orc.residual_dot2(A, X, B)
+    assert berr.max() <= 1e-13, (berr, info)
+    assert fwd_err(X, Xo) <= 2.0 ** -52 * n * kappa_inf(A), (fwd_err(X, Xo), info)
+    if kappa is not None and kappa >= 1e6:
+        assert info["precision"] == asolve.PREC_FP64 and info["detail"] & 1, info
+    elif kappa is None:
+        assert info["precision"] == prec and info["ir_iters"] >= 1, info
