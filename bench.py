@@ -16,12 +16,14 @@ is timed beside it.
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) each rank solves its own batch (weak scaling).
 
-Two more workloads print their own JSON line (not the headline):
+More workloads print their own JSON line (not the headline):
   --workload large   single dense systems n in --sizes (default 8192,16384),
                      general U diag(logspace(0,-k)) V^T and SPD with kappa in
                      {1e2, 1e4, 1e6}, nrhs in {1, 64}: mixed precision
                      (FP32 factors on tcgen05, FP64 refinement) vs the FP64
                      path, time per solve with CUDA events.
+  --workload band    one band system in band storage, n = 10^6, kl = ku in
+                     {2, 8, 32}, nrhs in {1, 16}: time per asolve_solve_band.
   --workload plain   five single systems at n = 200 (general N(0,1), lower
                      triangular, SPD, tridiagonal, U diag(logspace(0,-14)) V^T
                      with Haar U, V), one right-hand side: latency of one
@@ -538,6 +540,72 @@ def large_workload(args):
         "clocks": clk.summary(), "cases": cases}), flush=True)
 
 
+# --------------------------------------------------------------- band
+def band_workload(args):
+    """Memory-bound configuration: one band system of order n = 10^6 in
+    band storage, kl = ku = k, off-diagonal N(0,1), diagonal 1 + row abs
+    sum, nrhs right-hand sides; time of one asolve_solve_band call (scan of
+    the band, GBTRF-equivalent factorisation, solve, rcond estimate,
+    backward error) with CUDA events."""
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.band_n
+    ks = [int(x) for x in args.band_k.split(",")]
+    nrhs_list = [int(x) for x in args.band_nrhs.split(",")]
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    ctx = asolve.Context()
+    st = torch.cuda.ExternalStream(ctx.stream)
+    rows = []
+    with ClockSampler(0) as clk:
+        for k in ks:
+            g = synth.gen(1000 + k, dev)
+            AB = synth.band_storage_dd(n, k, k, g, device=dev)  # row j = column j of the band layout
+            Bm = synth.rhs(n, max(nrhs_list), g, dev)
+            for nrhs in nrhs_list:
+                B = Bm[:nrhs].contiguous()
+                X = torch.zeros_like(B)
+                rc, info = ctx.solve_band(AB, 2 * k + 1, k, k, B, n, nrhs, X, asolve.BERR)  # warm-up
+                times = []
+                for _ in range(args.steps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(st)
+                    rc, info = ctx.solve_band(AB, 2 * k + 1, k, k, B, n, nrhs, X, asolve.BERR)
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = statistics.median(times)
+                io_bytes = 8.0 * n * (2 * k + 1) + 16.0 * n * nrhs  # band of A, B, X: each once
+                row = {"n": n, "kl": k, "ku": k, "nrhs": nrhs, "ms": ms, "rc": rc, "route": info["route"],
+                       "kl_found": info["kl"], "ku_found": info["ku"], "berr": info["berr"],
+                       "rcond": info["rcond"], "io_bytes": io_bytes,
+                       "io_gbs": io_bytes / (ms * 1e-3) / 1e9}
+                row["io_frac_of_hbm"] = row["io_gbs"] / hbm
+                rows.append(row)
+                log(f"band n={n} k={k} nrhs={nrhs}: {ms:.2f} ms rc={rc} berr={info['berr']:.2e} "
+                    f"A+B+X at {row['io_gbs']:.1f} GB/s")
+            del AB, Bm
+            torch.cuda.empty_cache()
+    ctx.close()
+    head = rows[0]
+    ok = all(r["rc"] == 0 and r["berr"] <= BERR_BAR for r in rows)
+    print(json.dumps({
+        "metric": "solves/s at backward err <=1e-13 (band system, n = 10^6)",
+        "value": (1000.0 / head["ms"]) if ok else 0.0, "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "replicas only", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"band: n={n}, kl=ku in {ks}, nrhs in {nrhs_list}, diagonally dominant, "
+                               "band storage", "l2": "inputs larger than L2"},
+        "roofline_note": "the band factorisation is a sequential chain along n; io_gbs is the band of A, "
+                         "B and X read or written once over the whole call, against the measured HBM copy "
+                         "bandwidth",
+        "clocks": clk.summary(), "cases": rows}), flush=True)
+
+
 # --------------------------------------------------------------- plain
 def plain_workload(args):
     from paper_2007_11208_gb300 import asolve, build, synth
@@ -725,7 +793,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per GPU (smaller values are for profiling runs only)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve", "plain"])
+    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve", "plain", "band"])
+    ap.add_argument("--band-n", type=int, default=1_000_000, help="band: order")
+    ap.add_argument("--band-k", default="2,8,32", help="band: kl = ku values")
+    ap.add_argument("--band-nrhs", default="1,16", help="band: right-hand-side counts")
     ap.add_argument("--reps", type=int, default=1000, help="plain: repetitions per system")
     ap.add_argument("--sizes", default="8192,16384", help="large: matrix sizes")
     ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds (general, spd, lower)")
@@ -745,6 +816,8 @@ def main():
         return serve_workload(args)
     if args.workload == "plain":
         return plain_workload(args)
+    if args.workload == "band":
+        return band_workload(args)
     if args.impl == "reference":
         reference(args)
     else:

@@ -549,9 +549,13 @@ struct WaveBW {
   static constexpr int value = sizeof(T) == 4 ? 128 : 64;
 };
 
+// Dinv (optional): inverses of the BW x BW diagonal blocks of the triangle,
+// block b at Dinv + b * BW * BW, column-major (k_diag_inv).  With them the
+// diagonal step is a product with the inverse instead of a substitution.
 template <typename T, typename V>
 __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__ M, int ldm, int n, int lower, int trans,
-                                                       int unit, V* x, int ldx, int nrhs, int* flags, int* err) {
+                                                       int unit, V* x, int ldx, int nrhs, int* flags, int* err,
+                                                       const T* __restrict__ Dinv) {
   constexpr int BW = WaveBW<T>::value;
   constexpr int P = kThreads / BW;          // thread parts per row
   constexpr int NQ = kWaveNR / P;           // right-hand sides per thread (multi mode)
@@ -579,6 +583,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__
     }
     cp_async_commit();
   };
+  // the inverse of diagonal block bi (op applies to it as to T's tiles)
+  auto issue_inv = [&](int buf, int bi) {
+    const T* src = Dinv + (size_t)bi * BW * BW;
+    for (int e = tid; e < BW * BW; e += kThreads) {
+      const int c = e / BW, rr = e % BW;
+      cp_async_el<sizeof(T)>(&tile[buf][c][rr], src + (size_t)c * BW + rr);
+    }
+    cp_async_commit();
+  };
   // element (i, j) of op(T)(bi, bj) in buffer buf
   auto E = [&](int buf, int i, int j) -> V { return trans ? (V)tile[buf][i][j] : (V)tile[buf][j][i]; };
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
@@ -595,12 +608,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__
       acc[q] = (on && r < bs) ? x[(size_t)(c0 + (single ? 0 : c)) * ldx + r0 + r] : V(0);
     }
     // first tile: pair (o, 0), or the diagonal block when o == 0
-    issue(0, bo, o > 0 ? (elower ? 0 : nblk - 1) : bo);
+    if (o > 0) issue(0, bo, elower ? 0 : nblk - 1);
+    else if (Dinv) issue_inv(0, bo);
+    else issue(0, bo, bo);
     for (int p = 0; p < o; ++p) {
       const int bp = elower ? p : nblk - 1 - p;
       const int buf = p & 1;
       // prefetch the next pair's tile (or the diagonal block) meanwhile
       if (p + 1 < o) issue(buf ^ 1, bo, elower ? p + 1 : nblk - 2 - p);
+      else if (Dinv) issue_inv(buf ^ 1, bo);
       else issue(buf ^ 1, bo, bo);
       if (tid == 0) {
         const int* f = flags + chunk * nblk + p;
@@ -655,6 +671,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) xs[part + P * q][r] = acc[q];
+    }
+    if (Dinv) {
+      // x = inv(D) rhs: the same product as the pair updates, from zero
+      __syncthreads();
+      if (single) {
+        const int j0 = part * (BW / P);
+        V t = V(0);
+#pragma unroll 8
+        for (int j = j0; j < j0 + BW / P; ++j) t += E(dbuf, r, j) * xs[0][j];
+        xs[1 + part][r] = t;  // rows 1..P of xs are free in this mode
+        __syncthreads();
+        if (part == 0 && r < bs) {
+          V u = xs[1][r];
+#pragma unroll
+          for (int k = 1; k < P; ++k) u += xs[1 + k][r];
+          x[(size_t)c0 * ldx + r0 + r] = u;
+        }
+      } else {
+        V t[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) t[q] = V(0);
+#pragma unroll 4
+        for (int j = 0; j < BW; ++j) {
+          const V e = E(dbuf, r, j);
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) t[q] += e * xs[part + P * q][j];
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int c = part + P * q;
+          if (c < nc && r < bs) x[(size_t)(c0 + c) * ldx + r0 + r] = t[q];
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release(flags + it, 1);
+      continue;
     }
     // reciprocals of the diagonal (one division per row, off the chain)
     __shared__ V s_rinv[BW];
@@ -887,6 +940,54 @@ struct WaveBuf {
   int grid; // co-resident CTAs
 };
 
+// Inverses of the 128 x 128 diagonal blocks of FP32 factors, for the
+// wavefront solve's diagonal step: Linv[b] = inv(L(b, b)) (unit diagonal
+// when unitL; only the triangle below the diagonal is read),
+// Uinv[b] = inv(U(b, b)) (upper triangle with the diagonal), each block
+// column-major with ld 128 and the identity past the matrix's last row.
+// One CTA per block: threads 0..127 form the columns of inv(L), threads
+// 128..255 those of inv(U), by substitution against the identity (rows in
+// increasing, respectively decreasing, order).  Either output may be null.
+constexpr int kInvBW = 128;
+constexpr size_t kDiagInvSmem = sizeof(float) * 3 * kInvBW * (kInvBW + 1);
+__global__ void __launch_bounds__(kThreads, 1) k_diag_inv(const float* __restrict__ W, int ldw, int n, int unitL,
+                                                        float* __restrict__ Linv, float* __restrict__ Uinv) {
+  constexpr int BW = kInvBW, LD = BW + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* D = reinterpret_cast<float*>(smem);  // D[i * LD + k] = W(r0 + i, r0 + k)
+  float* XL = D + BW * LD;                    // XL[i * LD + j] = inv(L)(i, j)
+  float* XU = XL + BW * LD;
+  const int b = blockIdx.x, r0 = b * BW, bs = min(BW, n - r0), tid = threadIdx.x;
+  for (int e = tid; e < BW * BW; e += kThreads) {
+    const int k = e / BW, i = e % BW;  // column k, row i: coalesced over i
+    D[i * LD + k] = (i < bs && k < bs) ? W[(size_t)(r0 + k) * ldw + r0 + i] : 0.f;
+    XL[i * LD + k] = 0.f;
+    XU[i * LD + k] = 0.f;
+  }
+  __syncthreads();
+  const int j = tid & (BW - 1);
+  if (tid < BW) {
+    if (Linv)
+      for (int i = 0; i < BW; ++i) {
+        float s = (i == j) ? 1.f : 0.f;
+        for (int k = 0; k < i; ++k) s -= D[i * LD + k] * XL[k * LD + j];
+        XL[i * LD + j] = (i >= bs || unitL) ? s : s / D[i * LD + i];
+      }
+  } else if (Uinv) {
+    for (int i = BW - 1; i >= 0; --i) {
+      float s = (i == j) ? 1.f : 0.f;
+      for (int k = i + 1; k < BW; ++k) s -= D[i * LD + k] * XU[k * LD + j];
+      XU[i * LD + j] = (i >= bs) ? s : s / D[i * LD + i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < BW * BW; e += kThreads) {
+    const int k = e / BW, i = e % BW;
+    if (Linv) Linv[(size_t)b * BW * BW + (size_t)k * BW + i] = XL[i * LD + k];
+    if (Uinv) Uinv[(size_t)b * BW * BW + (size_t)k * BW + i] = XU[i * LD + k];
+  }
+}
+
 template <typename T, typename V>
 constexpr size_t wave_smem() {
   return sizeof(T) * 2 * (size_t)WaveBW<T>::value * (WaveBW<T>::value + 1) +
@@ -905,11 +1006,13 @@ struct Fac {  // a factorisation of the large path and its scratch
   size_t panel_smem;
   WaveBuf wb;
   int gemm_mode = 3;  // FP32 factors: operand mode of the trailing updates (launch_gemm_tc)
+  const T* dinvL = nullptr;  // FP32 factors: inverses of the 128 x 128 diagonal blocks (k_diag_inv)
+  const T* dinvU = nullptr;
 };
 
 template <typename T>
 int tri_solve_large(const T* M, int ldm, int n, bool lower, bool trans, bool unit, void* xv, int nrhs,
-                    bool vfloat, const WaveBuf& wb, cudaStream_t st) {
+                    bool vfloat, const WaveBuf& wb, cudaStream_t st, const T* dinv = nullptr) {
   const int nblk = (n + WaveBW<T>::value - 1) / WaveBW<T>::value;
   const int items = nblk * ((nrhs + kWaveNR - 1) / kWaveNR);
   if (items > wb.cap) return ASOLVE_E_NOMEM;
@@ -919,14 +1022,15 @@ int tri_solve_large(const T* M, int ldm, int n, bool lower, bool trans, bool uni
   int* fl = wb.flags;
   int* er = wb.err;
   const T* Mp = M;
+  const T* Dp = dinv;
   if (vfloat) {
     float* x = static_cast<float*>(xv);
-    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er};
+    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er, &Dp};
     LCK(cudaLaunchCooperativeKernel((void*)k_trsv_wave<T, float>, dim3(G), dim3(kThreads), args,
                                     wave_smem<T, float>(), st));
   } else {
     double* x = static_cast<double*>(xv);
-    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er};
+    void* args[] = {&Mp, &ld, &nn, &lw, &tw, &uw, &x, &ldx, &nr, &fl, &er, &Dp};
     LCK(cudaLaunchCooperativeKernel((void*)k_trsv_wave<T, double>, dim3(G), dim3(kThreads), args,
                                     wave_smem<T, double>(), st));
   }
@@ -941,21 +1045,21 @@ int apply_large(const Fac<T>& f, bool lu, int n, V* x, int nrhs, bool trans, V* 
     if (!trans) {
       k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 0);
       LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
-      int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, true, x, nrhs, vf, f.wb, st);
+      int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, true, x, nrhs, vf, f.wb, st, f.dinvL);
       if (rc) return rc;
-      return tri_solve_large<T>(f.W, f.ldw, n, false, false, false, x, nrhs, vf, f.wb, st);
+      return tri_solve_large<T>(f.W, f.ldw, n, false, false, false, x, nrhs, vf, f.wb, st, f.dinvU);
     }
-    int rc = tri_solve_large<T>(f.W, f.ldw, n, false, true, false, x, nrhs, vf, f.wb, st);
+    int rc = tri_solve_large<T>(f.W, f.ldw, n, false, true, false, x, nrhs, vf, f.wb, st, f.dinvU);
     if (rc) return rc;
-    rc = tri_solve_large<T>(f.W, f.ldw, n, true, true, true, x, nrhs, vf, f.wb, st);
+    rc = tri_solve_large<T>(f.W, f.ldw, n, true, true, true, x, nrhs, vf, f.wb, st, f.dinvL);
     if (rc) return rc;
     k_permute<V><<<g, 256, 0, st>>>(x, tmp, n, nrhs, f.perm, 1);
     LCK(cudaMemcpyAsync(x, tmp, sizeof(V) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
     return ASOLVE_OK;
   }
-  int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, false, x, nrhs, vf, f.wb, st);
+  int rc = tri_solve_large<T>(f.W, f.ldw, n, true, false, false, x, nrhs, vf, f.wb, st, f.dinvL);
   if (rc) return rc;
-  return tri_solve_large<T>(f.W, f.ldw, n, true, true, false, x, nrhs, vf, f.wb, st);
+  return tri_solve_large<T>(f.W, f.ldw, n, true, true, false, x, nrhs, vf, f.wb, st, f.dinvL);
 }
 
 template <typename T>
@@ -987,8 +1091,10 @@ int set_large_attrs() {
   LCK(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   LCK(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   // the panel kernel also has a little static shared memory
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4) {
     LCK(cudaFuncSetAttribute(k_lu_panel32, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+    LCK(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagInvSmem));
+  }
   else
     LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   LCK(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1144,6 +1250,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   size_t b = 0;
   b += sizeof(double) * ldw * n + 256;                 // working matrix (FP64 worst case)
   b += 2 * sizeof(int) * n + 512;                      // piv, perm
+  b += 2 * sizeof(float) * (size_t)((n + kInvBW - 1) / kInvBW) * kInvBW * kInvBW + 512;  // diagonal-block inverses
   b += sizeof(double) * kLB * kLB + 256;               // Dtmp
   b += 4 * sizeof(double) * (size_t)n * nrhs + 1024;   // R, Xs, tmp, (spare)
   b += 4 * sizeof(double) * (size_t)n + 512;           // estimator vectors
@@ -1169,7 +1276,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   void* Wv = ar.take(sizeof(double) * (size_t)ldw * n);
   int* piv = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
   int* perm = static_cast<int*>(ar.take(sizeof(int) * (size_t)n));
-  if (!Wv || !piv || !perm) return ASOLVE_E_NOMEM;
+  const size_t inv_elems = (size_t)((n + kInvBW - 1) / kInvBW) * kInvBW * kInvBW;
+  float* dinvL = static_cast<float*>(ar.take(sizeof(float) * inv_elems));
+  float* dinvU = static_cast<float*>(ar.take(sizeof(float) * inv_elems));
+  if (!Wv || !piv || !perm || !dinvL || !dinvU) return ASOLVE_E_NOMEM;
   LargeReuse* kept = a.reuse;
   constexpr uint32_t kRouteFlags = ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_NO_APPROX;
   const bool reuse_hit = kept && kept->valid && kept->A == a.A && kept->n == a.n &&
@@ -1396,6 +1506,8 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if (kept->precision != ASOLVE_PREC_FP64) {  // FP32-stored factors
       if ((rc = set_large_attrs<float>())) return rc;
       Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
+      f.dinvL = dinvL;  // kept with the factor (they follow it in the workspace)
+      f.dinvU = kept->lu ? dinvU : nullptr;
       int iters = 0;
       double berr = NAN;
       const int ok = mixed_ir(f, kept->lu != 0, iters, berr);
@@ -1468,6 +1580,12 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         break;  // FP32 factorisation failed: FP64 path decides
       }
       const bool lu = !try_chol;
+      // inverses of the diagonal blocks for the wavefront solves
+      k_diag_inv<<<(n + kInvBW - 1) / kInvBW, kThreads, kDiagInvSmem, st>>>(f.W, ldw, n, lu ? 1 : 0, dinvL,
+                                                                            lu ? dinvU : nullptr);
+      LCK(cudaGetLastError());
+      f.dinvL = dinvL;
+      f.dinvU = lu ? dinvU : nullptr;
       double rcv = NAN;
       bool gate_ok = true;
       if (!no_rcond) {

@@ -271,11 +271,13 @@ def test_concurrent_producers(lib_ready):
 
 def test_lanes_overlap(lib_ready):
     """Small requests submitted right after a large one are not held behind
-    it: the batch lane solves them while the large lane factors."""
+    it: the batch lane solves them while the large lane factors.  The
+    pattern runs twice and the second round is judged, so that first-use
+    costs (workspaces, graph capture) do not decide the order."""
     from paper_2007_11208_gb300 import asolve
     rng = np.random.default_rng(31)
     ctx = asolve.Context()
-    nL = 4096
+    nL = 6144
     AL = _mat("general", nL, rng)
     bL = rng.standard_normal((nL, 1))
     dAL = dev_colmajor(AL)
@@ -289,24 +291,25 @@ def test_lanes_overlap(lib_ready):
         dB, _ = dev_rhs(B, n)
         small.append((dev_colmajor(A), dB, torch.zeros_like(dB), n))
     torch.cuda.synchronize()
-    rc, tL = ctx.submit(dAL, dBL, nL, 1, dXL)
-    assert rc == asolve.OK
-    ts = []
-    for dA, dB, dX, n in small:
-        rc, t = ctx.submit(dA, dB, n, 1, dX)
+    for _ in range(2):
+        rc, tL = ctx.submit(dAL, dBL, nL, 1, dXL)
         assert rc == asolve.OK
-        ts.append(t)
-    lat_small = []
-    for t in ts:
-        st, info, lat = ctx.poll(t, -1)
+        ts = []
+        for dA, dB, dX, n in small:
+            rc, t = ctx.submit(dA, dB, n, 1, dX)
+            assert rc == asolve.OK
+            ts.append(t)
+        lat_small = []
+        for t in ts:
+            st, info, lat = ctx.poll(t, -1)
+            assert st == asolve.OK
+            lat_small.append(lat)
+        st, info, lat_large = ctx.poll(tL, -1)
         assert st == asolve.OK
-        lat_small.append(lat)
-    st, info, lat_large = ctx.poll(tL, -1)
-    assert st == asolve.OK
     # every small request finished before the large one
     assert max(lat_small) < lat_large, (max(lat_small), lat_large)
     stats = ctx.serve_stats()
-    assert stats["large_solves"] == 1 and stats["batches"] >= 1
+    assert stats["large_solves"] == 2 and stats["batches"] >= 2
     ctx.close()
 
 
