@@ -184,6 +184,25 @@ __device__ __forceinline__ void warp_argmax_first(T& v, int& idx) {
   }
 }
 
+// Pivot search of partial pivoting on a warp.  abs_key(v): the bit pattern
+// of |v| plus one (non-negative doubles order as unsigned integers), 0 for
+// NaN, which is never a pivot.  warp_first_max_key: the first lane holding
+// the largest non-zero key (high words reduced first, then low words among
+// the lanes that hold the largest high word), -1 if no lane has one; kmax
+// gets the key.
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  const double a = fabs(v);
+  return (a == a) ? (unsigned long long)__double_as_longlong(a) + 1ull : 0ull;
+}
+__device__ __forceinline__ int warp_first_max_key(unsigned long long key, unsigned long long& kmax) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  kmax = ((unsigned long long)mhi << 32) | mlo;
+  const unsigned ball = __ballot_sync(0xffffffffu, key != 0ull && hi == mhi && lo == mlo);
+  return ball ? __ffs(ball) - 1 : -1;
+}
+
 __device__ __forceinline__ int64_t ldg_i64(const int64_t* p) { return __ldg(p); }
 
 }  // namespace asv

@@ -24,6 +24,7 @@
 #include <string.h>
 
 #include "band_warp.cuh"
+#include "est_host.cuh"
 
 namespace asv {
 
@@ -142,13 +143,15 @@ __global__ void __launch_bounds__(32) k_band_lu_win(double* __restrict__ F, int 
     __syncwarp();
     double* cj = slot(j);
     const int km = min(kl, n - 1 - j);
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int t = lane; t <= km; t += 32) {
-      const double v = fabs(cj[kv + t]);
-      if (v > best) { best = v; bi = t; }
+    // the first largest |a(j+t, j)|, t = 0..km, in passes of 32 candidates
+    int bi = -1;
+    unsigned long long kbest = 0ull;
+    for (int t0 = 0; t0 <= km; t0 += 32) {
+      const int t = t0 + lane;
+      unsigned long long kp;
+      const int l = warp_first_max_key(t <= km ? abs_key(cj[kv + t]) : 0ull, kp);
+      if (l >= 0 && kp > kbest) { kbest = kp; bi = t0 + l; }
     }
-    warp_argmax_first(best, bi);
     if (bi < 0 || bi > km || !(cj[kv + bi] != 0.0)) {  // exact zero (or invalid) pivot
       if (lane == 0) *fail = j + 1;
       cp_wait_all();
@@ -361,6 +364,301 @@ __global__ void k_band_berr(const double* __restrict__ AB, int64_t ldab, int kud
   }
 }
 
+// ------------------------------------------------ partitioned sweeps
+// The solve with the band factors is four linear recurrences (sweeps) that
+// carry a window of the vector from step to step:
+//   SW_L  forward, step j = 0..n-1: window x[j..j+kl]; interchange with row
+//         piv[j], eliminate rows j+1.. with column j of L; out x[j]; in x[j+kl+1]
+//   SW_U  backward, i = n-1..0: element q = y[i-q], q <= kv; x_i = w0 / u_ii,
+//         w_q -= u(i-q, i) x_i; out x[i]; in y[i-kv-1]
+//   SW_UT forward, i = 0..n-1: w0 = b_i, w_q = z_{i-q}; z_i = (w0 - sum_q
+//         u(i-q, i) w_q) / u_ii; out z_i; in b_{i+1}
+//   SW_LT backward, j = n-1..0: window x[j..j+kl]; w0 -= sum_t l(j+t, j) w_t,
+//         interchange with row piv[j]; out x[j+kl]; in x[j-1] (the last step
+//         flushes x[0..kl])
+// Each step is affine in the window, so the n steps are cut into P blocks:
+//   maps: for every block, the window after it from each unit starting
+//         window with no inputs (one lane each) -- the block's matrix T_b;
+//         it depends on the factors only and is kept for every solve;
+//   part: from a zero window with the block's inputs -- the vector t_b;
+//   scan: one CTA chains W_{b+1} = T_b W_b + t_b from the true first window;
+//   out:  every block reruns its steps from W_b and writes its outputs.
+// The steps are those of the sequential sweeps; only the order in which
+// the contributions of earlier blocks are summed changes.
+enum : int { SW_L = 0, SW_U = 1, SW_UT = 2, SW_LT = 3 };
+
+struct SweepCtx {
+  const double* F;
+  int ldf, n, kl, ku;
+  const int* piv;
+  int L, P;  // steps per block, blocks
+};
+
+__host__ __device__ __forceinline__ int sw_ws(int kind, int kl, int ku) {
+  return (kind == SW_L || kind == SW_LT) ? kl + 1 : kl + ku + 1;
+}
+
+// one step of sweep KIND on the window w (element e in w[e], WM >= window
+// size); xin: inputs (null: none), out: outputs (null: not written)
+template <int KIND, int WM>
+__device__ __forceinline__ void sw_step(const SweepCtx& c, double (&w)[WM], int s, const double* __restrict__ xin,
+                                        double* __restrict__ out) {
+  const int n = c.n, kl = c.kl, kv = c.kl + c.ku;
+  if (KIND == SW_L) {
+    const int j = s;
+    const double* col = c.F + (size_t)j * c.ldf + kv;  // col[t] = l(j+t, j)
+    const int km = min(kl, n - 1 - j);
+    const int d = __ldg(c.piv + j) - j;
+    const double e0 = w[0];
+    double ed = e0;
+#pragma unroll
+    for (int t = 1; t < WM; ++t) ed = (t == d) ? w[t] : ed;
+#pragma unroll
+    for (int t = 1; t < WM; ++t) w[t] = (t == d) ? e0 : w[t];
+    w[0] = ed;
+#pragma unroll
+    for (int t = 1; t < WM; ++t)
+      if (t <= km) w[t] = fma(-__ldg(col + t), ed, w[t]);
+    if (out) out[j] = ed;
+#pragma unroll
+    for (int t = 0; t + 1 < WM; ++t) w[t] = w[t + 1];
+    w[WM - 1] = 0.0;
+    const double in = (xin && j + kl + 1 < n) ? xin[j + kl + 1] : 0.0;
+#pragma unroll
+    for (int t = 0; t < WM; ++t) w[t] = (t == kl) ? in : w[t];
+  } else if (KIND == SW_U) {
+    const int i = n - 1 - s;
+    const double* col = c.F + (size_t)i * c.ldf + kv;  // col[-q] = u(i-q, i)
+    const int lim = min(kv, i);
+    const double xi = w[0] / __ldg(col);
+#pragma unroll
+    for (int q = 1; q < WM; ++q)
+      if (q <= lim) w[q] = fma(-__ldg(col - q), xi, w[q]);
+    if (out) out[i] = xi;
+#pragma unroll
+    for (int q = 0; q + 1 < WM; ++q) w[q] = w[q + 1];
+    w[WM - 1] = 0.0;
+    const double in = (xin && i - kv - 1 >= 0) ? xin[i - kv - 1] : 0.0;
+#pragma unroll
+    for (int q = 0; q < WM; ++q) w[q] = (q == kv) ? in : w[q];
+  } else if (KIND == SW_UT) {
+    const int i = s;
+    const double* col = c.F + (size_t)i * c.ldf + kv;
+    const int lim = min(kv, i);
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 1; q < WM; ++q)
+      if (q <= lim) acc = fma(__ldg(col - q), w[q], acc);
+    const double zi = (w[0] - acc) / __ldg(col);
+    if (out) out[i] = zi;
+    w[0] = zi;
+#pragma unroll
+    for (int q = WM - 1; q >= 1; --q) w[q] = (q <= kv) ? w[q - 1] : 0.0;
+    w[0] = (xin && i + 1 < n) ? xin[i + 1] : 0.0;
+  } else {  // SW_LT
+    const int j = n - 1 - s;
+    const double* col = c.F + (size_t)j * c.ldf + kv;
+    const int km = min(kl, n - 1 - j);
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 1; t < WM; ++t)
+      if (t <= km) acc = fma(__ldg(col + t), w[t], acc);
+    const double v = w[0] - acc;
+    const int d = __ldg(c.piv + j) - j;
+    double ed = v;
+#pragma unroll
+    for (int t = 1; t < WM; ++t) ed = (t == d) ? w[t] : ed;
+#pragma unroll
+    for (int t = 1; t < WM; ++t) w[t] = (t == d) ? v : w[t];
+    w[0] = ed;
+    if (j == 0) {
+      if (out)
+#pragma unroll
+        for (int t = 0; t < WM; ++t)
+          if (t <= kl && t < n) out[t] = w[t];
+      return;
+    }
+    if (out && j + kl < n) {
+      double ek = 0.0;
+#pragma unroll
+      for (int t = 0; t < WM; ++t) ek = (t == kl) ? w[t] : ek;
+      out[j + kl] = ek;
+    }
+#pragma unroll
+    for (int t = WM - 1; t >= 1; --t) w[t] = (t <= kl) ? w[t - 1] : 0.0;
+    w[0] = xin ? xin[j - 1] : 0.0;
+  }
+}
+
+// maps: T[b][col][r] = element r of the window after block b from unit
+// window e_col (no inputs); grid (P, ceil(ws / 32)), 32 threads
+template <int KIND, int WM>
+__global__ void __launch_bounds__(32) k_sw_maps(SweepCtx c, int ws, double* __restrict__ T) {
+  const int b = blockIdx.x, col = blockIdx.y * 32 + threadIdx.x;
+  if (col >= ws) return;
+  double w[WM];
+#pragma unroll
+  for (int e = 0; e < WM; ++e) w[e] = (e == col) ? 1.0 : 0.0;
+  const int s0 = b * c.L, s1 = min(c.n, s0 + c.L);
+  for (int s = s0; s < s1; ++s) sw_step<KIND, WM>(c, w, s, nullptr, nullptr);
+  double* o = T + ((size_t)b * ws + col) * ws;
+#pragma unroll
+  for (int e = 0; e < WM; ++e)
+    if (e < ws) o[e] = w[e];
+}
+
+// part: tv[b][r] = element r of the window after block b from a zero window
+// with the block's inputs; one thread per block
+template <int KIND, int WM>
+__global__ void __launch_bounds__(128) k_sw_part(SweepCtx c, int ws, const double* __restrict__ xin,
+                                                 double* __restrict__ tv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= c.P) return;
+  double w[WM];
+#pragma unroll
+  for (int e = 0; e < WM; ++e) w[e] = 0.0;
+  const int s0 = b * c.L, s1 = min(c.n, s0 + c.L);
+  for (int s = s0; s < s1; ++s) sw_step<KIND, WM>(c, w, s, xin, nullptr);
+#pragma unroll
+  for (int e = 0; e < WM; ++e)
+    if (e < ws) tv[(size_t)b * ws + e] = w[e];
+}
+
+// scan: one CTA; Ws[b] = the true window before block b.  T_b and t_b
+// stream through a three-stage cp.async ring.
+constexpr int kSwScanThreads = 128;
+__host__ __device__ constexpr size_t sw_scan_smem(int ws) { return sizeof(double) * 3 * ((size_t)ws * ws + ws) + 2 * sizeof(double) * 128; }
+template <int KIND>
+__global__ void __launch_bounds__(kSwScanThreads) k_sw_scan(SweepCtx c, int ws, const double* __restrict__ xin,
+                                                           const double* __restrict__ T,
+                                                           const double* __restrict__ tv, double* __restrict__ Ws) {
+  extern __shared__ __align__(16) double sm[];
+  const int stage = ws * ws + ws;
+  double* W = sm + 3 * (size_t)stage;  // current window (128 slots)
+  const int tid = threadIdx.x, n = c.n, kl = c.kl, kv = c.kl + c.ku;
+  auto issue = [&](int b) {
+    if (b < c.P) {
+      double* dst = sm + (size_t)(b % 3) * stage;
+      const double* srcT = T + (size_t)b * ws * ws;
+      for (int e = tid; e < ws * ws; e += kSwScanThreads) cp_async8(dst + e, srcT + e);
+      for (int e = tid; e < ws; e += kSwScanThreads) cp_async8(dst + ws * ws + e, tv + (size_t)b * ws + e);
+    }
+    cp_commit();
+  };
+  issue(0);
+  issue(1);
+  if (tid < ws) {
+    double v = 0.0;
+    if (KIND == SW_L) v = (tid <= kl && tid < n) ? xin[tid] : 0.0;
+    else if (KIND == SW_U) v = (tid <= kv && n - 1 - tid >= 0) ? xin[n - 1 - tid] : 0.0;
+    else if (KIND == SW_UT) v = (tid == 0) ? xin[0] : 0.0;
+    else v = (tid == 0) ? xin[n - 1] : 0.0;
+    W[tid] = v;
+  }
+  for (int b = 0; b < c.P; ++b) {
+    issue(b + 2);
+    cp_wait<2>();
+    __syncthreads();
+    const double* st = sm + (size_t)(b % 3) * stage;
+    double nw = 0.0;
+    if (tid < ws) {
+      Ws[(size_t)b * ws + tid] = W[tid];
+      nw = st[ws * ws + tid];
+      for (int col = 0; col < ws; ++col) nw = fma(st[col * ws + tid], W[col], nw);
+    }
+    __syncthreads();
+    if (tid < ws) W[tid] = nw;
+  }
+  cp_wait_all();
+}
+
+// out: block b reruns its steps from Ws[b] with its inputs and writes its
+// outputs; one thread per block
+template <int KIND, int WM>
+__global__ void __launch_bounds__(128) k_sw_out(SweepCtx c, int ws, const double* __restrict__ xin,
+                                                const double* __restrict__ Ws, double* __restrict__ xout) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= c.P) return;
+  double w[WM];
+#pragma unroll
+  for (int e = 0; e < WM; ++e) w[e] = (e < ws) ? Ws[(size_t)b * ws + e] : 0.0;
+  const int s0 = b * c.L, s1 = min(c.n, s0 + c.L);
+  for (int s = s0; s < s1; ++s) sw_step<KIND, WM>(c, w, s, xin, xout);
+}
+
+constexpr int kSwMaxWs = 72;     // widest window of the partitioned sweeps
+constexpr int64_t kSwMinN = 2048;  // shorter systems keep the one-warp sweeps
+
+struct SweepPlan {
+  SweepCtx c;
+  double* T[4];   // maps of the four sweeps
+  double* tv;     // P x ws_max
+  double* Ws;     // P x ws_max
+  double* tmp;    // n
+};
+
+int sw_blocks(int64_t n) {
+  int P = (int)sqrt(1.5 * (double)n);
+  return P < 1 ? 1 : (P > 4096 ? 4096 : P);
+}
+
+size_t sw_bytes(int64_t n, int kl, int ku) {
+  const int P0 = sw_blocks(n);
+  const int L = (int)((n + P0 - 1) / P0);
+  const int P = (int)((n + L - 1) / L);
+  size_t b = 0;
+  for (int k = 0; k < 4; ++k) {
+    const size_t ws = (size_t)sw_ws(k, kl, ku);
+    b += (sizeof(double) * (size_t)P * ws * ws + 255) & ~(size_t)255;
+  }
+  b += 2 * ((sizeof(double) * (size_t)P * (kl + ku + 1) + 255) & ~(size_t)255);
+  b += (sizeof(double) * (size_t)n + 255) & ~(size_t)255;
+  return b;
+}
+
+template <int KIND, int WM>
+int sw_run_wm(const SweepPlan& pl, int ws, const double* xin, double* xout, bool maps, cudaStream_t st) {
+  const SweepCtx& c = pl.c;
+  if (maps) {
+    k_sw_maps<KIND, WM><<<dim3((unsigned)c.P, (unsigned)((ws + 31) / 32)), 32, 0, st>>>(c, ws, pl.T[KIND]);
+    BCK(cudaGetLastError());
+    return ASOLVE_OK;
+  }
+  const unsigned g = (unsigned)((c.P + 127) / 128);
+  k_sw_part<KIND, WM><<<g, 128, 0, st>>>(c, ws, xin, pl.tv);
+  const size_t sm = sw_scan_smem(ws);
+  static bool attr = false;
+  if (!attr) {
+    BCK(cudaFuncSetAttribute(k_sw_scan<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sw_scan_smem(kSwMaxWs)));
+    attr = true;
+  }
+  k_sw_scan<KIND><<<1, kSwScanThreads, sm, st>>>(c, ws, xin, pl.T[KIND], pl.tv, pl.Ws);
+  k_sw_out<KIND, WM><<<g, 128, 0, st>>>(c, ws, xin, pl.Ws, xout);
+  BCK(cudaGetLastError());
+  return ASOLVE_OK;
+}
+
+// one sweep (maps: precompute T of this sweep instead)
+template <int KIND>
+int sw_run(const SweepPlan& pl, const double* xin, double* xout, bool maps, cudaStream_t st) {
+  const int ws = sw_ws(KIND, pl.c.kl, pl.c.ku);
+  if (ws <= 8) return sw_run_wm<KIND, 8>(pl, ws, xin, xout, maps, st);
+  if (ws <= 24) return sw_run_wm<KIND, 24>(pl, ws, xin, xout, maps, st);
+  return sw_run_wm<KIND, kSwMaxWs>(pl, ws, xin, xout, maps, st);
+}
+
+// x <- inv(A) x (trans: inv(A)^T x) in place, through pl.tmp
+int sw_apply(const SweepPlan& pl, double* x, bool trans, cudaStream_t st) {
+  int rc;
+  if (!trans) {
+    if ((rc = sw_run<SW_L>(pl, x, pl.tmp, false, st))) return rc;
+    return sw_run<SW_U>(pl, pl.tmp, x, false, st);
+  }
+  if ((rc = sw_run<SW_UT>(pl, x, pl.tmp, false, st))) return rc;
+  return sw_run<SW_LT>(pl, pl.tmp, x, false, st);
+}
+
 int window_r(int kv) {
   const int need = (kv + 1 + 31) / 32;
   if (need <= 1) return 1;
@@ -389,8 +687,10 @@ bool band_window_fits(int64_t kl, int64_t ku) {
 size_t band_ws_bytes(int64_t n, int64_t kl, int64_t ku, int64_t nrhs) {
   (void)nrhs;
   const size_t ldf = (size_t)(2 * kl + ku + 1);
+  size_t sw = 0;  // partitioned sweeps: sized for the widest window they take
+  if (n >= kSwMinN) sw = (kl + ku + 1 <= kSwMaxWs) ? sw_bytes(n, (int)kl, (int)ku) : sw_bytes(n, kSwMaxWs - 1, 0);
   return round256(sizeof(double) * ldf * (size_t)n) + round256(sizeof(int) * (size_t)n) +
-         2 * round256(sizeof(double) * (size_t)n) + kTailBytes;
+         2 * round256(sizeof(double) * (size_t)n) + sw + kTailBytes;
 }
 
 // Device memory needed before the true bandwidths are known (declared band).
@@ -477,6 +777,35 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
     return info->status = svd_ok ? ASOLVE_PENDING : ASOLVE_E_SINGULAR;
   }
   BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
+  // long systems with windows of up to kSwMaxWs: partitioned sweeps
+  const bool par = n >= kSwMinN && kv + 1 <= kSwMaxWs;
+  SweepPlan pl{};
+  if (par) {
+    char* q = reinterpret_cast<char*>(exi + ((n + 31) & ~(int64_t)31));
+    q = reinterpret_cast<char*>(((uintptr_t)q + 255) & ~(uintptr_t)255);
+    const int P0 = sw_blocks(n);
+    pl.c = SweepCtx{F, ldf, (int)n, kl, ku, piv, 0, 0};
+    pl.c.L = (int)((n + P0 - 1) / P0);
+    pl.c.P = (int)((n + pl.c.L - 1) / pl.c.L);
+    for (int k = 0; k < 4; ++k) {
+      pl.T[k] = reinterpret_cast<double*>(q);
+      const size_t ws = (size_t)sw_ws(k, kl, ku);
+      q += round256(sizeof(double) * (size_t)pl.c.P * ws * ws);
+    }
+    pl.tv = reinterpret_cast<double*>(q);
+    q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
+    pl.Ws = reinterpret_cast<double*>(q);
+    q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
+    pl.tmp = reinterpret_cast<double*>(q);
+    int rc;
+    if ((rc = sw_run<SW_L>(pl, nullptr, nullptr, true, st)) || (rc = sw_run<SW_U>(pl, nullptr, nullptr, true, st)))
+      return info->status = rc;
+    if (!no_rcond &&
+        ((rc = sw_run<SW_UT>(pl, nullptr, nullptr, true, st)) || (rc = sw_run<SW_LT>(pl, nullptr, nullptr, true, st))))
+      return info->status = rc;
+    for (int64_t c = 0; c < nrhs; ++c)
+      if ((rc = sw_apply(pl, a.X + (size_t)c * n, false, st))) return info->status = rc;
+  } else
   switch (R) {
     case 1: k_band_solve<1><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
     case 2: k_band_solve<2><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
@@ -486,7 +815,13 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   }
   BCK(cudaGetLastError());
   double rc = NAN;
-  if (!no_rcond) {
+  if (!no_rcond && par) {
+    double est = NAN;
+    auto apply = [&](double* v, bool tr) { return sw_apply(pl, v, tr, st); };
+    const int erc = est_host<double>((int)n, ev, exi, dscal, dint, apply, st, &est);
+    if (erc) return info->status = erc;
+    rc = rcond_from_est(norm1, est);
+  } else if (!no_rcond) {
     switch (R) {
       case 1: k_band_est<1, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
       case 2: k_band_est<2, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;

@@ -23,14 +23,15 @@ __device__ int warp_band_lu(WarpBand& b) {
   int ju = 0;
   for (int j = 0; j < b.n; ++j) {
     const int km = min(b.kl, b.n - 1 - j);
-    double best = -1.0;
-    int bi = 0x7fffffff;
-    for (int t = lane; t <= km; t += 32) {
-      double v = fabs(b.at(j + t, j));
-      if (v > best) { best = v; bi = t; }
+    // the first largest |a(j+t, j)|, t = 0..km, in passes of 32 candidates
+    int jp = -1;
+    unsigned long long kbest = 0ull;
+    for (int t0 = 0; t0 <= km; t0 += 32) {
+      const int t = t0 + lane;
+      unsigned long long kp;
+      const int l = warp_first_max_key(t <= km ? abs_key(b.at(j + t, j)) : 0ull, kp);
+      if (l >= 0 && kp > kbest) { kbest = kp; jp = t0 + l; }
     }
-    warp_argmax_first(best, bi);
-    const int jp = bi;
     if (jp < 0 || jp > km) return j + 1;  // only NaN candidates
     if (lane == 0) b.piv[j] = j + jp;
     const double pv = b.at(j + jp, j);

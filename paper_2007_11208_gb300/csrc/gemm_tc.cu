@@ -137,7 +137,7 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 // LOWER: C is square and only its lower triangle is needed; tiles strictly
 // above the diagonal are skipped.
 template <bool TRANS_B, bool LOWER>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 3)
     k_gemm_tc(float* __restrict__ C, int ldc, const float* __restrict__ A, int lda, const float* __restrict__ B,
               int ldb, int M, int N, int K, int passes, int* err) {
   if (LOWER && blockIdx.y > blockIdx.x) return;
@@ -168,27 +168,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool ok = true;
   uint32_t phase = 0;
   const int nchunks = (K + kTcK - 1) / kTcK;
-  for (int ch = 0; ch < nchunks && ok; ++ch) {
-    const int k0 = ch * kTcK;
-    // stage A: element (r, k) = A[(k0 + k) * lda + m0 + r]; lanes over r
-    for (int e = tid; e < kTcM * kTcK; e += kTcThreads) {
-      const int r = e & (kTcM - 1), k = e >> 7;
-      const float v = (m0 + r < M && k0 + k < K) ? __ldg(A + (size_t)(k0 + k) * lda + m0 + r) : 0.f;
-      float hi, lo;
-      tf32_split(v, hi, lo);
-      *reinterpret_cast<float*>(sAh + tc_off(r, k)) = (passes == 3) ? hi : v;
-      if (passes == 3) *reinterpret_cast<float*>(sAl + tc_off(r, k)) = lo;
+  // Each thread's 32 elements of A and of B for one K chunk are loaded into
+  // registers together (all loads in flight at once); the next chunk's
+  // loads are issued while the tensor core works on the current one.
+  //   A: thread t holds row t, k = 0..31 (coalesced over rows)
+  //   B: (n, k) with lanes over k (or over n when B is transposed)
+  constexpr int kPer = kTcM * kTcK / kTcThreads;  // 32
+  float va[kPer], vb[kPer];
+  auto load_chunk = [&](int k0) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int r = tid, k = i;
+      va[i] = (m0 + r < M && k0 + k < K) ? __ldg(A + (size_t)(k0 + k) * lda + m0 + r) : 0.f;
     }
-    // stage B: element (n, k) = B[(n0 + n) * ldb + k0 + k] (lanes over k),
-    // or B[(k0 + k) * ldb + n0 + n] when transposed (lanes over n)
-    for (int e = tid; e < kTcN * kTcK; e += kTcThreads) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + i * kTcThreads;
       const int k = TRANS_B ? (e >> 7) : (e & (kTcK - 1)), n = TRANS_B ? (e & (kTcN - 1)) : (e >> 5);
       float v = 0.f;
       if (n0 + n < N && k0 + k < K)
         v = TRANS_B ? __ldg(B + (size_t)(k0 + k) * ldb + n0 + n) : __ldg(B + (size_t)(n0 + n) * ldb + k0 + k);
+      vb[i] = v;
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
+  for (int ch = 0; ch < nchunks && ok; ++ch) {
+    // stage the registers: A element (r, k), B element (n, k)
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
       float hi, lo;
-      tf32_split(v, hi, lo);
-      *reinterpret_cast<float*>(sBh + tc_off(n, k)) = (passes == 3) ? hi : v;
+      tf32_split(va[i], hi, lo);
+      *reinterpret_cast<float*>(sAh + tc_off(tid, i)) = (passes == 3) ? hi : va[i];
+      if (passes == 3) *reinterpret_cast<float*>(sAl + tc_off(tid, i)) = lo;
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = tid + i * kTcThreads;
+      const int k = TRANS_B ? (e >> 7) : (e & (kTcK - 1)), n = TRANS_B ? (e & (kTcN - 1)) : (e >> 5);
+      float hi, lo;
+      tf32_split(vb[i], hi, lo);
+      *reinterpret_cast<float*>(sBh + tc_off(n, k)) = (passes == 3) ? hi : vb[i];
       if (passes == 3) *reinterpret_cast<float*>(sBl + tc_off(n, k)) = lo;
     }
     // generic-proxy writes -> visible to the tensor core's async proxy
@@ -211,6 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_commit(mbar_a);
     }
+    if (ch + 1 < nchunks) load_chunk((ch + 1) * kTcK);  // in flight during the MMAs
     // the stage may be rewritten only after the MMAs have read it; the
     // verdict is made uniform across the block before anyone acts on it
     const bool waited = mbar_wait(mbar_a, phase);

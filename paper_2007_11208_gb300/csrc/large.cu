@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "cta_linalg.cuh"
+#include "est_host.cuh"
 
 namespace asv {
 
@@ -851,61 +852,6 @@ __global__ void k_build_perm(const int* piv, int n, int* perm) {
   }
 }
 
-// estimator helpers (one CTA of 1024 threads each)
-template <typename V>
-__global__ void k_vec_sumabs(const V* x, int n, double* out) {
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs((double)x[i]);
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-    *out = t;
-  }
-}
-template <typename V>
-__global__ void k_vec_argmax(const V* x, int n, int* out, double* vals, int jprev) {
-  __shared__ double rv[32];
-  __shared__ int ri[32];
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = fabs((double)x[i]);
-    if (a > best) { best = a; bi = i; }
-  }
-  warp_argmax_first(best, bi);
-  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = rv[0];
-    int ii = ri[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-      if (rv[k] > b || (rv[k] == b && ri[k] < ii)) { b = rv[k]; ii = ri[k]; }
-    *out = ii;
-    vals[0] = (ii >= 0 && ii < n) ? fabs((double)x[ii]) : 0.0;
-    vals[1] = (jprev >= 0 && jprev < n) ? (double)x[jprev] : 0.0;
-  }
-}
-// mode 0: x = 1/n; 1: x = e_j; 2: alternating test vector;
-// 3: xi = sign(x), x = xi, flag[0] |= (sign changed)
-template <typename V>
-__global__ void k_vec_set(V* x, V* xi, int n, int mode, int j, int* flag) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    if (mode == 0) x[i] = V(1) / V(n);
-    else if (mode == 1) x[i] = (i == j) ? V(1) : V(0);
-    else if (mode == 2) x[i] = ((i & 1) ? V(-1) : V(1)) * (V(1) + V(i) / V(n - 1));
-    else {
-      const V sg = x[i] >= V(0) ? V(1) : V(-1);
-      if (sg != xi[i]) atomicOr(flag, 1);
-      xi[i] = sg;
-      x[i] = sg;
-    }
-  }
-}
-
 
 // ===================================================================== host
 size_t scan_large_workspace(int64_t n);
@@ -1173,71 +1119,6 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
   return ASOLVE_OK;
 }
 
-// 1-norm estimate of inv(A) (Hager 1984, Higham 1988), the iteration driven
-// from the host; apply(v, trans) overwrites the device vector v.
-template <typename V, typename Apply>
-int est_large(int n, V* v, V* xi, double* dscal, int* dint, Apply apply, cudaStream_t st, double* out) {
-  auto sumabs = [&](double* r) -> int {
-    k_vec_sumabs<V><<<1, 1024, 0, st>>>(v, n, dscal);
-    LCK(cudaMemcpyAsync(r, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
-    LCK(cudaStreamSynchronize(st));
-    return ASOLVE_OK;
-  };
-  const int g = (n + 255) / 256;
-  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 0, 0, dint);
-  int rc = apply(v, false);
-  if (rc) return rc;
-  double est;
-  if (n == 1) {
-    V h;
-    LCK(cudaMemcpyAsync(&h, v, sizeof(V), cudaMemcpyDeviceToHost, st));
-    LCK(cudaStreamSynchronize(st));
-    *out = fabs((double)h);
-    return ASOLVE_OK;
-  }
-  if ((rc = sumabs(&est))) return rc;
-  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 3, 0, dint);
-  if ((rc = apply(v, true))) return rc;
-  int k = 2;
-  int jprev = -1;
-  for (;;) {
-    int j;
-    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, jprev);
-    LCK(cudaMemcpyAsync(&j, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LCK(cudaStreamSynchronize(st));
-    if (j < 0 || j >= n) { est = NAN; break; }
-    k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 1, j, dint);
-    if ((rc = apply(v, false))) return rc;
-    const double estold = est;
-    if ((rc = sumabs(&est))) return rc;
-    LCK(cudaMemsetAsync(dint, 0, sizeof(int), st));
-    k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 3, 0, dint);
-    int changed = 0;
-    LCK(cudaMemcpyAsync(&changed, dint, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LCK(cudaStreamSynchronize(st));
-    if (!changed || est <= estold) break;
-    if ((rc = apply(v, true))) return rc;
-    double vals[2];
-    int jn;
-    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, j);
-    LCK(cudaMemcpyAsync(&jn, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LCK(cudaMemcpyAsync(vals, dscal + 1, sizeof(vals), cudaMemcpyDeviceToHost, st));
-    LCK(cudaStreamSynchronize(st));
-    ++k;
-    if (jn < 0 || jn >= n) { est = NAN; break; }
-    jprev = j;
-    if (vals[1] == vals[0] || k > 5) break;
-  }
-  k_vec_set<V><<<g, 256, 0, st>>>(v, xi, n, 2, 0, dint);
-  if ((rc = apply(v, false))) return rc;
-  double s2;
-  if ((rc = sumabs(&s2))) return rc;
-  const double temp = 2.0 * s2 / (double)(3 * n);
-  if (temp > est) est = temp;
-  *out = est;
-  return ASOLVE_OK;
-}
-
 double rcond_of(double anorm, double est) {
   if (anorm == 0.0 || std::isinf(est) || est == 0.0) return 0.0;
   return (1.0 / est) / anorm;
@@ -1379,7 +1260,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if (!no_rcond) {
       double est;
       auto apply = [&](double* v, bool tr) { return tri_solve_large<double>(a.A, n, n, lower, tr, false, v, 1, false, wb, st); };
-      rc = est_large<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est);
+      rc = est_host<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est);
       if (rc) return rc;
       rc_val = rcond_of(sr.norm1, est);
     }
@@ -1591,7 +1472,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       if (!no_rcond) {
         double est;
         auto apply = [&](float* v, bool tr) { return apply_large<float, float>(f, lu, n, v, 1, tr, (float*)tmp, st); };
-        rc = est_large<float>(n, (float*)ev, (float*)exi, dscal, dint, apply, st, &est);
+        rc = est_host<float>(n, (float*)ev, (float*)exi, dscal, dint, apply, st, &est);
         if (rc) return rc;
         rcv = rcond_of(sr.norm1, est);
         gate_ok = rcv >= 1.0 / klim;
@@ -1650,7 +1531,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (!no_rcond) {
     double est;
     auto apply = [&](double* v, bool tr) { return apply_large<double, double>(f, lu, n, v, 1, tr, (double*)tmp, st); };
-    if ((rc = est_large<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est))) return rc;
+    if ((rc = est_host<double>(n, (double*)ev, (double*)exi, dscal, dint, apply, st, &est))) return rc;
     rcv = rcond_of(sr.norm1, est);
   }
   info->rcond = rcv;
