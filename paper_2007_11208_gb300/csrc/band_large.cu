@@ -122,6 +122,8 @@ __global__ void k_band_to_dense(const double* __restrict__ AB, int64_t ldab, int
 }
 
 // ------------------------------------------------------------ factor
+constexpr int kFlatNP = 8;  // update pairs per lane of the narrow-band factorisation
+
 // GBTRF on F with the active window in shared memory: S = kv+1+kD column
 // slots of ldf doubles; column c lives in slot c % S while it is active.
 __global__ void __launch_bounds__(32) k_band_lu_win(double* __restrict__ F, int ldf, int n, int kl, int ku,
@@ -135,6 +137,17 @@ __global__ void __launch_bounds__(32) k_band_lu_win(double* __restrict__ F, int 
     if (c < n)
       for (int r = lane; r < ldf; r += 32) cp_async8(slot(c) + r, F + (size_t)c * ldf + r);
     cp_commit();
+  }
+  // narrow bands: the kl x kv update pairs spread over the lanes, at most
+  // kFlatNP per lane (pair e: row 1 + e % kl, column e / kl after j)
+  const bool flat = kl >= 1 && kl * kv <= 32 * kFlatNP;
+  int ft[kFlatNP], fc[kFlatNP];
+#pragma unroll
+  for (int i = 0; i < kFlatNP; ++i) {
+    const int e = lane + 32 * i;
+    const bool on = flat && e < kl * kv;
+    ft[i] = on ? 1 + e % kl : 0;
+    fc[i] = on ? e / kl : 0;
   }
   int ju = 0;
   for (int j = 0; j < n; ++j) {
@@ -172,18 +185,32 @@ __global__ void __launch_bounds__(32) k_band_lu_win(double* __restrict__ F, int 
     const double inv = 1.0 / cj[kv];
     for (int t = 1 + lane; t <= km; t += 32) cj[kv + t] *= inv;
     __syncwarp();
-    // rank-1 update of rows j+1..j+km, columns j+1..ju; lane <-> row
-    for (int t0 = 1; t0 <= km; t0 += 32) {
-      const int t = t0 + lane;
-      const bool on = t <= km;
-      const double l = on ? cj[kv + t] : 0.0;
-      int sc = (j + 1) % S;
+    // rank-1 update of rows j+1..j+km, columns j+1..ju
+    if (flat) {  // lane <-> fixed (row, column) pairs of the window
+      const int sj = j % S;
+#pragma unroll
+      for (int i = 0; i < kFlatNP; ++i) {
+        const int t = ft[i], cc = fc[i];
+        int sl = sj + 1 + cc;
+        if (sl >= S) sl -= S;
+        if (t > 0 && t <= km && j + 1 + cc <= ju) {
+          double* col = win + (size_t)sl * ldf + kv - 1 - cc;  // col[0]: row j of column j+1+cc
+          col[t] = fma(-cj[kv + t], col[0], col[t]);
+        }
+      }
+    } else {  // lane <-> row
+      for (int t0 = 1; t0 <= km; t0 += 32) {
+        const int t = t0 + lane;
+        const bool on = t <= km;
+        const double l = on ? cj[kv + t] : 0.0;
+        int sc = (j + 1) % S;
 #pragma unroll 4
-      for (int c = j + 1; c <= ju; ++c) {
-        double* cc = win + (size_t)sc * ldf;
-        const double u = cc[kv + j - c];
-        if (on) cc[kv + j + t - c] = fma(-l, u, cc[kv + j + t - c]);
-        sc = (sc + 1 == S) ? 0 : sc + 1;
+        for (int c = j + 1; c <= ju; ++c) {
+          double* cc = win + (size_t)sc * ldf;
+          const double u = cc[kv + j - c];
+          if (on) cc[kv + j + t - c] = fma(-l, u, cc[kv + j + t - c]);
+          sc = (sc + 1 == S) ? 0 : sc + 1;
+        }
       }
     }
     __syncwarp();

@@ -545,7 +545,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
 constexpr int kBandR = 2;
 constexpr int kBandRingBytes = band_ring_doubles(kBandR) * 8 + 64;  // ring + pivot ring, per warp
 
-
 // Warp-scope estimator (same iteration as cta_est_inv_norm1).
 __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi, double* ring, int* pring) {
   const int lane = threadIdx.x & 31;
