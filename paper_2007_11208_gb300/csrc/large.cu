@@ -801,6 +801,82 @@ __global__ void __launch_bounds__(kThreads) k_residual_large(const double* __res
   }
 }
 
+// FP64 residual for up to 8 right-hand sides, split over k so that every
+// SM has many independent loads of A in flight: blockIdx.y takes the k
+// segment [seg * klen, (seg + 1) * klen) and writes its partial products
+// P[seg][c][r]; k_residual_sum adds the segments in order (the result does
+// not depend on scheduling) and forms R = B - sum and max |R|.
+//   nrhs <= 2: one thread per row on DFMA (A read once, eight loads ahead);
+//   nrhs <= 8: one warp per 8-row group on mma.sync f64.
+constexpr int kResMaxSeg = 32;
+__global__ void __launch_bounds__(256) k_residual_part_fma(const double* __restrict__ A, int n,
+                                                           const double* __restrict__ X, int nrhs, int klen,
+                                                           double* __restrict__ P) {
+  const int r = blockIdx.x * 256 + threadIdx.x, seg = blockIdx.y;
+  const int k0 = seg * klen, k1 = min(n, k0 + klen);
+  if (r >= n) return;
+  double s0 = 0.0, s1 = 0.0;
+  int k = k0;
+  for (; k + 8 <= k1; k += 8) {
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = __ldg(A + (size_t)(k + q) * n + r);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      s0 = fma(a[q], __ldg(X + k + q), s0);
+      if (nrhs > 1) s1 = fma(a[q], __ldg(X + (size_t)n + k + q), s1);
+    }
+  }
+  for (; k < k1; ++k) {
+    const double a = __ldg(A + (size_t)k * n + r);
+    s0 = fma(a, __ldg(X + k), s0);
+    if (nrhs > 1) s1 = fma(a, __ldg(X + (size_t)n + k), s1);
+  }
+  P[((size_t)seg * nrhs) * n + r] = s0;
+  if (nrhs > 1) P[((size_t)seg * nrhs + 1) * n + r] = s1;
+}
+
+__global__ void __launch_bounds__(64) k_residual_part_mma(const double* __restrict__ A, int n,
+                                                          const double* __restrict__ X, int nrhs, int klen,
+                                                          double* __restrict__ P) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3, seg = blockIdx.y;
+  const int r0 = (blockIdx.x * 2 + w) * 8;
+  if (r0 >= n) return;
+  const int k0 = seg * klen, k1 = min(n, k0 + klen);  // klen is a multiple of 4
+  const int ra = r0 + g;
+  const bool xok = g < nrhs;
+  double c0 = 0.0, c1 = 0.0;
+#pragma unroll 8
+  for (int k = k0; k < k1; k += 4) {
+    const int ka = k + t;
+    const double a = (ra < n && ka < k1) ? __ldg(A + (size_t)ka * n + ra) : 0.0;
+    const double b = (xok && ka < k1) ? __ldg(X + (size_t)g * n + ka) : 0.0;
+    dmma_8x8x4(c0, c1, a, b);
+  }
+  const int r = r0 + g;
+  if (r < n) {
+    if (2 * t < nrhs) P[((size_t)seg * nrhs + 2 * t) * n + r] = c0;
+    if (2 * t + 1 < nrhs) P[((size_t)seg * nrhs + 2 * t + 1) * n + r] = c1;
+  }
+}
+
+__global__ void k_residual_sum(const double* __restrict__ P, int nseg, int n, int nrhs,
+                               const double* __restrict__ B, double* __restrict__ R,
+                               unsigned long long* rmax) {
+  const int c = blockIdx.y;
+  double m = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int seg = 0; seg < nseg; ++seg) s += P[((size_t)seg * nrhs + c) * n + r];
+    const double v = B[(size_t)c * n + r] - s;
+    R[(size_t)c * n + r] = v;
+    m = fmax(m, fabs(v));
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(rmax + c, (unsigned long long)__double_as_longlong(m));
+}
+
 // ------------------------------------------------------ vector helpers
 template <typename V>
 __global__ void k_colmax_abs(const V* __restrict__ x, int n, int nrhs, unsigned long long* out) {
@@ -877,6 +953,30 @@ struct Arena {
     cudaError_t _e = (x);                           \
     if (_e != cudaSuccess) return ASOLVE_E_CUDA;    \
   } while (0)
+
+// R = B - A X in FP64 with rmax[c] |= max |R(:, c)| (rmax zeroed by the
+// caller); P: kResMaxSeg x 8 x n doubles of scratch.
+int residual_large(const double* A, int n, const double* B, const double* X, int nrhs, double* R,
+                   unsigned long long* rmax, double* P, int num_sms, cudaStream_t st) {
+  if (nrhs > 8) {
+    k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(A, n, B, X, nrhs, R, rmax);
+    LCK(cudaGetLastError());
+    return ASOLVE_OK;
+  }
+  const bool fma_path = nrhs <= 2;
+  const int gx = fma_path ? (n + 255) / 256 : (n + 15) / 16;
+  int nseg = (4 * num_sms + gx - 1) / gx;  // about four CTAs of loads per SM
+  nseg = nseg < 1 ? 1 : (nseg > kResMaxSeg ? kResMaxSeg : nseg);
+  int klen = (n + nseg - 1) / nseg;
+  klen = (klen + 7) & ~7;
+  nseg = (n + klen - 1) / klen;
+  if (fma_path) k_residual_part_fma<<<dim3(gx, nseg), 256, 0, st>>>(A, n, X, nrhs, klen, P);
+  else k_residual_part_mma<<<dim3(gx, nseg), 64, 0, st>>>(A, n, X, nrhs, klen, P);
+  k_residual_sum<<<dim3((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, nrhs), 256, 0, st>>>(P, nseg, n, nrhs,
+                                                                                              B, R, rmax);
+  LCK(cudaGetLastError());
+  return ASOLVE_OK;
+}
 
 // Scratch of the wavefront triangular solve: one flag per work item.
 struct WaveBuf {
@@ -1134,6 +1234,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += 2 * sizeof(float) * (size_t)((n + kInvBW - 1) / kInvBW) * kInvBW * kInvBW + 512;  // diagonal-block inverses
   b += sizeof(double) * kLB * kLB + 256;               // Dtmp
   b += 4 * sizeof(double) * (size_t)n * nrhs + 1024;   // R, Xs, tmp, (spare)
+  b += sizeof(double) * kResMaxSeg * 8 * (size_t)n + 256;  // residual partials
   b += 4 * sizeof(double) * (size_t)n + 512;           // estimator vectors
   b += 2 * sizeof(double) * 1024 * (kLB + 4) + 2 * sizeof(double) * kLB + 1024;  // panel buffers (G <= 1024)
   b += scan_large_workspace(n) + 4096;
@@ -1228,12 +1329,13 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (arc) return info->status = arc;
   const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
   double* R = static_cast<double*>(ar.take(sizeof(double) * (size_t)n * nrhs));
+  double* Pres = static_cast<double*>(ar.take(sizeof(double) * kResMaxSeg * 8 * (size_t)n));  // residual partials
   void* xs = ar.take(sizeof(double) * (size_t)n * nrhs);
   void* tmp = ar.take(sizeof(double) * (size_t)n * nrhs);
   void* ev = ar.take(sizeof(double) * (size_t)n);
   void* exi = ar.take(sizeof(double) * (size_t)n);
   unsigned long long* colmax = static_cast<unsigned long long*>(ar.take(sizeof(unsigned long long) * 3 * nrhs));
-  if (!R || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
+  if (!R || !Pres || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
   // ---- triangular route (Sec. 2.2): FP64 substitution on A itself
   if (cls == ASOLVE_CLS_LOWER || cls == ASOLVE_CLS_UPPER) {
     const bool lower = cls == ASOLVE_CLS_LOWER;
@@ -1267,7 +1369,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     info->rcond = rc_val;
     if (a.flags & ASOLVE_BERR) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      {
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        if (rr_) return rr_;
+      }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
       std::vector<unsigned long long> hm((size_t)3 * nrhs);
@@ -1333,7 +1438,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     int ok = 0;
     for (int it = 0;; ++it) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
-      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      {
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        if (rr_) return rr_;
+      }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
       LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
       LCK(cudaStreamSynchronize(st));
@@ -1417,7 +1525,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if ((rc = apply_large<double, double>(f, kept->lu != 0, n, a.X, nrhs, false, (double*)tmp, st))) return rc;
     if (a.flags & ASOLVE_BERR) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
-      k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+      {
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        if (rr_) return rr_;
+      }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
       LCK(cudaMemcpyAsync(hb.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
       LCK(cudaStreamSynchronize(st));
@@ -1537,7 +1648,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   info->rcond = rcv;
   if (a.flags & ASOLVE_BERR) {
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-    k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(a.A, n, a.B, a.X, nrhs, R, colmax);
+    {
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        if (rr_) return rr_;
+      }
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
     std::vector<unsigned long long> hm((size_t)3 * nrhs);

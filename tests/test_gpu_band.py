@@ -89,7 +89,10 @@ def check_against_oracle(orc, AB, kld, kud, B, rc, info, X, berr=False):
 
 CASES = [(1, 0, 0, 1), (2, 1, 0, 1), (5, 1, 1, 2), (33, 2, 3, 3), (100, 8, 8, 1), (257, 0, 7, 2),
          (300, 5, 0, 1), (1000, 32, 32, 4), (1025, 31, 1, 1), (2000, 40, 20, 3), (5000, 2, 2, 16),
-         (4097, 60, 50, 2)]
+         (4097, 60, 50, 2),
+         # n >= 2048 with windows of at most 72: the partitioned sweeps (one-sided
+         # bands, the widest window, a block count that leaves a ragged last block)
+         (2048, 0, 9, 3), (3001, 7, 0, 2), (2100, 35, 35, 1), (20011, 3, 4, 5)]
 
 
 @pytest.mark.parametrize("n,kl,ku,nrhs", CASES)
