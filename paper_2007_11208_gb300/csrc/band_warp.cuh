@@ -126,7 +126,7 @@ __device__ void warp_band_apply(const WarpBand& b, double* x, bool trans) {
 // steps run by one warp: the window of the vector being eliminated sits in
 // registers across the lanes (element e in register e >> 5 of lane e & 31),
 // and the factor columns stream through a cp.async ring kD steps ahead.
-constexpr int kD = 4;           // cp.async prefetch distance (column steps)
+constexpr int kD = 16;          // cp.async prefetch distance (column steps)
 constexpr int kMaxR = 8;        // register-window width: kl+ku+1 <= 32 * kMaxR
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {

@@ -934,6 +934,8 @@ cudaError_t set_class_attrs() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_tri_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_band_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarps * kBandRingBytes);
+  if (e != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
 }
