@@ -16,9 +16,13 @@
 //                  stream through a cp.async ring;
 //   k_band_est     the estimate, driven on the device by one warp with the
 //                  same sweeps.
-// Bandwidths beyond those windows fall back to the warp routines that work
-// on global memory directly (band_warp.cuh).  Scan, packing and the FP64
-// backward error are ordinary data-parallel kernels.
+// From n = 2048 on (windows of up to 72 elements) the solve and the estimate
+// instead run the partitioned sweeps (k_sw_*): each sweep is a linear
+// recurrence, evaluated block-parallel through per-block transfer maps and
+// one chained scan, with the estimate's iteration driven from the host
+// (est_host.cuh).  Bandwidths beyond the windows fall back to the warp
+// routines that work on global memory directly (band_warp.cuh).  Scan,
+// packing and the FP64 backward error are ordinary data-parallel kernels.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>

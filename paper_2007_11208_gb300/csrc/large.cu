@@ -10,12 +10,16 @@
 //                        (one grid barrier per column), its row swaps are
 //                        applied to the other columns, U12 = inv(L11) A12,
 //                        and the trailing update A22 -= L21 U12;
-//   triangular (Sec. 2.2, Eq. 3) blocked forward/back substitution.
-// The working matrix is FP32 in the mixed-precision mode (trailing updates
-// on the tcgen05 tensor cores, 3xTF32 split) and FP64 in the plain mode
-// (trailing updates on the FP64 mma.sync instruction).  Refinement (FP64
-// residual on mma.sync f64), the 1-norm condition estimate and the
-// per-column backward error are driven from the host.
+//   triangular (Sec. 2.2, Eq. 3) blocked forward/back substitution: one
+//                        cooperative wavefront launch per solve.
+// The working matrix is FP32 in the mixed-precision modes (trailing updates
+// on the tcgen05 tensor cores: 3xTF32 split, or single BF16 / FP16
+// products; the FP32 panel elects pivots with one atomic per CTA; solves
+// multiply by the inverses of the 128 x 128 diagonal blocks) and FP64 in
+// the plain mode (trailing updates on the FP64 mma.sync instruction; solves
+// by substitution).  Refinement (FP64 residual split over k), the 1-norm
+// condition estimate (est_host.cuh) and the per-column backward error are
+// driven from the host.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
