@@ -1053,7 +1053,6 @@ struct Fac {  // a factorisation of the large path and its scratch
   T* Dtmp;       // 128 x 128 inverse of the current diagonal block
   int* fail;     // device
   PanelBuf pb;
-  size_t panel_smem;
   WaveBuf wb;
   int gemm_mode = 3;  // FP32 factors: operand mode of the trailing updates (launch_gemm_tc)
   const T* dinvL = nullptr;  // FP32 factors: inverses of the 128 x 128 diagonal blocks (k_diag_inv)
@@ -1498,7 +1497,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     info->detail = kept->detail | 8;
     if (kept->precision != ASOLVE_PREC_FP64) {  // FP32-stored factors
       if ((rc = set_large_attrs<float>())) return rc;
-      Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
+      Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, wb};
       f.dinvL = dinvL;  // kept with the factor (they follow it in the workspace)
       f.dinvU = kept->lu ? dinvU : nullptr;
       int iters = 0;
@@ -1514,7 +1513,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       kept->valid = 0;  // the kept factor does not refine this right-hand side: start over
       return large_solve(a, ws, ws_bytes, info);
     }
-    Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0, wb};
+    Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, wb};
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
     std::vector<unsigned long long> hb((size_t)3 * nrhs);
@@ -1557,7 +1556,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   // FP16 tensor products), FP64 refinement
   if (a.precision != ASOLVE_PREC_FP64 && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
-    Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, 0, wb};
+    Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, wb};
     f.gemm_mode = a.precision == ASOLVE_PREC_BF16 ? kGemmBf16 : (a.precision == ASOLVE_PREC_FP16 ? kGemmFp16 : 3);
     // the refinement converges while kappa times the factors' relative
     // error stays below one: the 16-bit updates lower the kappa limit
@@ -1616,7 +1615,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   }
   // ---- FP64 path
   if ((rc = set_large_attrs<double>())) return rc;
-  Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, 0, wb};
+  Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, wb};
   info->precision = ASOLVE_PREC_FP64;
   info->detail = detail;
   bool lu = !chol;

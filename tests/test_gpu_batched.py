@@ -88,6 +88,42 @@ def test_host_buffers_same_bytes(ctx):
     assert [i["route"] for i in ih] == [i["route"] for i in idev]
 
 
+def test_host_buffers_shuffled_layout(ctx):
+    """A host-buffer batch of 2,600 systems stored in shuffled order (offsets
+    not increasing with the system index) gives the same bytes as the
+    device-buffer call."""
+    from paper_2007_11208_gb300 import asolve
+    rng = np.random.default_rng(12)
+    count = 2600
+    mats, rhss = [], []
+    for s in range(count):
+        n = int(rng.integers(4, 24))
+        mats.append(rng.standard_normal((n, n)) + 2 * np.sqrt(n) * np.eye(n))
+        rhss.append(rng.standard_normal((n, 1 + s % 3)))
+    order = rng.permutation(count)  # storage order of the blocks
+    pk = pack_batch([mats[i] for i in order], [rhss[i] for i in order])
+    pos = np.empty(count, dtype=np.int64)
+    pos[order] = np.arange(count)  # system s is stored as block pos[s]
+    n = np.array([mats[s].shape[0] for s in range(count)], dtype=np.int64)
+    r = np.array([rhss[s].shape[1] for s in range(count)], dtype=np.int64)
+    ao = np.array([pk["a_off_h"][pos[s]] for s in range(count)], dtype=np.int64)
+    bo = np.array([pk["b_off_h"][pos[s]] for s in range(count)], dtype=np.int64)
+    A = pk["A"].cpu().numpy()
+    B = pk["B"].cpu().numpy()
+    Xh = np.zeros_like(B)
+    ih = np.zeros(count * asolve.INFO_BYTES, dtype=np.uint8)
+    rc = ctx.solve_batched(count, n.ctypes.data, r.ctypes.data, ao.ctypes.data, bo.ctypes.data, A.ctypes.data,
+                           B.ctypes.data, Xh.ctypes.data, ih.ctypes.data, asolve.HOST_BUFFERS)
+    assert rc == 0
+    dn, dr, dao, dbo = (torch.from_numpy(a).cuda() for a in (n, r, ao, bo))
+    Xd = torch.zeros_like(pk["B"])
+    idv = torch.zeros(count * asolve.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    rc = ctx.solve_batched(count, dn, dr, dao, dbo, pk["A"], pk["B"], Xd, idv, asolve.SYNC)
+    assert rc == 0
+    assert np.array_equal(Xh, Xd.cpu().numpy())
+    assert np.array_equal(ih, idv.cpu().numpy())
+
+
 def test_invalid_entries(ctx):
     mats = [np.eye(4), np.eye(3)]
     pk = pack_batch(mats, [np.ones(4), np.ones(3)])
