@@ -63,6 +63,9 @@ PEAK_FP32 = 152 * 128 * 2 * 2.07e9
 PEAK_DFMA = 1.0e12
 PEAK_DMMA = 4.1e12
 COUNT = 10000  # systems per GPU per step (--count overrides, for small profiling runs)
+# dram__bytes_read.sum + dram__bytes_write.sum of k_lu_class on the
+# 1,000-system batch (3.393513 GB + 1.088180 GB)
+LU_CLASS_DRAM_BYTES_1000 = 3.393513e9 + 1.088180e9
 TUNING = os.path.join(ROOT, "paper_2007_11208_gb300", "tuning.json")  # autotuner output, if present
 SEED = 1
 
@@ -361,8 +364,16 @@ def ours(args):
             fl = fm[key32]
             ach = fl / (per[dom] / 1e3) / 1e12
             t_min = fm["t_min_ms"].get(dom, 0.0)
+            traffic = None
+            if dom == "k_lu_class" and COUNT > 0:
+                # DRAM bytes (read + write) of one k_lu_class launch from an ncu
+                # capture of a 1,000-system batch of the same generator
+                # (profiles/batched-1000_k_lu_class_k_chol_class_full.md),
+                # scaled by the number of systems
+                traffic = LU_CLASS_DRAM_BYTES_1000 * COUNT / 1000.0
             result["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                                  "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                                  "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
+                                  "traffic_unit": "bytes per launch",
                                   "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
                                   "note": "FP32 factor flops only; the FP64 refinement of the same "
                                           "kernel is not counted",
