@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_chol_diag(T* W, int ldw, int k0, i
 // two shuffles), so the 128 steps of forward substitution need no block
 // barrier.
 constexpr int kTrsmXP = kLB + 4;  // vector stride: 4 consecutive k of 8 vectors hit distinct banks
+constexpr int kTrsmBlockedRhs = 32;  // triangular route: blocked TRSM from this many right-hand sides
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_trsm_sub(T* __restrict__ W, int ldw, int k0, int kb, int lo, int hi,
@@ -148,6 +149,56 @@ __global__ void __launch_bounds__(kThreads) k_trsm_sub(T* __restrict__ W, int ld
 template <typename T>
 constexpr size_t trsm_smem() {
   return sizeof(T) * ((size_t)kLB * (kLB + 1) + 64 * kTrsmXP + kLB);
+}
+
+// Diagonal-block step of the blocked TRSM with many right-hand sides:
+// X(k0.., c) <- inv(T11) X(k0.., c) for the kb x kb block T11 of the
+// triangle M (lower: rows and columns k0..k0+kb-1 on and below the
+// diagonal, forward substitution; upper: on and above, backward), one CTA
+// per 64 right-hand sides, four threads per right-hand side.
+__global__ void __launch_bounds__(kThreads) k_trsm_rhs(const double* __restrict__ M, int ldm, int k0, int kb,
+                                                      double* __restrict__ X, int ldx, int nrhs, int upper) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double(*Ms)[kLB + 1] = reinterpret_cast<double(*)[kLB + 1]>(smem);  // Ms[i][k] = T11(i, k)
+  double* Xs = reinterpret_cast<double*>(smem + sizeof(double) * kLB * (kLB + 1));
+  double* rinv = Xs + 64 * kTrsmXP;
+  const int base = blockIdx.x * 64;
+  if (base >= nrhs) return;
+  const int cnt = min(64, nrhs - base);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kLB * kLB; e += kThreads) {
+    const int i = e & (kLB - 1), k = e >> 7;
+    const bool in = i < kb && k < kb && (upper ? k >= i : k <= i);
+    Ms[i][k] = in ? M[(size_t)(k0 + k) * ldm + k0 + i] : 0.0;
+  }
+  for (int e = tid; e < kLB * 64; e += kThreads) {
+    const int k = e & (kLB - 1), q = e >> 7;
+    Xs[q * kTrsmXP + k] = (k < kb && q < cnt) ? X[(size_t)(base + q) * ldx + k0 + k] : 0.0;
+  }
+  __syncthreads();
+  for (int i = tid; i < kLB; i += kThreads) rinv[i] = (i >= kb) ? 1.0 : 1.0 / Ms[i][i];
+  __syncthreads();
+  const int q = tid >> 2, t = tid & 3;
+  double* xq = Xs + q * kTrsmXP;
+  for (int ii = 0; ii < kb; ++ii) {
+    const int i = upper ? kb - 1 - ii : ii;
+    double part = 0.0;
+    if (upper)
+      for (int k = i + 1 + t; k < kb; k += 4) part += Ms[i][k] * xq[k];
+    else
+      for (int k = t; k < i; k += 4) part += Ms[i][k] * xq[k];
+    part += __shfl_xor_sync(0xffffffffu, part, 1);
+    part += __shfl_xor_sync(0xffffffffu, part, 2);
+    const double xi = (xq[i] - part) * rinv[i];
+    __syncwarp();
+    if (t == 0) xq[i] = xi;
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < kLB * 64; e += kThreads) {
+    const int k = e & (kLB - 1), qq = e >> 7;
+    if (k < kb && qq < cnt) X[(size_t)(base + qq) * ldx + k0 + k] = Xs[qq * kTrsmXP + k];
+  }
 }
 
 // ------------------------------------------------- LU panel (cooperative)
@@ -756,55 +807,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__
   }
 }
 
-// ------------------------------------------------------ FP64 residual
-// R = B - A X (FP64), one warp per 8-row group (two warps per CTA, so the
-// row groups spread over every SM), all right-hand sides in chunks of 8 on
-// mma.sync f64 (A fragment loaded once per chunk set).
-// rmax[c] (as bits of a non-negative double) <- max |R(:, c)|.
-__global__ void __launch_bounds__(kThreads) k_residual_large(const double* __restrict__ A, int n,
-                                                            const double* __restrict__ B, const double* __restrict__ X,
-                                                            int nrhs, double* __restrict__ R,
-                                                            unsigned long long* rmax) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3;
-  const int nchunk = (nrhs + 7) / 8;
-  const int nw = blockDim.x >> 5;
-  for (int r0 = (blockIdx.x * nw + w) * 8; r0 < n; r0 += gridDim.x * nw * 8) {
-    for (int cc = 0; cc < nchunk; cc += 8) {  // up to 64 right-hand sides per pass
-      double acc[8][2];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = 0.0;
-      const int ra = r0 + g;
-      for (int k = 0; k < n; k += 4) {
-        const int ka = k + t;
-        const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * n + ra) : 0.0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int col = (cc + q) * 8 + g;
-          if ((cc + q) < nchunk) {
-            const double bv = (col < nrhs && ka < n) ? X[(size_t)col * n + ka] : 0.0;
-            dmma_8x8x4(acc[q][0], acc[q][1], a, bv);
-          }
-        }
-      }
-      const int r = r0 + g;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if ((cc + q) >= nchunk) continue;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int col = (cc + q) * 8 + 2 * t + h;
-          if (r < n && col < nrhs) {
-            const double v = B[(size_t)col * n + r] - acc[q][h];
-            R[(size_t)col * n + r] = v;
-            atomicMax(rmax + col, (unsigned long long)__double_as_longlong(fabs(v)));
-          }
-        }
-      }
-    }
-  }
-}
-
 // FP64 residual for up to 8 right-hand sides, split over k so that every
 // SM has many independent loads of A in flight: blockIdx.y takes the k
 // segment [seg * klen, (seg + 1) * klen) and writes its partial products
@@ -962,8 +964,11 @@ struct Arena {
 // caller); P: kResMaxSeg x 8 x n doubles of scratch.
 int residual_large(const double* A, int n, const double* B, const double* X, int nrhs, double* R,
                    unsigned long long* rmax, double* P, int num_sms, cudaStream_t st) {
-  if (nrhs > 8) {
-    k_residual_large<<<(n + 15) / 16, 64, 0, st>>>(A, n, B, X, nrhs, R, rmax);
+  if (nrhs > 8) {  // R = B, then R -= A X on the mma.sync f64 GEMM, then max |R|
+    LCK(cudaMemcpyAsync(R, B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
+    k_gemm_dmma<false, false><<<dim3((n + kDmM - 1) / kDmM, (nrhs + kDmN - 1) / kDmN), kThreads, kDmSmem, st>>>(
+        R, n, A, n, X, n, n, nrhs, n);
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(R, n, nrhs, rmax);
     LCK(cudaGetLastError());
     return ASOLVE_OK;
   }
@@ -1135,6 +1140,7 @@ int set_large_attrs() {
   static bool done = false;
   if (done) return ASOLVE_OK;
   LCK(cudaFuncSetAttribute(k_trsm_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
+  LCK(cudaFuncSetAttribute(k_trsm_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<double>()));
   LCK(cudaFuncSetAttribute(k_gemm_dmma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   LCK(cudaFuncSetAttribute(k_gemm_dmma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   LCK(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
@@ -1359,8 +1365,26 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         }
     }
     LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
-    int rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, wb, st);
-    if (rc) return rc;
+    int rc;
+    if (nrhs >= kTrsmBlockedRhs) {
+      // many right-hand sides: blocked TRSM, diagonal blocks by substitution,
+      // the rest of the right-hand sides updated on mma.sync f64
+      const unsigned gr = (unsigned)((nrhs + 63) / 64);
+      for (int q = 0; q < n; q += kLB) {
+        const int k0 = lower ? q : ((n - 1 - q) / kLB) * kLB;
+        const int kb = std::min(kLB, n - k0);
+        k_trsm_rhs<<<gr, kThreads, trsm_smem<double>(), st>>>(a.A, n, k0, kb, a.X, n, nrhs, lower ? 0 : 1);
+        if (lower && k0 + kb < n)
+          LCK(gemm_update<double>(a.X + k0 + kb, n, a.A + (size_t)k0 * n + k0 + kb, n, a.X + k0, n, n - k0 - kb, nrhs,
+                                  kb, false, false, nullptr, 0, st));
+        if (!lower && k0 > 0)
+          LCK(gemm_update<double>(a.X, n, a.A + (size_t)k0 * n, n, a.X + k0, n, k0, nrhs, kb, false, false, nullptr, 0,
+                                  st));
+      }
+      LCK(cudaGetLastError());
+    } else if ((rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, wb, st))) {
+      return rc;
+    }
     double rc_val = NAN;
     if (!no_rcond) {
       double est;
