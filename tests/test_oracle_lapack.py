@@ -19,7 +19,12 @@ tests check it against scipy's LAPACK binding:
 * L and U (dense and band storage, fill rows included) equal to rounding;
 * rcond identical to xGECON / xPOCON / xTRCON / xGBCON to rounding, on
   random and on row- and column-graded matrices (scales 1e-8 .. 1e8) where
-  rcond falls to 1e-33.
+  rcond falls to 1e-33;
+* the minimum-norm solution of the SVD fallback (Sec. 2.5, xGELSD) on
+  gapless geometric spectra down to 1e-12, full rank and rank deficient,
+  with the same cut-off (singular values <= n eps sigma_max dropped): the
+  same rank, and solutions within 2 n eps kappa_k of each other (kappa_k
+  the condition number of the kept part; observed <= 1.5 eps kappa_k).
 
 The estimator follows Higham's 1-norm method, as xLACN2 does; the two must
 take the same branch at every step for the estimates to agree to rounding,
@@ -176,3 +181,23 @@ def test_singular_pivot_step_matches_getrf(orc):
     lu, piv, linfo = lapack.dgetrf(A)
     assert linfo > 0 and info == linfo
     np.testing.assert_array_equal(ipiv[:linfo - 1], piv[:linfo - 1])
+
+
+@pytest.mark.parametrize("n", [6, 30, 80])
+@pytest.mark.parametrize("lo", [-4, -8, -12])
+@pytest.mark.parametrize("deficient", [0, 3])
+def test_svd_min_norm_matches_gelsd(orc, n, lo, deficient):
+    linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(500 + n + 10 * lo + deficient)
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    kept = np.logspace(0, lo, n - deficient)
+    sig = np.concatenate([kept, np.full(deficient, 1e-20)])
+    A = (U * sig) @ V.T
+    B = rng.standard_normal((n, 2))
+    eps = np.finfo(np.float64).eps
+    X, rank = orc.svd_solve(A, B)                 # default cut-off n eps
+    Xg, _, rank_g, _ = linalg.lstsq(A, B, cond=n * eps, lapack_driver="gelsd")
+    assert rank == rank_g == n - deficient
+    kappa_k = kept[0] / kept[-1]
+    assert np.abs(X - Xg).max() <= 2 * n * eps * kappa_k * np.abs(Xg).max()
