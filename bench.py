@@ -213,6 +213,35 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
 
 
+def large_case_roofline(kind, prec, n, nrhs, ms, peaks):
+    """Roofline of one single-system solve: the larger of two time floors,
+    the algorithmic flops at the peak of the arithmetic that bounds them and
+    one read of A (8 n^2 bytes) at the HBM peak; frac = floor / measured.
+
+    Flops: LU 2n^3/3, Cholesky n^3/3 (plus 2 n^2 nrhs for the two
+    triangular solves), triangular route n^2 nrhs.  Peaks: the FP64 path and
+    the triangular route at the mma.sync f64 rate measured on this GPU
+    (PEAK_DMMA); the mixed path's trailing updates at the 3xTF32 rate
+    (three TF32 products, TF32 = half the measured bf16 burst rate); the
+    BF16 / FP16 updates at the measured bf16 burst rate."""
+    flops = {"general": 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs,
+             "spd": 1.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs,
+             "lower": float(n) * n * nrhs}[kind]
+    bf16 = peaks["bf16_tflops"] * 1e12
+    if kind == "lower" or prec == "fp64":
+        peak, unit_src = PEAK_DMMA, "FP64 mma.sync (measured 4.1 TFLOP/s)"
+    elif prec == "mixed":
+        peak, unit_src = bf16 / 6.0, f"3xTF32 = bf16 {peaks['src']} / 6"
+    else:
+        peak, unit_src = bf16, f"bf16 {peaks['src']} (burst)"
+    t_alu = flops / peak
+    t_hbm = 8.0 * n * n / (peaks["hbm_gbs"] * 1e9)
+    floor = max(t_alu, t_hbm)
+    return {"bound": "alu" if t_alu >= t_hbm else "hbm", "flops": flops,
+            "achieved_tflops": flops / (ms * 1e-3) / 1e12, "peak_tflops": peak / 1e12,
+            "peak_src": unit_src, "floor_ms": floor * 1e3, "frac": floor / (ms * 1e-3)}
+
+
 def oracle_sample(pk, budget_s=15.0, max_threads=None):
     """Time the oracle as it stands on a bounded sample of the batch."""
     import oracle
@@ -488,6 +517,7 @@ def large_workload(args):
              (asolve.PREC_FP16, "fp16")]
     precs = [p for p in precs if p[1] in args.precs.split(",")]
     ctxs = {p: asolve.Context(precision=p) for p, _ in precs}
+    peaks = load_peaks()
     cases = []
     with ClockSampler(0) as clk:
         for n in sizes:
@@ -523,7 +553,8 @@ def large_workload(args):
                                          "berr": info["berr"], "rcond": info["rcond"],
                                          "detail": info["detail"],
                                          "flops_per_s": ({"general": 2.0 / 3.0 * n ** 3, "spd": 1.0 / 3.0 * n ** 3,
-                                                          "lower": float(n) * n * nrhs}[kind]) / (ms * 1e-3)}
+                                                          "lower": float(n) * n * nrhs}[kind]) / (ms * 1e-3),
+                                         "roofline": large_case_roofline(kind, name, n, nrhs, ms, peaks)}
                             log(n, kind, f"{kappa:.0e}", nrhs, name, f"{ms:.2f} ms", info["route"],
                                 info["precision"], info["ir_iters"], f"{info['berr']:.2e}")
                         if "fp64" in row and "mixed" in row:
@@ -548,6 +579,7 @@ def large_workload(args):
                                f"kappa={head['kappa']:.0e}, nrhs={head['nrhs']}, {hp}",
                    "l2": "inputs larger than L2"},
         "fp64_path_ms": head.get("fp64", {}).get("ms"), "speedup_vs_fp64_path": head.get("speedup"),
+        "roofline": head[hp].get("roofline"),
         "clocks": clk.summary(), "cases": cases}), flush=True)
 
 

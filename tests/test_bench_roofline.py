@@ -1,0 +1,44 @@
+"""Host arithmetic of the single-system roofline in bench.py (no GPU)."""
+import pytest
+
+import bench
+
+PEAKS = {"hbm_gbs": 6783.5, "bf16_tflops": 1917.9, "src": "measured"}
+
+
+def test_fp64_lu_is_alu_bound_at_the_dmma_rate():
+    n, ms = 8192, 444.6
+    r = bench.large_case_roofline("general", "fp64", n, 1, ms, PEAKS)
+    flops = 2.0 / 3.0 * n ** 3 + 2.0 * n * n
+    assert r["bound"] == "alu"
+    assert r["flops"] == pytest.approx(flops)
+    assert r["floor_ms"] == pytest.approx(flops / bench.PEAK_DMMA * 1e3)
+    assert r["frac"] == pytest.approx(r["floor_ms"] / ms)
+    assert r["achieved_tflops"] / r["peak_tflops"] == pytest.approx(r["frac"])
+
+
+def test_precision_selects_the_peak():
+    n, ms = 16384, 50.0  # large enough that every precision is ALU-bound
+    mixed = bench.large_case_roofline("spd", "mixed", n, 1, ms, PEAKS)
+    bf16 = bench.large_case_roofline("spd", "bf16", n, 1, ms, PEAKS)
+    fp16 = bench.large_case_roofline("spd", "fp16", n, 1, ms, PEAKS)
+    assert mixed["peak_tflops"] == pytest.approx(1917.9 / 6)   # three TF32 products
+    assert bf16["peak_tflops"] == fp16["peak_tflops"] == pytest.approx(1917.9)
+    assert mixed["bound"] == bf16["bound"] == "alu"
+    assert mixed["floor_ms"] == pytest.approx(6 * bf16["floor_ms"])
+
+
+def test_triangular_route_is_fp64_whatever_the_precision():
+    for prec in ("mixed", "fp64", "bf16"):
+        r = bench.large_case_roofline("lower", prec, 16384, 256, 285.8, PEAKS)
+        assert r["peak_tflops"] == pytest.approx(bench.PEAK_DMMA / 1e12)
+        assert r["flops"] == pytest.approx(16384.0 ** 2 * 256)
+
+
+def test_one_rhs_triangular_solve_is_hbm_bound():
+    # n^2 flops against one 8 n^2-byte read of A: far below the ridge point
+    n, ms = 16384, 27.7
+    r = bench.large_case_roofline("lower", "fp64", n, 1, ms, PEAKS)
+    assert r["bound"] == "hbm"
+    assert r["floor_ms"] == pytest.approx(8.0 * n * n / 6783.5e9 * 1e3)
+    assert 0 < r["frac"] < 1
