@@ -201,3 +201,31 @@ def test_svd_min_norm_matches_gelsd(orc, n, lo, deficient):
     assert rank == rank_g == n - deficient
     kappa_k = kept[0] / kept[-1]
     assert np.abs(X - Xg).max() <= 2 * n * eps * kappa_k * np.abs(Xg).max()
+
+
+@pytest.mark.parametrize("n,kl,ku", [(50, 2, 2), (300, 8, 3), (200, 1, 7), (64, 32, 32)])
+def test_column_dominant_band_takes_no_interchanges(orc, n, kl, ku):
+    """Gaussian elimination keeps diagonal dominance by columns in every
+    Schur complement, so partial pivoting finds the diagonal entry first at
+    every step: the oracle's band LU and xGBTRF both return the identity
+    pivot sequence, and the factors are those of elimination without
+    pivoting."""
+    rng = np.random.default_rng(600 + n + kl)
+    A = _random_band(rng, n, kl, ku)
+    np.fill_diagonal(A, 0.0)
+    d = 1.0 + np.abs(A).sum(axis=0)            # column sums: dominance by columns
+    A[np.diag_indices(n)] = d * np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    AB = orc.band_pack(A, kl, ku)
+    F, ipiv, info = orc.band_lu_factor(AB, kl, ku)
+    lub, piv, linfo = lapack.dgbtrf(AB, kl, ku)
+    assert info == linfo == 0
+    np.testing.assert_array_equal(ipiv, np.arange(n))
+    np.testing.assert_array_equal(piv, np.arange(n))
+    # factors of unpivoted elimination, from the dense oracle LU with the
+    # same (identity) pivots
+    Fd, ipd, _ = orc.lu_factor(A)
+    np.testing.assert_array_equal(ipd, np.arange(n))
+    kv = kl + ku
+    for j in range(n):
+        for i in range(max(0, j - ku), min(n, j + kl + 1)):
+            assert F[kv + i - j, j] == pytest.approx(Fd[i, j], rel=1e-12, abs=1e-14)
