@@ -1,4 +1,6 @@
-"""Host arithmetic of the single-system roofline in bench.py (no GPU)."""
+"""Host logic of bench.py (no GPU): the single-system roofline and how the
+oracle legs count a verified solve."""
+import numpy as np
 import pytest
 
 import bench
@@ -42,3 +44,13 @@ def test_one_rhs_triangular_solve_is_hbm_bound():
     assert r["bound"] == "hbm"
     assert r["floor_ms"] == pytest.approx(8.0 * n * n / 6783.5e9 * 1e3)
     assert 0 < r["frac"] < 1
+
+
+def test_oracle_verified_counts_like_the_metric(orc):
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((40, 40)) + 10 * np.eye(40)
+    assert bench.oracle_solve_verified(orc, A, rng.standard_normal((40, 3)))
+    # a zero column: LU fails, the SVD route answers (status W_APPROX): not counted
+    S = A.copy()
+    S[:, 5] = 0.0
+    assert not bench.oracle_solve_verified(orc, S, rng.standard_normal((40, 1)))
