@@ -54,3 +54,10 @@ def test_oracle_verified_counts_like_the_metric(orc):
     S = A.copy()
     S[:, 5] = 0.0
     assert not bench.oracle_solve_verified(orc, S, rng.standard_normal((40, 1)))
+
+
+def test_cpu_baseline_leg_runs_on_a_small_batch(orc):
+    pk = bench.make_batch("cpu", bench.SEED, count=48)
+    r = bench.oracle_sample(pk, budget_s=0.2, max_threads=2)
+    assert r["kind"] == "oracle" and r["cores"] == 2 and r["unit"] == bench.UNIT
+    assert r["value"] > 0 and "systems of the same batch" in r["sample"]
