@@ -28,6 +28,11 @@ More workloads print their own JSON line (not the headline):
                      triangular, SPD, tridiagonal, U diag(logspace(0,-14)) V^T
                      with Haar U, V), one right-hand side: latency of one
                      asolve_solve call per system over --reps repetitions.
+  --workload replica the paper's Tables 1-4 on the GPU: 1000 random systems
+                     per kind (5-diagonal band, lower triangular, sympd,
+                     dense) and n in {100, 250, 500, 1000}, adaptive solver
+                     vs the standard LU solver (ASOLVE_FORCE_LU), time per
+                     system and reduction in %.
   --workload serve   request server: Poisson arrivals of FP64 requests in
                      host memory, n log-uniform in [32, 8192], the batched
                      class mix, kappa log-uniform in [1e1, 1e12], HBM budget
@@ -717,6 +722,90 @@ def plain_workload(args):
         "clocks": clk.summary(), "systems": rows}), flush=True)
 
 
+# --------------------------------------------------------------- paper replica
+# reduction (%) of the adaptive solver against the standard LU solver in the
+# paper's Tables 1-3 (banded, triangular, sympd) and the detection overhead
+# (%) of Table 4 (dense), n = 100, 250, 500, 1000; Intel Core i5-5200U
+PAPER_TABLES = {"band5": [67.89, 83.45, 89.02, 91.18], "lower": [72.78, 73.59, 79.61, 84.09],
+                "sympd": [17.35, 25.62, 24.02, 27.54], "dense": [-1.627, -0.243, -0.114, -0.187]}
+
+
+def replica_workload(args):
+    """The paper's evaluation (Sec. 3, Tables 1-4) on the GPU.  For each
+    matrix kind and n, one batch of --replica-count random systems (one
+    right-hand side each) is solved by the adaptive solver and by the
+    standard solver (ASOLVE_FORCE_LU: LU whatever the structure; the scan
+    still runs, for the non-finite check); time per system = batched call
+    time / count, CUDA events on the context stream, median of --steps."""
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sizes = [int(x) for x in args.replica_sizes.split(",")]
+    count = args.replica_count
+    prec = {"fp64": asolve.PREC_FP64, "mixed": asolve.PREC_MIXED}[args.replica_prec]
+    ctx = asolve.Context(precision=prec)
+    st = torch.cuda.ExternalStream(ctx.stream)
+    tables, launches = {}, 0
+    with ClockSampler(0) as clk:
+        for kind in synth.REPLICA_KINDS:
+            rows = []
+            for n in sizes:
+                pk = synth.replica_batch(kind, n, count, SEED + n, dev)
+                nd, rd = pk["n"].to(dev), pk["nrhs"].to(dev)
+                ao, bo = pk["a_off"].to(dev), pk["b_off"].to(dev)
+                X = torch.zeros_like(pk["B"])
+                infos = torch.zeros(count * asolve.INFO_BYTES, dtype=torch.uint8, device=dev)
+                row = {"n": n}
+                for name, flags in (("standard", asolve.FORCE_LU), ("adaptive", 0)):
+                    for _ in range(max(args.warmup, 1)):
+                        rc = ctx.solve_batched(count, nd, rd, ao, bo, pk["A"], pk["B"], X, infos, flags)
+                        assert rc == 0, rc
+                    times = []
+                    for _ in range(args.steps):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        torch.cuda.synchronize()
+                        e0.record(st)
+                        rc = ctx.solve_batched(count, nd, rd, ao, bo, pk["A"], pk["B"], X, infos, flags)
+                        e1.record(st)
+                        torch.cuda.synchronize()
+                        assert rc == 0, rc
+                        times.append(e0.elapsed_time(e1))
+                        launches += 7
+                    inf = asolve.infos_from_tensor(infos)
+                    hist = {}
+                    for i in inf:
+                        hist[i["route"]] = hist.get(i["route"], 0) + 1
+                    row[name] = {"s_per_system": statistics.median(times) * 1e-3 / count,
+                                 "status_ok": sum(1 for i in inf if i["status"] == 0),
+                                 "routes": {str(r): c for r, c in sorted(hist.items())}}
+                a, b = row["adaptive"]["s_per_system"], row["standard"]["s_per_system"]
+                row["reduction_pct"] = 100.0 * (1.0 - a / b)
+                paper = dict(zip((100, 250, 500, 1000), PAPER_TABLES[kind])).get(n)
+                if paper is not None:
+                    row["paper_reduction_pct"] = paper
+                log(kind, n, f"standard {b * 1e6:.1f} us", f"adaptive {a * 1e6:.1f} us",
+                    f"reduction {row['reduction_pct']:.1f}%")
+                rows.append(row)
+                del pk, X, infos
+                torch.cuda.empty_cache()
+            tables[kind] = rows
+    ctx.close()
+    # headline of this workload: the mean reduction over the structured kinds
+    red = [r["reduction_pct"] for kd in ("band5", "lower", "sympd") for r in tables[kd]]
+    print(json.dumps({
+        "metric": "reduction of time per system, adaptive vs standard LU (paper Tables 1-3)",
+        "value": statistics.mean(red), "unit": "%", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(args.warmup, 1), "ms_per_step": None, "higher_is_better": True,
+        "scaling": "replicas only", "vs_baseline": None,
+        "dtype": "f64" if args.replica_prec == "fp64" else "f64 (mixed)", "data": "synthetic",
+        "config": {"workload": f"paper-replica: {count} systems per kind and n, n in {sizes}, "
+                               "band5/lower/sympd/dense (Sec. 3, Fig. 3 recipes), 1 rhs",
+                   "l2": "inputs larger than L2 from n = 250 (count = 1000)"},
+        "gpu_launches": launches, "clocks": clk.summary(), "tables": tables}), flush=True)
+
+
 # --------------------------------------------------------------- serving
 def _serve_templates(count, seed, dev, nmin=32, nmax=8192):
     """Request templates: n log-uniform, batched class mix, kappa log-uniform."""
@@ -848,7 +937,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--count", type=int, default=COUNT,
                     help="systems per GPU (smaller values are for profiling runs only)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "large", "serve", "plain", "band"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "large", "serve", "plain", "band", "replica"])
+    ap.add_argument("--replica-sizes", default="100,250,500,1000")
+    ap.add_argument("--replica-count", type=int, default=1000)
+    ap.add_argument("--replica-prec", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--band-n", type=int, default=1_000_000, help="band: order")
     ap.add_argument("--band-k", default="2,8,32", help="band: kl = ku values")
     ap.add_argument("--band-nrhs", default="1,16", help="band: right-hand-side counts")
@@ -873,6 +966,8 @@ def main():
         return plain_workload(args)
     if args.workload == "band":
         return band_workload(args)
+    if args.workload == "replica":
+        return replica_workload(args)
     if args.impl == "reference":
         reference(args)
     else:

@@ -26,6 +26,13 @@ distributions below are the ones the benchmark configurations name):
                signs (exact spectrum at O(n^2) cost, for large n)
   tri_kappa    T = D (I + s N), N strictly triangular N(0,1), s = 1/n,
                D = diag(logspace(0, -log10 kappa))
+  replica_*    the paper's evaluation (Sec. 3, Fig. 3): entries U[-0.5, 0.5]
+               (Fig. 3's randu - 0.5); sympd R^T R + I (Fig. 3), mirrored;
+               dense as drawn; lower triangle and 5-diagonal band with
+               diagonal 1 + row sum of |off-diagonal| (the paper does not
+               give these two recipes; dominance keeps them on their routes,
+               since random triangles are exponentially ill-conditioned);
+               right-hand side U[0, 1] (Fig. 3's fill::randu)
 """
 from __future__ import annotations
 
@@ -296,3 +303,39 @@ def packed_batch(specs, seed, device="cpu"):
             "nrhs": torch.tensor([s[2] for s in specs], dtype=torch.int64),
             "a_off": torch.tensor(a_off, dtype=torch.int64),
             "b_off": torch.tensor(b_off, dtype=torch.int64)}
+
+
+REPLICA_KINDS = ("band5", "lower", "sympd", "dense")
+
+
+def replica_batch(kind, n, count, seed, device="cpu"):
+    """`count` systems of order n for one row of the paper's Tables 1-4,
+    packed like packed_batch (one right-hand side each)."""
+    g = gen(seed, device)
+    R = torch.rand((count, n, n), generator=g, device=device, dtype=F64) - 0.5
+    i = torch.arange(n, device=device)
+    if kind == "sympd":
+        A = R.transpose(1, 2) @ R
+        A.diagonal(dim1=1, dim2=2).add_(1.0)
+        A = torch.tril(A) + torch.tril(A, -1).transpose(1, 2)
+    elif kind == "dense":
+        A = R
+    elif kind in ("lower", "band5"):
+        d = i[None, :] - i[:, None]  # column - row
+        keep = (d < 0) if kind == "lower" else ((d != 0) & (d.abs() <= 2))
+        A = torch.where(keep, R, torch.zeros((), dtype=F64, device=device))
+        A.diagonal(dim1=1, dim2=2).copy_(1.0 + A.abs().sum(dim=2))
+    else:
+        raise ValueError(kind)
+    del R
+    sa, sb = align(n * n), align(n)
+    Af = torch.zeros((count, sa), dtype=F64, device=device)
+    Af[:, :n * n] = A.transpose(1, 2).reshape(count, n * n)  # column-major per system
+    del A
+    Bf = torch.zeros((count, sb), dtype=F64, device=device)
+    Bf[:, :n] = torch.rand((count, n), generator=g, device=device, dtype=F64)
+    idx = torch.arange(count, dtype=torch.int64)
+    return {"A": Af.reshape(-1), "B": Bf.reshape(-1),
+            "n": torch.full((count,), n, dtype=torch.int64),
+            "nrhs": torch.ones(count, dtype=torch.int64),
+            "a_off": idx * sa, "b_off": idx * sb}

@@ -61,3 +61,26 @@ def test_cpu_baseline_leg_runs_on_a_small_batch(orc):
     r = bench.oracle_sample(pk, budget_s=0.2, max_threads=2)
     assert r["kind"] == "oracle" and r["cores"] == 2 and r["unit"] == bench.UNIT
     assert r["value"] > 0 and "systems of the same batch" in r["sample"]
+
+
+@pytest.mark.parametrize("kind,cls,route", [("band5", 1, 1), ("lower", 2, 2), ("sympd", 4, 4),
+                                            ("dense", 5, 6)])
+def test_replica_batches_take_their_tables_routes(orc, kind, cls, route):
+    """Each kind of the paper's Tables 1-4 reaches the solver its table is
+    about (banded, triangular, Cholesky, LU) with an answer of status OK;
+    offsets are 32-element aligned as the batched API wants."""
+    from paper_2007_11208_gb300 import synth
+    n, count = 100, 3
+    pk = synth.replica_batch(kind, n, count, 11)
+    assert all(int(o) % 32 == 0 for o in pk["a_off"]) and all(int(o) % 32 == 0 for o in pk["b_off"])
+    for s in range(count):
+        o, q = int(pk["a_off"][s]), int(pk["b_off"][s])
+        A = pk["A"][o:o + n * n].numpy().reshape(n, n).T
+        b = pk["B"][q:q + n].numpy()
+        assert 0.0 <= b.min() and b.max() <= 1.0
+        X, info = orc.solve(A, b)
+        assert (info["cls"], info["route"], info["status"]) == (cls, route, 0)
+        if kind == "band5":
+            assert info["kl"] == info["ku"] == 2
+        if kind == "sympd":
+            assert np.array_equal(A, A.T)
