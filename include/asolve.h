@@ -192,8 +192,9 @@ int asolve_solve(asolve_ctx* ctx, const double* A, const double* B, int64_t n,
  * AB is ldab x n column-major with A(i,j) at AB[(ku+i-j) + j*ldab],
  * ldab >= kl+ku+1, for the declared bandwidths kl, ku.  The system always
  * takes the banded route, with the true bandwidths found inside the band.
- * The SVD fallback is available for n <= 4096 only (the dense copy); above
- * that a failure returns E_SINGULAR and a low rcond W_ILLCOND.  Synchronous. */
+ * The SVD fallback is available for n <= 1024 only (it runs on a dense
+ * copy); above that a failure returns E_SINGULAR and a low rcond
+ * W_ILLCOND.  Synchronous. */
 int asolve_solve_band(asolve_ctx* ctx, const double* AB, int64_t ldab, int64_t kl,
                       int64_t ku, const double* B, int64_t n, int64_t nrhs,
                       uint32_t flags, double* X, asolve_info* info);
