@@ -1,0 +1,96 @@
+"""Parity at the benchmark's full sizes, in the launch configuration that
+bench.py times.
+
+* The 10,000-system headline batch (bench.py's generator, seed, precision,
+  panel-width table and flags), launched as one batched call: every system
+  is verified by the library's in-kernel FP64 backward error, and one
+  system in 97 is compared with the oracle one by one (class, kl/ku, route
+  and status bit-exact; X within 2^-52 n kappa_inf of the oracle's X; the
+  oracle's compensated residual for the backward error).
+* Single dense systems of the large configuration (general n = 16384 and
+  SPD n = 8192, kappa 1e4, one right-hand side, mixed precision, the
+  bench's seeds): beyond the oracle's O(n^3) solve in a test, so they are
+  checked through properties that hold at any size -- the oracle's
+  compensated residual bounds the backward error, and a known solution the
+  forward error (kappa_inf <= n kappa_2 by construction).
+
+The file is collected last (after test_zz_no_alloc.py): the largest runs,
+and a failure here leaves every other test already run.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import fwd_err, kappa_inf
+
+pytestmark = pytest.mark.gpu
+BERR = 1e-13
+EPS = np.finfo(np.float64).eps
+
+
+def test_headline_batch_sampled_against_oracle(orc):
+    import bench
+    from paper_2007_11208_gb300 import asolve, build
+    build.build()
+    dev = torch.device("cuda", 0)
+    count = bench.COUNT
+    pk = bench.make_batch(dev, bench.rank_seed(0), count)
+    tuning = bench.TUNING if os.path.exists(bench.TUNING) else None
+    ctx = asolve.Context(precision=asolve.PREC_MIXED, tuning=tuning)
+    X = torch.zeros_like(pk["B"])
+    infos = torch.zeros(count * asolve.INFO_BYTES, dtype=torch.uint8, device=dev)
+    rc = ctx.solve_batched(count, pk["n"], pk["nrhs"], pk["a_off"], pk["b_off"], pk["A"], pk["B"], X, infos,
+                           asolve.BERR | asolve.SYNC)
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    inf = asolve.infos_from_tensor(infos)
+    assert len(inf) == count
+    bad = [s for s, i in enumerate(inf) if not (i["status"] == 0 and i["berr"] <= BERR)]
+    assert not bad, [(s, inf[s]) for s in bad[:5]]
+    specs = pk["specs"]
+    routes = set()
+    for s in range(0, count, 97):
+        n, r = specs[s][1], specs[s][2]
+        o, q = int(pk["a_off_h"][s]), int(pk["b_off_h"][s])
+        A = pk["A"][o:o + n * n].cpu().numpy().reshape(n, n).T
+        B = pk["B"][q:q + n * r].cpu().numpy().reshape(r, n).T
+        Xg = X[q:q + n * r].cpu().numpy().reshape(r, n).T
+        Xo, io = orc.solve(A, B)
+        i = inf[s]
+        assert (i["cls"], i["kl"], i["ku"], i["route"], i["status"]) == \
+            (io["cls"], io["kl"], io["ku"], io["route"], io["status"]), (s, i, io)
+        routes.add(i["route"])
+        assert fwd_err(Xg, Xo) <= 2.0 ** -52 * n * kappa_inf(A), (s, i, fwd_err(Xg, Xo))
+        _, berr = orc.residual_dot2(A, Xg, B)
+        assert berr.max() <= BERR, (s, i, berr)
+    assert {1, 2, 4, 6} <= routes, routes
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind,n", [("general", 16384), ("spd", 8192)])
+def test_large_configuration_full_size(orc, kind, n):
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    kappa = 1e4
+    g = synth.gen(int(n + 17 * kappa) % 100003, dev)  # bench.py's seed for this case
+    M = synth.spectrum_fast(n, g, kappa, spd=(kind == "spd"), device=dev)  # M[j, i] = A[i, j]
+    xt = synth.rhs(n, 1, g, dev)                                          # known solution, (1, n)
+    B = (M.t() @ xt.t()).t().contiguous()                                 # A x_true
+    X = torch.zeros_like(B)
+    ctx = asolve.Context(precision=asolve.PREC_MIXED)
+    rc, info = ctx.solve(M, B, n, 1, X, asolve.BERR)
+    torch.cuda.synchronize()
+    assert rc == 0, (rc, info)
+    assert info["route"] == (asolve.ROUTE_CHOL if kind == "spd" else asolve.ROUTE_LU), info
+    assert info["berr"] <= BERR, info
+    A = M.cpu().numpy().T
+    x = X.cpu().numpy().reshape(n, 1)
+    b = B.cpu().numpy().reshape(n, 1)
+    x_true = xt.cpu().numpy().reshape(n, 1)
+    _, berr = orc.residual_dot2(A, x, b)
+    assert berr.max() <= BERR, berr
+    assert np.abs(x - x_true).max() / np.abs(x_true).max() <= EPS * n * (n * kappa)
+    ctx.close()
