@@ -667,6 +667,35 @@ def band_workload(args):
 
 
 # --------------------------------------------------------------- plain
+def launch_floor_us(reps=200):
+    """Median host wall time of replaying a CUDA graph of one tiny kernel
+    and synchronising: the floor under one asolve_solve call, which is one
+    graph launch and one stream synchronisation.  None if the capture
+    fails (the workload's own numbers stand without it)."""
+    try:
+        s = torch.cuda.Stream()
+        x = torch.zeros(1, device="cuda")
+        with torch.cuda.stream(s):
+            x.add_(1.0)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            x.add_(1.0)
+        for _ in range(20):
+            g.replay()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            g.replay()
+            torch.cuda.synchronize()
+            t.append((time.perf_counter() - t0) * 1e6)
+        return float(np.percentile(t, 50))
+    except Exception as e:  # noqa: BLE001 -- a missing floor must not stop the workload
+        log("launch floor not measured:", repr(e))
+        return None
+
+
 def plain_workload(args):
     from paper_2007_11208_gb300 import asolve, build, synth
     build.build()
@@ -711,12 +740,14 @@ def plain_workload(args):
                          "e2e_p50_us": float(np.percentile(e2e, 50))})
             log(rows[-1])
     ctx.close()
+    floor = launch_floor_us()
     med = float(np.median([r["p50_us"] for r in rows]))
     print(json.dumps({
         "metric": "latency of one adaptive solve (n=200, 1 rhs), median over the five systems",
         "value": med, "unit": "us", "n_gpus": 1, "steps": args.reps, "warmup": 20, "ms_per_step": med / 1e3,
         "higher_is_better": False, "scaling": "replicas only", "vs_baseline": None, "dtype": "f64 (mixed)",
         "data": "synthetic", "config": {"workload": "plain-200: general/lower/spd/tridiag/ill, seed 0"},
+        "launch_floor_us": floor,
         "e2e": {"value": float(np.median([r["e2e_p50_us"] for r in rows])), "unit": "us",
                 "h2d_bytes_per_step": 8 * (n * n + n), "d2h_bytes_per_step": 8 * n + 64},
         "clocks": clk.summary(), "systems": rows}), flush=True)

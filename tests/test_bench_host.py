@@ -84,3 +84,9 @@ def test_replica_batches_take_their_tables_routes(orc, kind, cls, route):
             assert info["kl"] == info["ku"] == 2
         if kind == "sympd":
             assert np.array_equal(A, A.T)
+
+
+def test_launch_floor_never_raises():
+    # without a GPU the capture fails and the plain workload reports None
+    r = bench.launch_floor_us(reps=5)
+    assert r is None or r > 0
