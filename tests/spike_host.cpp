@@ -1,0 +1,67 @@
+// Host driver of the partitioned band solve's per-thread routines
+// (band_spike.cuh), for the CPU tests: every thread index of every kernel
+// launch is run in turn, in launch order, with the same arguments the GPU
+// launches pass.
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "band_spike.cuh"
+
+using namespace asv::spk;
+
+namespace {
+
+void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::vector<int>& piv, double* x) {
+  const int64_t q = q_of(c);
+  std::vector<double> G((size_t)c.n), Y((size_t)(c.P * (q > 0 ? q : 1)));
+  for (int64_t b = 0; b < c.P; ++b) solve_step1(c, tr, b, x, G.data());
+  if (q > 0)
+    for (int64_t b = 0; b + 1 < c.P; ++b) solve_step2(c, tr, b, G.data(), M.data(), piv.data(), Y.data());
+  for (int64_t b = 0; b < c.P; ++b) solve_step3(c, tr, b, Y.data(), x);
+}
+
+}  // namespace
+
+// AB: A in band storage, A(i,j) at AB[ku + i - j + j*ldab].  Solves A x = b
+// into x and A^T xt = b into xt (b: n values).  far[0], far[1]: the largest
+// far-tip entry for A and for A^T; dom[0], dom[1]: dominance by rows / by
+// columns.  Returns 0, -1 - b if block b has a zero pivot, -1000 - b if
+// boundary system b is singular.
+extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, int64_t n, int64_t m,
+                                const double* bvec, double* x, double* xt, double* far, int* dom) {
+  const int64_t ldf = 2 * (int64_t)kl + ku + 1, kv = (int64_t)kl + ku;
+  std::vector<double> F((size_t)(ldf * n), 0.0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = j - ku; i <= j + kl; ++i)
+      if (i >= 0 && i < n) F[(size_t)(kv + i - j + j * ldf)] = AB[(size_t)(ku + i - j + j * ldab)];
+  Ctx c{F.data(), ldf, n, kl, ku, m, n / m};
+  dom[0] = dom[1] = 1;
+  for (int64_t i = 0; i < n; ++i) {
+    int r, cc;
+    dominance(c, i, &r, &cc);
+    dom[0] &= r;
+    dom[1] &= cc;
+  }
+  for (int64_t b = 0; b < c.P; ++b)
+    if (factor_block(c, b)) return (int)(-1 - b);
+  const int64_t q = q_of(c);
+  std::vector<double> scr((size_t)(n * (q > 0 ? q : 1)));
+  std::vector<double> M[2];
+  std::vector<int> piv[2];
+  for (int tr = 0; tr < 2; ++tr) {
+    M[tr].assign((size_t)(c.P * q * q + 1), 0.0);
+    piv[tr].assign((size_t)(c.P * q + 1), 0);
+    unsigned long long fb = 0;
+    for (int64_t t = 0; t < c.P * q; ++t) spike_column(c, tr != 0, t, scr.data(), M[tr].data(), &fb);
+    memcpy(&far[tr], &fb, sizeof(double));
+    for (int64_t b = 0; b + 1 < c.P; ++b)
+      if (q > 0 && factor_boundary(c, b, M[tr].data(), piv[tr].data())) return (int)(-1000 - b);
+  }
+  memcpy(x, bvec, sizeof(double) * (size_t)n);
+  memcpy(xt, bvec, sizeof(double) * (size_t)n);
+  solve_sys(c, false, M[0], piv[0], x);
+  solve_sys(c, true, M[1], piv[1], xt);
+  return 0;
+}
