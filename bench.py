@@ -607,6 +607,8 @@ def band_workload(args):
     sum, nrhs right-hand sides; time of one asolve_solve_band call (scan of
     the band, GBTRF-equivalent factorisation, solve, rcond estimate,
     backward error) with CUDA events."""
+    if args.band_spike:  # read by the library at its first band solve
+        os.environ["ASOLVE_BAND_SPIKE"] = "1"
     from paper_2007_11208_gb300 import asolve, build, synth
     build.build()
     torch.cuda.set_device(0)
@@ -641,6 +643,7 @@ def band_workload(args):
                 ms = statistics.median(times)
                 io_bytes = 8.0 * n * (2 * k + 1) + 16.0 * n * nrhs  # band of A, B, X: each once
                 row = {"n": n, "kl": k, "ku": k, "nrhs": nrhs, "ms": ms, "rc": rc, "route": info["route"],
+                       "partitioned": bool(info["detail"] & 16),
                        "kl_found": info["kl"], "ku_found": info["ku"], "berr": info["berr"],
                        "rcond": info["rcond"], "io_bytes": io_bytes,
                        "io_gbs": io_bytes / (ms * 1e-3) / 1e9}
@@ -659,7 +662,8 @@ def band_workload(args):
         "steps": args.steps, "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True,
         "scaling": "replicas only", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"band: n={n}, kl=ku in {ks}, nrhs in {nrhs_list}, diagonally dominant, "
-                               "band storage", "l2": "inputs larger than L2"},
+                               "band storage" + (", partitioned route enabled" if args.band_spike else ""),
+                   "l2": "inputs larger than L2"},
         "roofline_note": "the band factorisation is a sequential chain along n; io_gbs is the band of A, "
                          "B and X read or written once over the whole call, against the measured HBM copy "
                          "bandwidth",
@@ -970,6 +974,8 @@ def main():
                     help="systems per GPU (smaller values are for profiling runs only)")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "large", "serve", "plain", "band", "replica"])
+    ap.add_argument("--band-spike", action="store_true",
+                    help="band: enable the partitioned route for dominant bands (ASOLVE_BAND_SPIKE=1)")
     ap.add_argument("--replica-sizes", default="100,250,500,1000")
     ap.add_argument("--replica-count", type=int, default=1000)
     ap.add_argument("--replica-prec", default="fp64", choices=["fp64", "mixed"])

@@ -125,7 +125,9 @@ typedef struct {           /* 64 bytes, one per system */
   int32_t precision;       /* ASOLVE_PREC_* the final answer came from */
   int32_t detail;          /* bit 0: FP32 factor rejected by the rcond gate,
                               bit 1: refinement stalled, bit 2: FP32 Cholesky failed,
-                              bit 3: factorisation reused from an earlier resident request */
+                              bit 3: factorisation reused from an earlier resident request,
+                              bit 4: band system solved by the partitioned route for
+                              diagonally dominant bands (environment ASOLVE_BAND_SPIKE=1) */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */

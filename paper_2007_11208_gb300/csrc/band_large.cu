@@ -23,10 +23,21 @@
 // (est_host.cuh).  Bandwidths beyond the windows fall back to the warp
 // routines that work on global memory directly (band_warp.cuh).  Scan,
 // packing and the FP64 backward error are ordinary data-parallel kernels.
+//
+// With ASOLVE_BAND_SPIKE=1 in the environment, long systems (n >= 4096)
+// that are diagonally dominant by rows or by columns take a partitioned
+// route instead (band_spike.cuh, k_spk_*): blocks factored in parallel
+// without pivoting, one small system per block boundary, and solves with A
+// and A^T in three block-parallel steps; a zero pivot, a singular boundary
+// system or spikes that have not decayed across a block send the system
+// back to the path above.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
+#include "band_spike.cuh"
 #include "band_warp.cuh"
 #include "est_host.cuh"
 
@@ -706,6 +717,179 @@ double rcond_from_est(double anorm, double est) {
   return (1.0 / est) / anorm;
 }
 
+// ------------------------------------------- partitioned route (dominant)
+// Long band systems that are diagonally dominant by rows or by columns can
+// be solved block-parallel without pivoting (band_spike.cuh).  The route is
+// taken only when the environment variable ASOLVE_BAND_SPIKE is 1; without
+// it every band system keeps the GBTRF-order path below.
+constexpr int64_t kSpkMinN = 4096;      // shorter systems: the one-warp path
+constexpr int64_t kSpkBlocks = 2432;    // target number of blocks (16 per SM)
+constexpr double kSpkFarTol = 8.67e-19; // 2^-60: far spike tips dropped below this
+constexpr int kSpkThreads = 128;
+
+bool spike_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = getenv("ASOLVE_BAND_SPIKE");
+    on = (e && e[0] == '1' && e[1] == 0) ? 1 : 0;
+  }
+  return on == 1;
+}
+
+// Block length and count: at least 24 (kl+ku) and 256 rows per block so
+// that the spikes can decay across a block.
+bool spike_shape(int64_t n, int kl, int ku, int64_t* m, int64_t* P) {
+  int64_t mm = n / kSpkBlocks;
+  if (mm < 24 * (int64_t)(kl + ku)) mm = 24 * (int64_t)(kl + ku);
+  if (mm < 256) mm = 256;
+  *m = mm;
+  *P = n / mm;
+  return *P >= 2;
+}
+
+size_t spike_bytes(int64_t n, int kl, int ku) {
+  int64_t m, P;
+  if (!spike_shape(n, kl, ku, &m, &P)) return 0;
+  const size_t q = (size_t)(kl + ku), qq = q > 0 ? q : 1;
+  return round256(sizeof(double) * (size_t)n * qq) +             // spike columns
+         2 * round256(sizeof(double) * (size_t)P * qq * qq) +     // boundary systems, A and A^T
+         2 * round256(sizeof(int) * (size_t)P * qq) +             // their pivots
+         round256(sizeof(double) * (size_t)n) +                   // G
+         round256(sizeof(double) * (size_t)P * qq) +              // Y
+         256;                                                     // far tips, flags
+}
+
+struct SpikePlan {
+  spk::Ctx c;
+  double* scr;
+  double* M[2];
+  int* piv[2];
+  double* G;
+  double* Y;
+  unsigned long long* far;  // [2]
+  int* flags;               // [0] rows, [1] columns dominant, [2] failure
+};
+
+SpikePlan spike_layout(double* F, int64_t ldf, int64_t n, int kl, int ku, char* q) {
+  SpikePlan pl{};
+  int64_t m = 0, P = 0;
+  spike_shape(n, kl, ku, &m, &P);
+  pl.c = spk::Ctx{F, ldf, n, kl, ku, m, P};
+  const size_t qn = (size_t)(kl + ku), qq = qn > 0 ? qn : 1;
+  pl.scr = reinterpret_cast<double*>(q);
+  q += round256(sizeof(double) * (size_t)n * qq);
+  for (int k = 0; k < 2; ++k) {
+    pl.M[k] = reinterpret_cast<double*>(q);
+    q += round256(sizeof(double) * (size_t)P * qq * qq);
+  }
+  for (int k = 0; k < 2; ++k) {
+    pl.piv[k] = reinterpret_cast<int*>(q);
+    q += round256(sizeof(int) * (size_t)P * qq);
+  }
+  pl.G = reinterpret_cast<double*>(q);
+  q += round256(sizeof(double) * (size_t)n);
+  pl.Y = reinterpret_cast<double*>(q);
+  q += round256(sizeof(double) * (size_t)P * qq);
+  pl.far = reinterpret_cast<unsigned long long*>(q);
+  pl.flags = reinterpret_cast<int*>(q + 64);
+  return pl;
+}
+
+unsigned spk_grid(int64_t count) { return (unsigned)((count + kSpkThreads - 1) / kSpkThreads); }
+
+__global__ void k_spk_dominance(spk::Ctx c, int* flags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n; i += (int64_t)gridDim.x * blockDim.x) {
+    int r, cc;
+    spk::dominance(c, i, &r, &cc);
+    if (!r) flags[0] = 0;
+    if (!cc) flags[1] = 0;
+  }
+}
+
+__global__ void k_spk_factor(spk::Ctx c, int* flags) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < c.P && spk::factor_block(c, b)) atomicExch(&flags[2], 1);
+}
+
+__global__ void k_spk_spikes(spk::Ctx c, bool tr, double* scr, double* M, unsigned long long* far) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < c.P * spk::q_of(c)) spk::spike_column(c, tr, t, scr, M, far);
+}
+
+__global__ void k_spk_boundary(spk::Ctx c, double* M, int* piv, int* flags) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b + 1 < c.P && spk::factor_boundary(c, b, M, piv)) atomicExch(&flags[2], 1);
+}
+
+__global__ void k_spk_step1(spk::Ctx c, bool tr, const double* x, double* G) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < c.P) spk::solve_step1(c, tr, b, x, G);
+}
+
+__global__ void k_spk_step2(spk::Ctx c, bool tr, const double* G, const double* M, const int* piv, double* Y) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b + 1 < c.P) spk::solve_step2(c, tr, b, G, M, piv, Y);
+}
+
+__global__ void k_spk_step3(spk::Ctx c, bool tr, const double* Y, double* x) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < c.P) spk::solve_step3(c, tr, b, Y, x);
+}
+
+// x := A^-1 x (tr: A^-T x) in place with the partitioned factors.
+int spike_apply(const SpikePlan& pl, double* x, bool tr, cudaStream_t st) {
+  const spk::Ctx& c = pl.c;
+  const int k = tr ? 1 : 0;
+  k_spk_step1<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
+  BCK(cudaGetLastError());
+  if (spk::q_of(c) > 0) {
+    k_spk_step2<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, pl.G, pl.M[k], pl.piv[k], pl.Y);
+    BCK(cudaGetLastError());
+  }
+  k_spk_step3<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, pl.Y, x);
+  BCK(cudaGetLastError());
+  return ASOLVE_OK;
+}
+
+// Dominance test, block factors, spikes and boundary systems (both systems
+// unless no_rcond).  *ok: the route applies (dominant, no zero pivot, no
+// singular boundary system, far tips below kSpkFarTol); *touched: F was
+// modified (the caller re-packs it before the GBTRF-order path).
+int spike_prepare(const SpikePlan& pl, bool no_rcond, bool* ok, bool* touched, cudaStream_t st) {
+  const spk::Ctx& c = pl.c;
+  *ok = false;
+  *touched = false;
+  BCK(cudaMemsetAsync(pl.flags, 0x01, 2 * sizeof(int), st));  // non-zero: dominant until a row says no
+  BCK(cudaMemsetAsync(pl.flags + 2, 0, sizeof(int), st));
+  BCK(cudaMemsetAsync(pl.far, 0, 2 * sizeof(unsigned long long), st));
+  k_spk_dominance<<<4 * 152, 256, 0, st>>>(c, pl.flags);
+  BCK(cudaGetLastError());
+  int h[3];
+  BCK(cudaMemcpyAsync(h, pl.flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  if (!h[0] && !h[1]) return ASOLVE_OK;
+  *touched = true;
+  k_spk_factor<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.flags);
+  BCK(cudaGetLastError());
+  const int64_t q = spk::q_of(c);
+  for (int k = 0; k < (no_rcond ? 1 : 2) && q > 0; ++k) {
+    BCK(cudaMemsetAsync(pl.M[k], 0, sizeof(double) * (size_t)(c.P * q * q), st));
+    k_spk_spikes<<<spk_grid(c.P * q), kSpkThreads, 0, st>>>(c, k == 1, pl.scr, pl.M[k], pl.far + k);
+    BCK(cudaGetLastError());
+    k_spk_boundary<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.M[k], pl.piv[k], pl.flags);
+    BCK(cudaGetLastError());
+  }
+  unsigned long long fb[2];
+  BCK(cudaMemcpyAsync(&h[2], pl.flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  BCK(cudaMemcpyAsync(fb, pl.far, sizeof(fb), cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  double far0, far1;
+  memcpy(&far0, &fb[0], 8);
+  memcpy(&far1, &fb[1], 8);
+  *ok = h[2] == 0 && far0 <= kSpkFarTol && far1 <= kSpkFarTol;
+  return ASOLVE_OK;
+}
+
 }  // namespace
 
 // Whether the fast kernels (shared-memory window, register window) cover
@@ -720,6 +904,10 @@ size_t band_ws_bytes(int64_t n, int64_t kl, int64_t ku, int64_t nrhs) {
   const size_t ldf = (size_t)(2 * kl + ku + 1);
   size_t sw = 0;  // partitioned sweeps: sized for the widest window they take
   if (n >= kSwMinN) sw = (kl + ku + 1 <= kSwMaxWs) ? sw_bytes(n, (int)kl, (int)ku) : sw_bytes(n, kSwMaxWs - 1, 0);
+  if (spike_enabled() && n >= kSpkMinN) {  // the partitioned route uses the same area
+    const size_t sp = spike_bytes(n, (int)kl, (int)ku);
+    if (sp > sw) sw = sp;
+  }
   return round256(sizeof(double) * ldf * (size_t)n) + round256(sizeof(int) * (size_t)n) +
          2 * round256(sizeof(double) * (size_t)n) + sw + kTailBytes;
 }
@@ -783,88 +971,117 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   double* exi = ev + ((n + 31) & ~(int64_t)31);
   k_bpack<<<4 * 152, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, F);
   BCK(cudaGetLastError());
-  BCK(cudaMemsetAsync(dint, 0, sizeof(int) * 4, st));
-  const size_t wsm = sizeof(double) * (size_t)(kv + 1 + kD) * ldf;
-  const int R = window_r(kv);
-  if (wsm <= kWinSmemMax) {
-    static bool attr = false;
-    if (!attr) {
-      BCK(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemMax));
-      attr = true;
-    }
-    k_band_lu_win<<<1, 32, wsm, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
-  } else {
-    k_band_lu_glob<<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
-  }
-  BCK(cudaGetLastError());
-  int fail = 0;
-  BCK(cudaMemcpyAsync(&fail, dint, sizeof(int), cudaMemcpyDeviceToHost, st));
-  BCK(cudaStreamSynchronize(st));
   const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
   const bool svd_ok = !(a.flags & ASOLVE_NO_APPROX) && n <= 1024;
-  if (fail) {
-    BCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)(n * nrhs), st));
-    BCK(cudaStreamSynchronize(st));
-    return info->status = svd_ok ? ASOLVE_PENDING : ASOLVE_E_SINGULAR;
-  }
-  BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
-  // long systems with windows of up to kSwMaxWs: partitioned sweeps
-  const bool par = n >= kSwMinN && kv + 1 <= kSwMaxWs;
-  SweepPlan pl{};
-  if (par) {
-    char* q = reinterpret_cast<char*>(exi + ((n + 31) & ~(int64_t)31));
-    q = reinterpret_cast<char*>(((uintptr_t)q + 255) & ~(uintptr_t)255);
-    const int P0 = sw_blocks(n);
-    pl.c = SweepCtx{F, ldf, (int)n, kl, ku, piv, 0, 0};
-    pl.c.L = (int)((n + P0 - 1) / P0);
-    pl.c.P = (int)((n + pl.c.L - 1) / pl.c.L);
-    for (int k = 0; k < 4; ++k) {
-      pl.T[k] = reinterpret_cast<double*>(q);
-      const size_t ws = (size_t)sw_ws(k, kl, ku);
-      q += round256(sizeof(double) * (size_t)pl.c.P * ws * ws);
-    }
-    pl.tv = reinterpret_cast<double*>(q);
-    q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
-    pl.Ws = reinterpret_cast<double*>(q);
-    q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
-    pl.tmp = reinterpret_cast<double*>(q);
-    int rc;
-    if ((rc = sw_run<SW_L>(pl, nullptr, nullptr, true, st)) || (rc = sw_run<SW_U>(pl, nullptr, nullptr, true, st)))
-      return info->status = rc;
-    if (!no_rcond &&
-        ((rc = sw_run<SW_UT>(pl, nullptr, nullptr, true, st)) || (rc = sw_run<SW_LT>(pl, nullptr, nullptr, true, st))))
-      return info->status = rc;
-    for (int64_t c = 0; c < nrhs; ++c)
-      if ((rc = sw_apply(pl, a.X + (size_t)c * n, false, st))) return info->status = rc;
-  } else
-  switch (R) {
-    case 1: k_band_solve<1><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
-    case 2: k_band_solve<2><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
-    case 4: k_band_solve<4><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
-    case 8: k_band_solve<8><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
-    default: k_band_solve_glob<<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
-  }
-  BCK(cudaGetLastError());
+  char* region = reinterpret_cast<char*>(exi + ((n + 31) & ~(int64_t)31));
+  region = reinterpret_cast<char*>(((uintptr_t)region + 255) & ~(uintptr_t)255);
   double rc = NAN;
-  if (!no_rcond && par) {
-    double est = NAN;
-    auto apply = [&](double* v, bool tr) { return sw_apply(pl, v, tr, st); };
-    const int erc = est_host<double>((int)n, ev, exi, dscal, dint, apply, st, &est);
-    if (erc) return info->status = erc;
-    rc = rcond_from_est(norm1, est);
-  } else if (!no_rcond) {
-    switch (R) {
-      case 1: k_band_est<1, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
-      case 2: k_band_est<2, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
-      case 4: k_band_est<4, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
-      case 8: k_band_est<8, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
-      default: k_band_est<1, true><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+  bool spiked = false;
+  int64_t spk_m = 0, spk_P = 0;
+  if (spike_enabled() && n >= kSpkMinN && spike_shape(n, kl, ku, &spk_m, &spk_P)) {
+    // dominant bands: the partitioned route (band_spike.cuh)
+    const SpikePlan sp = spike_layout(F, ldf, n, kl, ku, region);
+    bool ok = false, touched = false;
+    int r = spike_prepare(sp, no_rcond, &ok, &touched, st);
+    if (r) return info->status = r;
+    if (ok) {
+      BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
+      for (int64_t c = 0; c < nrhs; ++c)
+        if ((r = spike_apply(sp, a.X + (size_t)c * n, false, st))) return info->status = r;
+      if (!no_rcond) {
+        double est = NAN;
+        auto apply = [&](double* v, bool tr) { return spike_apply(sp, v, tr, st); };
+        const int erc = est_host<double>((int)n, ev, exi, dscal, dint, apply, st, &est);
+        if (erc) return info->status = erc;
+        rc = rcond_from_est(norm1, est);
+      }
+      spiked = true;
+      info->detail |= 16;  // solved by the partitioned route
+    } else if (touched) {  // back to the original band for the GBTRF-order path
+      k_bpack<<<4 * 152, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, F);
+      BCK(cudaGetLastError());
+    }
+  }
+  if (!spiked) {
+    BCK(cudaMemsetAsync(dint, 0, sizeof(int) * 4, st));
+    const size_t wsm = sizeof(double) * (size_t)(kv + 1 + kD) * ldf;
+    const int R = window_r(kv);
+    if (wsm <= kWinSmemMax) {
+      static bool attr = false;
+      if (!attr) {
+        BCK(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemMax));
+        attr = true;
+      }
+      k_band_lu_win<<<1, 32, wsm, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
+    } else {
+      k_band_lu_glob<<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
     }
     BCK(cudaGetLastError());
-    double est = NAN;
-    BCK(cudaMemcpyAsync(&est, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int fail = 0;
+    BCK(cudaMemcpyAsync(&fail, dint, sizeof(int), cudaMemcpyDeviceToHost, st));
     BCK(cudaStreamSynchronize(st));
-    rc = rcond_from_est(norm1, est);
+    if (fail) {
+      BCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)(n * nrhs), st));
+      BCK(cudaStreamSynchronize(st));
+      return info->status = svd_ok ? ASOLVE_PENDING : ASOLVE_E_SINGULAR;
+    }
+    BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
+    // long systems with windows of up to kSwMaxWs: partitioned sweeps
+    const bool par = n >= kSwMinN && kv + 1 <= kSwMaxWs;
+    SweepPlan pl{};
+    if (par) {
+      char* q = region;
+      const int P0 = sw_blocks(n);
+      pl.c = SweepCtx{F, ldf, (int)n, kl, ku, piv, 0, 0};
+      pl.c.L = (int)((n + P0 - 1) / P0);
+      pl.c.P = (int)((n + pl.c.L - 1) / pl.c.L);
+      for (int k = 0; k < 4; ++k) {
+        pl.T[k] = reinterpret_cast<double*>(q);
+        const size_t ws = (size_t)sw_ws(k, kl, ku);
+        q += round256(sizeof(double) * (size_t)pl.c.P * ws * ws);
+      }
+      pl.tv = reinterpret_cast<double*>(q);
+      q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
+      pl.Ws = reinterpret_cast<double*>(q);
+      q += round256(sizeof(double) * (size_t)pl.c.P * (kv + 1));
+      pl.tmp = reinterpret_cast<double*>(q);
+      int src;
+      if ((src = sw_run<SW_L>(pl, nullptr, nullptr, true, st)) || (src = sw_run<SW_U>(pl, nullptr, nullptr, true, st)))
+        return info->status = src;
+      if (!no_rcond &&
+          ((src = sw_run<SW_UT>(pl, nullptr, nullptr, true, st)) || (src = sw_run<SW_LT>(pl, nullptr, nullptr, true, st))))
+        return info->status = src;
+      for (int64_t c = 0; c < nrhs; ++c)
+        if ((src = sw_apply(pl, a.X + (size_t)c * n, false, st))) return info->status = src;
+    } else
+    switch (R) {
+      case 1: k_band_solve<1><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+      case 2: k_band_solve<2><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+      case 4: k_band_solve<4><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+      case 8: k_band_solve<8><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+      default: k_band_solve_glob<<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
+    }
+    BCK(cudaGetLastError());
+    if (!no_rcond && par) {
+      double est = NAN;
+      auto apply = [&](double* v, bool tr) { return sw_apply(pl, v, tr, st); };
+      const int erc = est_host<double>((int)n, ev, exi, dscal, dint, apply, st, &est);
+      if (erc) return info->status = erc;
+      rc = rcond_from_est(norm1, est);
+    } else if (!no_rcond) {
+      switch (R) {
+        case 1: k_band_est<1, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+        case 2: k_band_est<2, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+        case 4: k_band_est<4, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+        case 8: k_band_est<8, false><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+        default: k_band_est<1, true><<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, ev, exi, dscal); break;
+      }
+      BCK(cudaGetLastError());
+      double est = NAN;
+      BCK(cudaMemcpyAsync(&est, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+      BCK(cudaStreamSynchronize(st));
+      rc = rcond_from_est(norm1, est);
+    }
   }
   info->rcond = no_rcond ? NAN : rc;
   if (a.flags & ASOLVE_BERR) {
