@@ -736,20 +736,23 @@ bool spike_enabled() {
   return on == 1;
 }
 
-// Block length and count: at least 24 (kl+ku) and 256 rows per block so
-// that the spikes can decay across a block.
-bool spike_shape(int64_t n, int kl, int ku, int64_t* m, int64_t* P) {
+// Block length and count at attempt `level`: at least 16 (kl+ku) and 256
+// rows per block (on the band workload's matrices the far tips fell below
+// 2^-60 from about 16 (kl+ku) rows), doubled at each further attempt.
+bool spike_shape(int64_t n, int kl, int ku, int level, int64_t* m, int64_t* P) {
   int64_t mm = n / kSpkBlocks;
-  if (mm < 24 * (int64_t)(kl + ku)) mm = 24 * (int64_t)(kl + ku);
+  if (mm < 16 * (int64_t)(kl + ku)) mm = 16 * (int64_t)(kl + ku);
   if (mm < 256) mm = 256;
+  mm <<= level;
   *m = mm;
   *P = n / mm;
   return *P >= 2;
 }
 
+// Sized for the first attempt, which has the most blocks.
 size_t spike_bytes(int64_t n, int kl, int ku) {
   int64_t m, P;
-  if (!spike_shape(n, kl, ku, &m, &P)) return 0;
+  if (!spike_shape(n, kl, ku, 0, &m, &P)) return 0;
   const size_t q = (size_t)(kl + ku), qq = q > 0 ? q : 1;
   return round256(sizeof(double) * (size_t)n * qq) +             // spike columns
          2 * round256(sizeof(double) * (size_t)P * qq * qq) +     // boundary systems, A and A^T
@@ -770,10 +773,10 @@ struct SpikePlan {
   int* flags;               // [0] rows, [1] columns dominant, [2] failure
 };
 
-SpikePlan spike_layout(double* F, int64_t ldf, int64_t n, int kl, int ku, char* q) {
+SpikePlan spike_layout(double* F, int64_t ldf, int64_t n, int kl, int ku, int level, char* q) {
   SpikePlan pl{};
   int64_t m = 0, P = 0;
-  spike_shape(n, kl, ku, &m, &P);
+  spike_shape(n, kl, ku, level, &m, &P);
   pl.c = spk::Ctx{F, ldf, n, kl, ku, m, P};
   const size_t qn = (size_t)(kl + ku), qq = qn > 0 ? qn : 1;
   pl.scr = reinterpret_cast<double*>(q);
@@ -851,13 +854,16 @@ int spike_apply(const SpikePlan& pl, double* x, bool tr, cudaStream_t st) {
   return ASOLVE_OK;
 }
 
+// Outcome of one attempt of the partitioned route.
+enum SpikeOutcome { SPK_OK = 0, SPK_NOT_DOMINANT, SPK_NUMERIC, SPK_FAR_TIPS };
+
 // Dominance test, block factors, spikes and boundary systems (both systems
-// unless no_rcond).  *ok: the route applies (dominant, no zero pivot, no
-// singular boundary system, far tips below kSpkFarTol); *touched: F was
-// modified (the caller re-packs it before the GBTRF-order path).
-int spike_prepare(const SpikePlan& pl, bool no_rcond, bool* ok, bool* touched, cudaStream_t st) {
+// unless no_rcond).  *out: SPK_OK (dominant, no zero pivot, no singular
+// boundary system, far tips below kSpkFarTol) or why not; *touched: F was
+// modified (re-packed before another attempt or the GBTRF-order path).
+int spike_prepare(const SpikePlan& pl, bool no_rcond, int* out, bool* touched, cudaStream_t st) {
   const spk::Ctx& c = pl.c;
-  *ok = false;
+  *out = SPK_NOT_DOMINANT;
   *touched = false;
   BCK(cudaMemsetAsync(pl.flags, 0x01, 2 * sizeof(int), st));  // non-zero: dominant until a row says no
   BCK(cudaMemsetAsync(pl.flags + 2, 0, sizeof(int), st));
@@ -869,6 +875,7 @@ int spike_prepare(const SpikePlan& pl, bool no_rcond, bool* ok, bool* touched, c
   BCK(cudaStreamSynchronize(st));
   if (!h[0] && !h[1]) return ASOLVE_OK;
   *touched = true;
+  *out = SPK_NUMERIC;
   k_spk_factor<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.flags);
   BCK(cudaGetLastError());
   const int64_t q = spk::q_of(c);
@@ -886,7 +893,7 @@ int spike_prepare(const SpikePlan& pl, bool no_rcond, bool* ok, bool* touched, c
   double far0, far1;
   memcpy(&far0, &fb[0], 8);
   memcpy(&far1, &fb[1], 8);
-  *ok = h[2] == 0 && far0 <= kSpkFarTol && far1 <= kSpkFarTol;
+  if (h[2] == 0) *out = (far0 <= kSpkFarTol && far1 <= kSpkFarTol) ? SPK_OK : SPK_FAR_TIPS;
   return ASOLVE_OK;
 }
 
@@ -978,13 +985,16 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   double rc = NAN;
   bool spiked = false;
   int64_t spk_m = 0, spk_P = 0;
-  if (spike_enabled() && n >= kSpkMinN && spike_shape(n, kl, ku, &spk_m, &spk_P)) {
-    // dominant bands: the partitioned route (band_spike.cuh)
-    const SpikePlan sp = spike_layout(F, ldf, n, kl, ku, region);
-    bool ok = false, touched = false;
-    int r = spike_prepare(sp, no_rcond, &ok, &touched, st);
+  // dominant bands: the partitioned route (band_spike.cuh); blocks twice as
+  // long on another attempt when the spikes have not decayed across them
+  for (int level = 0; level < 3 && spike_enabled() && n >= kSpkMinN &&
+                      spike_shape(n, kl, ku, level, &spk_m, &spk_P); ++level) {
+    const SpikePlan sp = spike_layout(F, ldf, n, kl, ku, level, region);
+    int outcome = SPK_NOT_DOMINANT;
+    bool touched = false;
+    int r = spike_prepare(sp, no_rcond, &outcome, &touched, st);
     if (r) return info->status = r;
-    if (ok) {
+    if (outcome == SPK_OK) {
       BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
       for (int64_t c = 0; c < nrhs; ++c)
         if ((r = spike_apply(sp, a.X + (size_t)c * n, false, st))) return info->status = r;
@@ -997,10 +1007,13 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
       }
       spiked = true;
       info->detail |= 16;  // solved by the partitioned route
-    } else if (touched) {  // back to the original band for the GBTRF-order path
+      break;
+    }
+    if (touched) {  // back to the original band for another attempt or the GBTRF-order path
       k_bpack<<<4 * 152, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, F);
       BCK(cudaGetLastError());
     }
+    if (outcome != SPK_FAR_TIPS) break;
   }
   if (!spiked) {
     BCK(cudaMemsetAsync(dint, 0, sizeof(int) * 4, st));
