@@ -839,17 +839,60 @@ __global__ void k_spk_step3(spk::Ctx c, bool tr, const double* Y, double* x) {
   if (b < c.P) spk::solve_step3(c, tr, b, Y, x);
 }
 
+// Wide bands (kl + ku >= kSpkWarpQ): one warp per block for the block
+// factorisation and the block solves, lanes over the rows of each step.
+constexpr int64_t kSpkWarpQ = 16;
+bool spk_warp(const spk::Ctx& c) { return spk::q_of(c) >= kSpkWarpQ; }
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_factor_w(spk::Ctx c, int* flags) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;  // the whole warp
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  if (spk::wfactor_block(c, b, run) && lane == 0) atomicExch(&flags[2], 1);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_step1_w(spk::Ctx c, bool tr, const double* x, double* G) {
+  __shared__ double red[kSpkThreads];
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  spk::wsolve_step1(c, tr, b, x, G, red + (threadIdx.x & ~31u), run);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_step3_w(spk::Ctx c, bool tr, const double* Y, double* x) {
+  __shared__ double red[kSpkThreads];
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  spk::wsolve_step3(c, tr, b, Y, x, red + (threadIdx.x & ~31u), run);
+}
+
 // x := A^-1 x (tr: A^-T x) in place with the partitioned factors.
 int spike_apply(const SpikePlan& pl, double* x, bool tr, cudaStream_t st) {
   const spk::Ctx& c = pl.c;
   const int k = tr ? 1 : 0;
-  k_spk_step1<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
+  const bool w = spk_warp(c);
+  if (w) k_spk_step1_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
+  else k_spk_step1<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
   BCK(cudaGetLastError());
   if (spk::q_of(c) > 0) {
     k_spk_step2<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, pl.G, pl.M[k], pl.piv[k], pl.Y);
     BCK(cudaGetLastError());
   }
-  k_spk_step3<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, pl.Y, x);
+  if (w) k_spk_step3_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, pl.Y, x);
+  else k_spk_step3<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, pl.Y, x);
   BCK(cudaGetLastError());
   return ASOLVE_OK;
 }
@@ -876,7 +919,8 @@ int spike_prepare(const SpikePlan& pl, bool no_rcond, int* out, bool* touched, c
   if (!h[0] && !h[1]) return ASOLVE_OK;
   *touched = true;
   *out = SPK_NUMERIC;
-  k_spk_factor<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.flags);
+  if (spk_warp(c)) k_spk_factor_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, pl.flags);
+  else k_spk_factor<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.flags);
   BCK(cudaGetLastError());
   const int64_t q = spk::q_of(c);
   for (int k = 0; k < (no_rcond ? 1 : 2) && q > 0; ++k) {

@@ -263,6 +263,155 @@ SPK_HD void solve_step3(const Ctx& c, bool tr, int64_t b, const double* Y, doubl
   solve_block(c, b, tr, x + s);
 }
 
+// ---------------------------------------------------------------- warps
+// Warp-cooperative versions of the block factorisation and the block
+// solves, for wide bands.  Each is a sequence of phases over lanes
+// 0..31: within a phase every lane writes entries no other lane touches and
+// reads only entries that no lane writes in that phase; the kernels put a
+// __syncwarp() between phases, and running the lanes of a phase one after
+// another gives the same result.  `red` is 32 doubles of per-warp scratch.
+
+// Factorisation, column j: (1) multipliers, rows j+1+lane, j+33+lane, ...
+SPK_HD void wlu_mult(const Ctx& c, int64_t e, int64_t j, int lane) {
+  const double p = fa(c, j, j);
+  const int64_t lo = imin(e - 1, j + c.kl);
+  for (int64_t i = j + 1 + lane; i <= lo; i += 32) fa(c, i, j) = fa(c, i, j) / p;
+}
+// (2) rank-1 update of the same rows, columns j+1 .. j+ku
+SPK_HD void wlu_update(const Ctx& c, int64_t e, int64_t j, int lane) {
+  const int64_t lo = imin(e - 1, j + c.kl), hi = imin(e - 1, j + c.ku);
+  for (int64_t i = j + 1 + lane; i <= lo; i += 32) {
+    const double l = fa(c, i, j);
+    if (l == 0.0) continue;
+    for (int64_t q = j + 1; q <= hi; ++q) fa(c, i, q) -= l * fa(c, j, q);
+  }
+}
+
+// Solve with A_bb, column j of L (forward): one phase.
+SPK_HD void wsolve_l(const Ctx& c, int64_t s, int64_t e, int64_t j, int lane, double* xl) {
+  const double xj = xl[j - s];
+  const int64_t lo = imin(e - 1, j + c.kl);
+  for (int64_t i = j + 1 + lane; i <= lo; i += 32) xl[i - s] -= fa(c, i, j) * xj;
+}
+// Column j of U (backward): (1) lane 0 divides, (2) the rows above update.
+SPK_HD void wsolve_u_div(const Ctx& c, int64_t s, int64_t j, int lane, double* xl) {
+  if (lane == 0) xl[j - s] = xl[j - s] / fa(c, j, j);
+}
+SPK_HD void wsolve_u_upd(const Ctx& c, int64_t s, int64_t j, int lane, double* xl) {
+  const double xj = xl[j - s];
+  for (int64_t i = imax(s, j - c.ku) + lane; i < j; i += 32) xl[i - s] -= fa(c, i, j) * xj;
+}
+// Solve with A_bb^T, row j of U^T (forward): (1) partial dot products,
+// (2) lane 0 sums them in lane order and divides.
+SPK_HD void wsolve_ut_dot(const Ctx& c, int64_t s, int64_t j, int lane, const double* xl, double* red) {
+  double t = 0.0;
+  for (int64_t i = imax(s, j - c.ku) + lane; i < j; i += 32) t += fa(c, i, j) * xl[i - s];
+  red[lane] = t;
+}
+SPK_HD void wsolve_ut_fin(const Ctx& c, int64_t s, int64_t j, int lane, double* xl, const double* red) {
+  if (lane != 0) return;
+  double t = 0.0;
+  for (int k = 0; k < 32; ++k) t += red[k];
+  xl[j - s] = (xl[j - s] - t) / fa(c, j, j);
+}
+// Row j of L^T (backward): (1) partial dot products, (2) lane 0 subtracts.
+SPK_HD void wsolve_lt_dot(const Ctx& c, int64_t s, int64_t e, int64_t j, int lane, const double* xl, double* red) {
+  double t = 0.0;
+  const int64_t lo = imin(e - 1, j + c.kl);
+  for (int64_t i = j + 1 + lane; i <= lo; i += 32) t += fa(c, i, j) * xl[i - s];
+  red[lane] = t;
+}
+SPK_HD void wsolve_lt_fin(int64_t s, int64_t j, int lane, double* xl, const double* red) {
+  if (lane != 0) return;
+  double t = 0.0;
+  for (int k = 0; k < 32; ++k) t += red[k];
+  xl[j - s] = xl[j - s] - t;
+}
+
+// Block drivers over a phase runner: run(f) calls f(lane) for this thread's
+// lane and then __syncwarp() (device), or f(0) .. f(31) in turn (host).
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD int wfactor_block(const Ctx& c, int64_t b, Run&& run) {
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  for (int64_t j = s; j < e; ++j) {
+    const double p = fa(c, j, j);  // every lane reads the same value: a uniform branch
+    if (!(p != 0.0) || p != p) return (int)(j - s) + 1;
+    run([&](int lane) { wlu_mult(c, e, j, lane); });
+    run([&](int lane) { wlu_update(c, e, j, lane); });
+  }
+  return 0;
+}
+
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD void wsolve_block(const Ctx& c, int64_t b, bool tr, double* xl, double* red, Run&& run) {
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  if (!tr) {
+    for (int64_t j = s; j < e; ++j)
+      if (xl[j - s] != 0.0) run([&](int lane) { wsolve_l(c, s, e, j, lane, xl); });
+    for (int64_t j = e - 1; j >= s; --j) {
+      run([&](int lane) { wsolve_u_div(c, s, j, lane, xl); });
+      run([&](int lane) { wsolve_u_upd(c, s, j, lane, xl); });
+    }
+  } else {
+    for (int64_t j = s; j < e; ++j) {
+      run([&](int lane) { wsolve_ut_dot(c, s, j, lane, xl, red); });
+      run([&](int lane) { wsolve_ut_fin(c, s, j, lane, xl, red); });
+    }
+    for (int64_t j = e - 1; j >= s; --j) {
+      run([&](int lane) { wsolve_lt_dot(c, s, e, j, lane, xl, red); });
+      run([&](int lane) { wsolve_lt_fin(s, j, lane, xl, red); });
+    }
+  }
+}
+
+// Solve steps 1 and 3 with one warp per block (steps 2 is per boundary).
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD void wsolve_step1(const Ctx& c, bool tr, int64_t b, const double* x, double* G, double* red, Run&& run) {
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  run([&](int lane) {
+    for (int64_t i = s + lane; i < e; i += 32) G[i] = x[i];
+  });
+  wsolve_block(c, b, tr, G + s, red, run);
+}
+
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD void wsolve_step3(const Ctx& c, bool tr, int64_t b, const double* Y, double* x, double* red, Run&& run) {
+  const int64_t q = q_of(c);
+  const int kl = sys_kl(c, tr), ku = sys_ku(c, tr);
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  // couplings with the neighbours' boundary unknowns: rows split over lanes
+  run([&](int lane) {
+    for (int64_t i = s + lane; i < e; i += 32) {
+      if (i < e - ku && i >= s + kl) continue;  // rows no coupling reaches
+      double t = x[i];
+      if (b + 1 < c.P)
+        for (int r = 0; r < ku; ++r) {
+          const int64_t J = e + r;
+          if (i >= J - ku) t -= sys_at(c, tr, i, J) * Y[(size_t)b * (size_t)q + kl + r];
+        }
+      if (b > 0)
+        for (int r = 0; r < kl; ++r) {
+          const int64_t J = s - kl + r;
+          if (i <= J + kl) t -= sys_at(c, tr, i, J) * Y[(size_t)(b - 1) * (size_t)q + r];
+        }
+      x[i] = t;
+    }
+  });
+  wsolve_block(c, b, tr, x + s, red, run);
+}
+
 // Diagonal dominance of the original matrix in F (before any factoring):
 // row i (by rows) and column i (by columns); one thread per index.
 SPK_HD void dominance(const Ctx& c, int64_t i, int* rowdom, int* coldom) {

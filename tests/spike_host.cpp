@@ -13,13 +13,27 @@ using namespace asv::spk;
 
 namespace {
 
-void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::vector<int>& piv, double* x) {
+// The warp kernels' phase runner on the host: the 32 lanes of a phase in
+// turn, in increasing or (to expose any dependence between the lanes of one
+// phase) decreasing order.
+bool g_reverse = false;
+auto lanes = [](auto&& f) {
+  for (int k = 0; k < 32; ++k) f(g_reverse ? 31 - k : k);
+};
+
+void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::vector<int>& piv, double* x,
+               bool warp) {
   const int64_t q = q_of(c);
   std::vector<double> G((size_t)c.n), Y((size_t)(c.P * (q > 0 ? q : 1)));
-  for (int64_t b = 0; b < c.P; ++b) solve_step1(c, tr, b, x, G.data());
+  double red[32];
+  for (int64_t b = 0; b < c.P; ++b)
+    if (warp) wsolve_step1(c, tr, b, x, G.data(), red, lanes);
+    else solve_step1(c, tr, b, x, G.data());
   if (q > 0)
     for (int64_t b = 0; b + 1 < c.P; ++b) solve_step2(c, tr, b, G.data(), M.data(), piv.data(), Y.data());
-  for (int64_t b = 0; b < c.P; ++b) solve_step3(c, tr, b, Y.data(), x);
+  for (int64_t b = 0; b < c.P; ++b)
+    if (warp) wsolve_step3(c, tr, b, Y.data(), x, red, lanes);
+    else solve_step3(c, tr, b, Y.data(), x);
 }
 
 }  // namespace
@@ -27,10 +41,14 @@ void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::v
 // AB: A in band storage, A(i,j) at AB[ku + i - j + j*ldab].  Solves A x = b
 // into x and A^T xt = b into xt (b: n values).  far[0], far[1]: the largest
 // far-tip entry for A and for A^T; dom[0], dom[1]: dominance by rows / by
-// columns.  Returns 0, -1 - b if block b has a zero pivot, -1000 - b if
-// boundary system b is singular.
+// columns.  warp: the one-warp-per-block factorisation and block solves
+// (lanes run phase by phase; 2: lanes in decreasing order) instead of one
+// thread per block.  Returns 0,
+// -1 - b if block b has a zero pivot, -1000 - b if boundary system b is
+// singular.
 extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, int64_t n, int64_t m,
-                                const double* bvec, double* x, double* xt, double* far, int* dom) {
+                                const double* bvec, double* x, double* xt, double* far, int* dom, int warp) {
+  g_reverse = warp == 2;
   const int64_t ldf = 2 * (int64_t)kl + ku + 1, kv = (int64_t)kl + ku;
   std::vector<double> F((size_t)(ldf * n), 0.0);
   for (int64_t j = 0; j < n; ++j)
@@ -45,7 +63,7 @@ extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, 
     dom[1] &= cc;
   }
   for (int64_t b = 0; b < c.P; ++b)
-    if (factor_block(c, b)) return (int)(-1 - b);
+    if (warp ? wfactor_block(c, b, lanes) : factor_block(c, b)) return (int)(-1 - b);
   const int64_t q = q_of(c);
   std::vector<double> scr((size_t)(n * (q > 0 ? q : 1)));
   std::vector<double> M[2];
@@ -61,7 +79,7 @@ extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, 
   }
   memcpy(x, bvec, sizeof(double) * (size_t)n);
   memcpy(xt, bvec, sizeof(double) * (size_t)n);
-  solve_sys(c, false, M[0], piv[0], x);
-  solve_sys(c, true, M[1], piv[1], xt);
+  solve_sys(c, false, M[0], piv[0], x, warp != 0);
+  solve_sys(c, true, M[1], piv[1], xt, warp != 0);
   return 0;
 }

@@ -26,7 +26,7 @@ def shim(tmp_path_factory):
     lib = C.CDLL(out)
     pd, i64 = C.POINTER(C.c_double), C.c_int64
     lib.spike_host_solve.argtypes = [pd, i64, C.c_int, C.c_int, i64, i64, pd, pd, pd, pd,
-                                     C.POINTER(C.c_int)]
+                                     C.POINTER(C.c_int), C.c_int]
     lib.spike_host_solve.restype = C.c_int
     return lib
 
@@ -35,14 +35,15 @@ def _p(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def run(shim, AB, kl, ku, m, b):
-    """AB: (kl+ku+1, n) band storage, A(i,j) at AB[ku+i-j, j]."""
+def run(shim, AB, kl, ku, m, b, warp=0):
+    """AB: (kl+ku+1, n) band storage, A(i,j) at AB[ku+i-j, j].  warp: the
+    one-warp-per-block routines, lanes run phase by phase."""
     AB = np.asfortranarray(AB, dtype=np.float64)
     n = AB.shape[1]
     x, xt, far = np.zeros(n), np.zeros(n), np.zeros(2)
     dom = (C.c_int * 2)()
     rc = shim.spike_host_solve(_p(AB), AB.shape[0], kl, ku, n, m, _p(np.ascontiguousarray(b)), _p(x),
-                               _p(xt), _p(far), dom)
+                               _p(xt), _p(far), dom, int(warp))
     return rc, x, xt, far, (dom[0], dom[1])
 
 
@@ -77,10 +78,11 @@ def check(orc, AB, kl, ku, x, xt, b):
 @pytest.mark.parametrize("n,kl,ku,m", [(3000, 2, 2, 300), (3000, 8, 8, 375), (3000, 32, 32, 750),
                                        (2500, 3, 0, 250), (2500, 0, 5, 250), (2000, 7, 2, 333),
                                        (1999, 1, 9, 401)])
-def test_row_dominant_bands_against_oracle(orc, shim, n, kl, ku, m):
+@pytest.mark.parametrize("warp", [False, True])
+def test_row_dominant_bands_against_oracle(orc, shim, n, kl, ku, m, warp):
     AB = row_dominant(n, kl, ku, n + kl)
     b = np.random.default_rng(kl + 10 * ku).standard_normal(n)
-    rc, x, xt, far, dom = run(shim, AB, kl, ku, m, b)
+    rc, x, xt, far, dom = run(shim, AB, kl, ku, m, b, warp)
     assert rc == 0 and dom[0] == 1
     assert far.max() < 1e-20, far  # truncation exact to rounding
     check(orc, AB, kl, ku, x, xt, b)
@@ -107,7 +109,7 @@ def test_column_dominant_band(orc, shim):
         j = np.arange(max(0, -d), min(n, n - d))
         AB[r, j] = A[j + d, j]
     b = rng.standard_normal(n)
-    rc, x, xt, far, dom = run(shim, AB, kl, ku, 300, b)
+    rc, x, xt, far, dom = run(shim, AB, kl, ku, 300, b, warp=True)
     assert rc == 0 and dom[1] == 1
     assert far.max() < 1e-20, far
     check(orc, AB, kl, ku, x, xt, b)
@@ -132,3 +134,30 @@ def test_zero_pivot_reports_the_block(shim):
     AB[:, 450] = 0.0
     rc, *_ = run(shim, AB, k, k, 150, np.ones(n))
     assert rc == -1 - 3
+
+
+def test_warp_and_thread_routines_agree(shim):
+    """The two versions take the same arithmetic steps per element (only the
+    order of the dot-product sums of the transposed solve differs)."""
+    n, k = 3000, 20
+    AB = row_dominant(n, k, k, 9)
+    b = np.random.default_rng(9).standard_normal(n)
+    r1 = run(shim, AB, k, k, 700, b, warp=False)
+    r2 = run(shim, AB, k, k, 700, b, warp=True)
+    assert r1[0] == r2[0] == 0
+    assert np.array_equal(r1[1], r2[1])
+    assert np.abs(r1[2] - r2[2]).max() <= 1e-14 * np.abs(r1[2]).max()
+
+
+@pytest.mark.parametrize("kl,ku", [(20, 20), (40, 5), (3, 37), (70, 70)])
+def test_warp_phases_do_not_depend_on_lane_order(shim, kl, ku):
+    """Within a phase no lane reads what another lane writes: running the
+    lanes of every phase in the opposite order gives the same bits."""
+    n = 4000
+    AB = row_dominant(n, kl, ku, kl + ku)
+    b = np.random.default_rng(kl).standard_normal(n)
+    m = max(16 * (kl + ku), 256)
+    fwd = run(shim, AB, kl, ku, m, b, warp=1)
+    rev = run(shim, AB, kl, ku, m, b, warp=2)
+    assert fwd[0] == rev[0] == 0
+    assert np.array_equal(fwd[1], rev[1]) and np.array_equal(fwd[2], rev[2])
