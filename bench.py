@@ -258,6 +258,40 @@ def oracle_solve_verified(oracle, A, B):
     return bool(np.all(berr <= BERR_BAR))
 
 
+def oracle_time_ms(fn, reps=1):
+    """Median wall time of fn() in ms (the oracle on one host core)."""
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        fn()
+        t.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(t)
+
+
+def oracle_large_baseline(kinds, sizes, kappa=1e4, n0=2048):
+    """The oracle on one n0 system per kind (same recipes as the large
+    workload, CPU generator), extrapolated to each size by n^3 (n^2 for
+    the triangular route): a naive O(n^3) solve at n = 16384 would take
+    hours.  Returns {kind: {"measured_ms": ms at n0, "extrapolated_ms": {n: ms}}}."""
+    import oracle
+    from paper_2007_11208_gb300 import synth
+    oracle.build()
+    out = {}
+    for kind in kinds:
+        g = synth.gen(int(n0 + 17 * kappa) % 100003)
+        if kind == "lower":
+            M = synth.tri_dd(n0, g, lower=True)
+        else:
+            M = synth.spectrum_fast(n0, g, kappa, spd=(kind == "spd"))
+        A = M.numpy().T
+        b = synth.rhs(n0, 1, g).numpy().reshape(n0, 1)
+        ms = oracle_time_ms(lambda: oracle.solve(A, b))
+        p = 2 if kind == "lower" else 3
+        out[kind] = {"measured_ms": ms, "n": n0,
+                     "extrapolated_ms": {str(n): ms * (n / n0) ** p for n in sizes}}
+    return out
+
+
 def oracle_sample(pk, budget_s=15.0, max_threads=None):
     """Time the oracle as it stands on a bounded sample of the batch."""
     import oracle
@@ -586,6 +620,15 @@ def large_workload(args):
     head = head[0] if head else cases[-1]
     hp = "mixed" if "mixed" in head else "fp64"
     ok = head[hp]["rc"] == 0 and head[hp]["berr"] <= BERR_BAR
+    cpu = None
+    if args.cpu_baseline:
+        ob = oracle_large_baseline(kinds, sizes)
+        hk = ob.get(head["kind"])
+        cpu = {"value": 1000.0 / hk["extrapolated_ms"][str(head["n"])] if hk else None, "unit": "solves/s",
+               "cores": 1, "kind": "oracle",
+               "sample": "one n = 2048 system per kind on one host core (nrhs 1), extrapolated by n^3 "
+                         "(n^2 for the triangular route) to each size",
+               "per_kind": ob}
     print(json.dumps({
         "metric": "solves/s at backward err <=1e-13 (single large dense system)",
         "value": (1000.0 / head[hp]["ms"]) if ok else 0.0, "unit": "solves/s",
@@ -596,7 +639,7 @@ def large_workload(args):
                                f"kappa={head['kappa']:.0e}, nrhs={head['nrhs']}, {hp}",
                    "l2": "inputs larger than L2"},
         "fp64_path_ms": head.get("fp64", {}).get("ms"), "speedup_vs_fp64_path": head.get("speedup"),
-        "roofline": head[hp].get("roofline"),
+        "roofline": head[hp].get("roofline"), "cpu_baseline": cpu,
         "clocks": clk.summary(), "cases": cases}), flush=True)
 
 
@@ -620,7 +663,7 @@ def band_workload(args):
     hbm = peaks.get("hbm_gbs") or 6800.0
     ctx = asolve.Context()
     st = torch.cuda.ExternalStream(ctx.stream)
-    rows = []
+    rows, cpu_ms = [], {}
     with ClockSampler(0) as clk:
         for k in ks:
             g = synth.gen(1000 + k, dev)
@@ -651,6 +694,14 @@ def band_workload(args):
                 rows.append(row)
                 log(f"band n={n} k={k} nrhs={nrhs}: {ms:.2f} ms rc={rc} berr={info['berr']:.2e} "
                     f"A+B+X at {row['io_gbs']:.1f} GB/s")
+            if args.cpu_baseline:  # the oracle on the same system, one right-hand side, one host core
+                import oracle
+                oracle.build()
+                ABh = np.asfortranarray(AB.cpu().numpy().T)  # LAPACK layout (2k+1, n)
+                bh = Bm[0].cpu().numpy().copy()
+                cpu_ms[k] = oracle_time_ms(lambda: oracle.solve_band(ABh, k, k, bh))
+                log(f"band n={n} k={k}: oracle {cpu_ms[k]:.0f} ms")
+                del ABh
             del AB, Bm
             torch.cuda.empty_cache()
     ctx.close()
@@ -664,6 +715,9 @@ def band_workload(args):
         "config": {"workload": f"band: n={n}, kl=ku in {ks}, nrhs in {nrhs_list}, diagonally dominant, "
                                "band storage" + (", partitioned route enabled" if args.band_spike else ""),
                    "l2": "inputs larger than L2"},
+        "cpu_baseline": ({"value": 1000.0 / cpu_ms[ks[0]], "unit": "solves/s", "cores": 1, "kind": "oracle",
+                          "sample": "one solve of the same system per k, one right-hand side, one host core",
+                          "ms_per_k": {str(k): v for k, v in cpu_ms.items()}} if cpu_ms else None),
         "roofline_note": "the band factorisation is a sequential chain along n; io_gbs is the band of A, "
                          "B and X read or written once over the whole call, against the measured HBM copy "
                          "bandwidth",
@@ -745,13 +799,22 @@ def plain_workload(args):
             log(rows[-1])
     ctx.close()
     floor = launch_floor_us()
+    cpu = None
+    if args.cpu_baseline:  # the oracle on the same five systems, one host core
+        import oracle
+        oracle.build()
+        bh = b.cpu().numpy().reshape(n, 1)
+        per = {name: oracle_time_ms(lambda A=A: oracle.solve(A.cpu().numpy().T, bh), reps=20) * 1e3
+               for name, A in mats.items()}
+        cpu = {"value": float(np.median(list(per.values()))), "unit": "us", "cores": 1, "kind": "oracle",
+               "sample": "the same five systems, 20 solves each, median", "per_system_us": per}
     med = float(np.median([r["p50_us"] for r in rows]))
     print(json.dumps({
         "metric": "latency of one adaptive solve (n=200, 1 rhs), median over the five systems",
         "value": med, "unit": "us", "n_gpus": 1, "steps": args.reps, "warmup": 20, "ms_per_step": med / 1e3,
         "higher_is_better": False, "scaling": "replicas only", "vs_baseline": None, "dtype": "f64 (mixed)",
         "data": "synthetic", "config": {"workload": "plain-200: general/lower/spd/tridiag/ill, seed 0"},
-        "launch_floor_us": floor,
+        "launch_floor_us": floor, "cpu_baseline": cpu,
         "e2e": {"value": float(np.median([r["e2e_p50_us"] for r in rows])), "unit": "us",
                 "h2d_bytes_per_step": 8 * (n * n + n), "d2h_bytes_per_step": 8 * n + 64},
         "clocks": clk.summary(), "systems": rows}), flush=True)

@@ -90,3 +90,11 @@ def test_launch_floor_never_raises():
     # without a GPU the capture fails and the plain workload reports None
     r = bench.launch_floor_us(reps=5)
     assert r is None or r > 0
+
+
+def test_oracle_large_baseline_extrapolates_by_the_route_order(orc):
+    r = bench.oracle_large_baseline(["general", "lower"], [1024, 2048], n0=256)
+    g, t = r["general"], r["lower"]
+    assert g["n"] == t["n"] == 256 and g["measured_ms"] > 0 and t["measured_ms"] > 0
+    assert g["extrapolated_ms"]["2048"] == pytest.approx(g["measured_ms"] * 8 ** 3)
+    assert t["extrapolated_ms"]["1024"] == pytest.approx(t["measured_ms"] * 4 ** 2)
