@@ -828,6 +828,34 @@ PAPER_TABLES = {"band5": [67.89, 83.45, 89.02, 91.18], "lower": [72.78, 73.59, 7
                 "sympd": [17.35, 25.62, 24.02, 27.54], "dense": [-1.627, -0.243, -0.114, -0.187]}
 
 
+def oracle_replica_tables(sizes=(100, 250, 500, 1000), count=4):
+    """The paper's comparison with the oracle on one host core: the
+    adaptive solve against the forced-LU solve, `count` systems per kind
+    and n (the replica recipes, CPU generator), mean time per system."""
+    import oracle
+    from paper_2007_11208_gb300 import synth
+    oracle.build()
+    out = {}
+    for kind in synth.REPLICA_KINDS:
+        rows = []
+        for n in sizes:
+            pk = synth.replica_batch(kind, n, count, SEED + n)
+            mats = []
+            for s_ in range(count):
+                o, q = int(pk["a_off"][s_]), int(pk["b_off"][s_])
+                mats.append((pk["A"][o:o + n * n].numpy().reshape(n, n).T, pk["B"][q:q + n].numpy().copy()))
+            t = {}
+            for name, flags in (("standard", oracle.FORCE_LU), ("adaptive", 0)):
+                t0 = time.perf_counter()
+                for A, b in mats:
+                    oracle.solve(A, b, flags=flags)
+                t[name] = (time.perf_counter() - t0) / count
+            rows.append({"n": n, "standard_s": t["standard"], "adaptive_s": t["adaptive"],
+                         "reduction_pct": 100.0 * (1.0 - t["adaptive"] / t["standard"])})
+        out[kind] = rows
+    return out
+
+
 def replica_workload(args):
     """The paper's evaluation (Sec. 3, Tables 1-4) on the GPU.  For each
     matrix kind and n, one batch of --replica-count random systems (one
@@ -901,7 +929,9 @@ def replica_workload(args):
         "config": {"workload": f"paper-replica: {count} systems per kind and n, n in {sizes}, "
                                "band5/lower/sympd/dense (Sec. 3, Fig. 3 recipes), 1 rhs",
                    "l2": "inputs larger than L2 from n = 250 (count = 1000)"},
-        "gpu_launches": launches, "clocks": clk.summary(), "tables": tables}), flush=True)
+        "gpu_launches": launches, "clocks": clk.summary(), "tables": tables,
+        "cpu_baseline": ({"kind": "oracle", "cores": 1, "sample": "4 systems per kind and n in {100, 250, 500, 1000}",
+                          "tables": oracle_replica_tables()} if args.cpu_baseline else None)}), flush=True)
 
 
 # --------------------------------------------------------------- serving
