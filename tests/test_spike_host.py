@@ -161,3 +161,17 @@ def test_warp_phases_do_not_depend_on_lane_order(shim, kl, ku):
     rev = run(shim, AB, kl, ku, m, b, warp=2)
     assert fwd[0] == rev[0] == 0
     assert np.array_equal(fwd[1], rev[1]) and np.array_equal(fwd[2], rev[2])
+
+
+def test_dominance_flags_refuse_a_plain_random_band(shim):
+    """A band with N(0,1) entries and no boosted diagonal is dominant
+    neither by rows nor by columns: the route is not taken for it."""
+    n, k = 3000, 4
+    AB = np.random.default_rng(12).standard_normal((2 * k + 1, n))
+    rc, x, xt, far, dom = run(shim, AB, k, k, 300, np.ones(n))
+    assert dom == (0, 0)
+    # the one-sided case: dominance by rows is exactly diag >= sum of the row
+    AB = row_dominant(n, k, k, 5)
+    AB[k, 1234] *= 0.5  # one row loses its dominance
+    rc, x, xt, far, dom = run(shim, AB, k, k, 300, np.ones(n))
+    assert dom[0] == 0
