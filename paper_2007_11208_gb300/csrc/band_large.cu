@@ -897,6 +897,36 @@ int spike_apply(const SpikePlan& pl, double* x, bool tr, cudaStream_t st) {
   return ASOLVE_OK;
 }
 
+// FP64 normwise backward error of X, the maximum over the right-hand sides
+// (||b - Ax||inf / (||A||inf ||x||inf + ||b||inf)), into *out.
+int band_berr(const BandArgs& a, int kl, int ku, double norminf, unsigned long long* colmax, double* out,
+              cudaStream_t st) {
+  const int64_t n = a.n, nrhs = a.nrhs;
+  BCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+  dim3 g((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
+  k_band_berr<<<g, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, a.B, a.X, (int)nrhs, colmax);
+  BCK(cudaGetLastError());
+  unsigned long long hm[3 * 256];
+  BCK(cudaMemcpyAsync(hm, colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  double be = 0.0;
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double rm, xm, bm;
+    memcpy(&rm, &hm[c], 8);
+    memcpy(&xm, &hm[nrhs + c], 8);
+    memcpy(&bm, &hm[2 * nrhs + c], 8);
+    const double den = norminf * xm + bm;
+    const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+    if (!(b1 <= be)) be = b1;
+  }
+  *out = be;
+  return ASOLVE_OK;
+}
+
+// The partitioned route's answer is kept only with a backward error this
+// far below the 1e-13 bar (2^-46); otherwise the GBTRF-order path solves.
+constexpr double kSpkBerrMax = 1.4210854715202004e-14;
+
 // Outcome of one attempt of the partitioned route.
 enum SpikeOutcome { SPK_OK = 0, SPK_NOT_DOMINANT, SPK_NUMERIC, SPK_FAR_TIPS };
 
@@ -1028,6 +1058,7 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   region = reinterpret_cast<char*>(((uintptr_t)region + 255) & ~(uintptr_t)255);
   double rc = NAN;
   bool spiked = false;
+  double spike_be = NAN;
   int64_t spk_m = 0, spk_P = 0;
   // dominant bands: the partitioned route (band_spike.cuh); blocks twice as
   // long on another attempt when the spikes have not decayed across them
@@ -1042,6 +1073,11 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
       BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
       for (int64_t c = 0; c < nrhs; ++c)
         if ((r = spike_apply(sp, a.X + (size_t)c * n, false, st))) return info->status = r;
+      // a posteriori check, whatever the scaling of A: the backward error
+      if ((r = band_berr(a, kl, ku, norminf, colmax, &spike_be, st))) return info->status = r;
+      if (!(spike_be <= kSpkBerrMax)) outcome = SPK_NUMERIC;
+    }
+    if (outcome == SPK_OK) {
       if (!no_rcond) {
         double est = NAN;
         auto apply = [&](double* v, bool tr) { return spike_apply(sp, v, tr, st); };
@@ -1142,22 +1178,10 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   }
   info->rcond = no_rcond ? NAN : rc;
   if (a.flags & ASOLVE_BERR) {
-    BCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
-    dim3 g((unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024), (unsigned)nrhs);
-    k_band_berr<<<g, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, a.B, a.X, (int)nrhs, colmax);
-    BCK(cudaGetLastError());
-    unsigned long long hm[3 * 256];
-    BCK(cudaMemcpyAsync(hm, colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
-    BCK(cudaStreamSynchronize(st));
-    double be = 0.0;
-    for (int64_t c = 0; c < nrhs; ++c) {
-      double rm, xm, bm;
-      memcpy(&rm, &hm[c], 8);
-      memcpy(&xm, &hm[nrhs + c], 8);
-      memcpy(&bm, &hm[2 * nrhs + c], 8);
-      const double den = norminf * xm + bm;
-      const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
-      if (!(b1 <= be)) be = b1;
+    double be = spike_be;
+    if (!spiked) {
+      const int r = band_berr(a, kl, ku, norminf, colmax, &be, st);
+      if (r) return info->status = r;
     }
     info->berr = be;
   } else {
