@@ -163,7 +163,14 @@ def infos_from_tensor(t: torch.Tensor) -> list:
 
 
 class Context:
-    """Owns an asolve_ctx (one CUDA stream, workspaces, captured graphs)."""
+    """Owns an asolve_ctx (one CUDA stream, workspaces, captured graphs).
+
+    The library's stream is non-blocking, so it is not ordered after work
+    queued on torch's streams.  Every call below first makes the context
+    stream wait for torch's current stream (inputs written there are
+    complete before the library reads them) and afterwards makes torch's
+    current stream wait for the context stream (outputs are complete before
+    later torch work reads them).  Both are device-side waits on events."""
 
     def __init__(self, tuning=None, **cfg):
         """tuning: path of a panel-width table written by autotune.py (optional)."""
@@ -172,8 +179,28 @@ class Context:
         rc = lib().asolve_create(C.byref(self._h), C.byref(c))
         if rc != OK:
             raise RuntimeError(f"asolve_create: {strerror(rc)}")
+        self._dev = None
+        if torch.cuda.is_available():
+            d = int(c.device)
+            self._dev = torch.device("cuda", d if d >= 0 else torch.cuda.current_device())
+        self._ext = None
         if tuning is not None:
             self.load_tuning(tuning)
+
+    def _lib_stream(self):
+        if self._ext is None:
+            self._ext = torch.cuda.ExternalStream(self.stream, device=self._dev)
+        return self._ext
+
+    def _order_in(self):
+        """Context stream waits for torch's current stream."""
+        if self._dev is not None:
+            self._lib_stream().wait_stream(torch.cuda.current_stream(self._dev))
+
+    def _order_out(self):
+        """torch's current stream waits for the context stream."""
+        if self._dev is not None:
+            torch.cuda.current_stream(self._dev).wait_stream(self._lib_stream())
 
     def set_panel_widths(self, kind: int, widths) -> int:
         arr = (C.c_int32 * len(widths))(*[int(x) for x in widths])
@@ -190,6 +217,7 @@ class Context:
                     raise RuntimeError(f"asolve_set_panel_widths: {strerror(rc)}")
 
     def close(self):
+        self._ext = None
         if self._h:
             lib().asolve_destroy(self._h)
             self._h = C.c_void_p()
@@ -210,6 +238,7 @@ class Context:
 
     def scan(self, A: torch.Tensor, n: int) -> dict:
         r = ScanResult()
+        self._order_in()
         rc = lib().asolve_scan(self._h, _ptr(A), n, C.byref(r))
         if rc != OK:
             raise RuntimeError(f"asolve_scan: {strerror(rc)}")
@@ -221,7 +250,9 @@ class Context:
         _need(B, n * nrhs, "B")
         _need(X, n * nrhs, "X")
         inf = Info()
+        self._order_in()
         rc = lib().asolve_solve(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(inf))
+        self._order_out()
         return rc, info_dict(inf)
 
     def solve_band(self, AB, ldab: int, kl: int, ku: int, B, n: int, nrhs: int, X, flags: int = 0):
@@ -229,19 +260,27 @@ class Context:
         _need(B, n * nrhs, "B")
         _need(X, n * nrhs, "X")
         inf = Info()
+        self._order_in()
         rc = lib().asolve_solve_band(self._h, _ptr(AB), ldab, kl, ku, _ptr(B), n, nrhs, flags,
                                      _ptr(X), C.byref(inf))
+        self._order_out()
         return rc, info_dict(inf)
 
     def solve_batched(self, count, n, nrhs, a_off, b_off, A, B, X, infos, flags: int = 0) -> int:
-        return lib().asolve_solve_batched(self._h, count, _ptr(n), _ptr(nrhs), _ptr(a_off),
-                                          _ptr(b_off), _ptr(A), _ptr(B), _ptr(X), flags,
-                                          _ptr(infos))
+        self._order_in()
+        rc = lib().asolve_solve_batched(self._h, count, _ptr(n), _ptr(nrhs), _ptr(a_off),
+                                        _ptr(b_off), _ptr(A), _ptr(B), _ptr(X), flags,
+                                        _ptr(infos))
+        self._order_out()
+        return rc
 
     def solve_batched_ptrs(self, count, n, nrhs, A_ptrs, B_ptrs, X_ptrs, infos, flags: int = 0) -> int:
         """n, nrhs: int64 device tensors; *_ptrs: int64 device tensors of addresses."""
-        return lib().asolve_solve_batched_ptrs(self._h, count, _ptr(n), _ptr(nrhs), _ptr(A_ptrs),
-                                               _ptr(B_ptrs), _ptr(X_ptrs), flags, _ptr(infos))
+        self._order_in()
+        rc = lib().asolve_solve_batched_ptrs(self._h, count, _ptr(n), _ptr(nrhs), _ptr(A_ptrs),
+                                             _ptr(B_ptrs), _ptr(X_ptrs), flags, _ptr(infos))
+        self._order_out()
+        return rc
 
     def submit(self, A, B, n: int, nrhs: int, X, flags: int = 0):
         """Queue one request; returns (rc, ticket).  The buffers must outlive it."""
@@ -249,6 +288,10 @@ class Context:
         _need(B, n * nrhs, "B")
         _need(X, n * nrhs, "X")
         t = C.c_uint64(0)
+        # the server's lanes run on streams of their own: inputs written on
+        # torch's current stream must be complete before they are queued
+        if self._dev is not None and not (flags & HOST_BUFFERS):
+            torch.cuda.current_stream(self._dev).synchronize()
         rc = lib().asolve_submit(self._h, _ptr(A), _ptr(B), n, nrhs, flags, _ptr(X), C.byref(t))
         return rc, t.value
 

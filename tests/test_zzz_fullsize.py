@@ -87,6 +87,8 @@ def test_large_configuration_full_size(orc, kind, n):
     assert info["route"] == (asolve.ROUTE_CHOL if kind == "spd" else asolve.ROUTE_LU), info
     assert info["berr"] <= BERR, info
     A = M.cpu().numpy().T
+    sr = orc.scan(A)  # the oracle's scan of the bytes the GPU read (Sec. 2.1-2.3, Fig. 4)
+    assert (info["cls"], info["kl"], info["ku"]) == (sr["cls"], sr["kl"], sr["ku"]), (info, sr)
     x = X.cpu().numpy().reshape(n, 1)
     b = B.cpu().numpy().reshape(n, 1)
     x_true = xt.cpu().numpy().reshape(n, 1)
