@@ -7,9 +7,46 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "asolve.h"
 
 namespace asv {
+
+// Kernel attributes such as a raised dynamic shared memory limit belong to
+// one device.  PerDeviceOnce runs a setup step once per device, from any
+// host thread: the first caller on a device runs it under a mutex, later
+// callers only read the device's flag.  A failed setup is tried again by
+// the next call; devices beyond the table run it on every call.
+struct PerDeviceOnce {
+  static constexpr int kMaxDevices = 64;
+  std::atomic<int> done[kMaxDevices];
+  std::mutex mu;
+  template <class F>
+  cudaError_t run(F&& setup) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return setup();
+    if (done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    e = setup();
+    if (e == cudaSuccess) done[dev].store(1, std::memory_order_release);
+    return e;
+  }
+};
+
+// Raise one kernel's dynamic shared memory limit on the current device
+// (once per device and call site).
+#define ASV_SMEM_LIMIT_ONCE(kernel, bytes)                                                      \
+  ([&]() -> cudaError_t {                                                                      \
+    static ::asv::PerDeviceOnce once_;                                                         \
+    return once_.run([&]() {                                                                   \
+      return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes)); \
+    });                                                                                        \
+  }())
 
 constexpr int kWarp = 32;
 constexpr int kBatchNMax = 1024;   // largest n handled by the per-CTA batched path

@@ -669,12 +669,7 @@ int sw_run_wm(const SweepPlan& pl, int ws, const double* xin, double* xout, bool
   const unsigned g = (unsigned)((c.P + 127) / 128);
   k_sw_part<KIND, WM><<<g, 128, 0, st>>>(c, ws, xin, pl.tv);
   const size_t sm = sw_scan_smem(ws);
-  static bool attr = false;
-  if (!attr) {
-    BCK(cudaFuncSetAttribute(k_sw_scan<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sw_scan_smem(kSwMaxWs)));
-    attr = true;
-  }
+  BCK(ASV_SMEM_LIMIT_ONCE(k_sw_scan<KIND>, sw_scan_smem(kSwMaxWs)));
   k_sw_scan<KIND><<<1, kSwScanThreads, sm, st>>>(c, ws, xin, pl.T[KIND], pl.tv, pl.Ws);
   k_sw_out<KIND, WM><<<g, 128, 0, st>>>(c, ws, xin, pl.Ws, xout);
   BCK(cudaGetLastError());
@@ -1100,11 +1095,7 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
     const size_t wsm = sizeof(double) * (size_t)(kv + 1 + kD) * ldf;
     const int R = window_r(kv);
     if (wsm <= kWinSmemMax) {
-      static bool attr = false;
-      if (!attr) {
-        BCK(cudaFuncSetAttribute(k_band_lu_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmemMax));
-        attr = true;
-      }
+      BCK(ASV_SMEM_LIMIT_ONCE(k_band_lu_win, kWinSmemMax));
       k_band_lu_win<<<1, 32, wsm, st>>>(F, ldf, (int)n, kl, ku, piv, dint);
     } else {
       k_band_lu_glob<<<1, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, dint);

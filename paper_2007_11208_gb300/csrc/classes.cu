@@ -924,20 +924,21 @@ size_t dense_slot_bytes(int nmax) {
   return ((svd > dense ? svd : dense) + 4095) & ~(size_t)4095;
 }
 
+// Shared memory limits of the class kernels on the current device (once per
+// device; contexts on several devices each call it).
 cudaError_t set_class_attrs() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e;
-  e = cudaFuncSetAttribute(k_chol_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lu_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_tri_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_band_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kWarps * kBandRingBytes);
-  if (e != cudaSuccess) return e;
-  done = true;
-  return cudaSuccess;
+  static PerDeviceOnce once;
+  return once.run([]() {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_chol_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_lu_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_tri_class, cudaFuncAttributeMaxDynamicSharedMemorySize, kDenseSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_band_class, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kWarps * kBandRingBytes);
+  });
 }
 
 cudaError_t launch_route(const BatchDesc* d, cudaStream_t st) {

@@ -449,12 +449,8 @@ template <bool TB, bool LO, int OP>
 static cudaError_t launch_gemm_tc16_t(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M,
                                       int N, int K, int* err, cudaStream_t st) {
   const int smem = 4 * kTileBytes;  // as k_gemm_tc: at most 3 CTAs (384 TMEM columns) per SM
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc16<TB, LO, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ASV_SMEM_LIMIT_ONCE((k_gemm_tc16<TB, LO, OP>), smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN);
   k_gemm_tc16<TB, LO, OP><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, err);
   return cudaGetLastError();
@@ -475,13 +471,8 @@ static cudaError_t launch_gemm_tc_t(float* C, int ldc, const float* A, int lda, 
   // always 64 KB: at most 3 CTAs per SM, i.e. at most 384 of the 512
   // tensor-memory columns, so an allocation never waits on another CTA
   const int smem = 4 * kTileBytes;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_gemm_tc<TB, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kTileBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ASV_SMEM_LIMIT_ONCE((k_gemm_tc<TB, LO>), smem);
+  if (e != cudaSuccess) return e;
   dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN);
   k_gemm_tc<TB, LO><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, passes, err);
   return cudaGetLastError();

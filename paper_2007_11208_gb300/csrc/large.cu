@@ -1135,30 +1135,41 @@ cudaError_t gemm_update<double>(double* C, int ldc, const double* A, int lda, co
   return cudaGetLastError();
 }
 
+// Shared memory limits of the large-path kernels on the current device.
 template <typename T>
-int set_large_attrs() {
-  static bool done = false;
-  if (done) return ASOLVE_OK;
-  LCK(cudaFuncSetAttribute(k_trsm_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
-  LCK(cudaFuncSetAttribute(k_trsm_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<double>()));
-  LCK(cudaFuncSetAttribute(k_gemm_dmma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
-  LCK(cudaFuncSetAttribute(k_gemm_dmma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
-  LCK(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
-  LCK(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+cudaError_t set_large_attrs_dev() {
+#define SA(x)                                  \
+  do {                                         \
+    const cudaError_t e_ = (x);                \
+    if (e_ != cudaSuccess) return e_;          \
+  } while (0)
+  SA(cudaFuncSetAttribute(k_trsm_sub<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>()));
+  SA(cudaFuncSetAttribute(k_trsm_rhs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<double>()));
+  SA(cudaFuncSetAttribute(k_gemm_dmma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  SA(cudaFuncSetAttribute(k_gemm_dmma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  SA(cudaFuncSetAttribute(k_gemm_dmma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
+  SA(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   // the panel kernel also has a little static shared memory
   if constexpr (sizeof(T) == 4) {
-    LCK(cudaFuncSetAttribute(k_lu_panel32, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
-    LCK(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagInvSmem));
+    SA(cudaFuncSetAttribute(k_lu_panel32, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+    SA(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagInvSmem));
   }
   else
-    LCK(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
-  LCK(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SA(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+  SA(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)wave_smem<T, float>()));
-  LCK(cudaFuncSetAttribute(k_trsv_wave<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  SA(cudaFuncSetAttribute(k_trsv_wave<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)wave_smem<T, double>()));
-  LCK(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-  done = true;
-  return ASOLVE_OK;
+  SA(cudaFuncSetAttribute(k_chol_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+  return cudaSuccess;
+#undef SA
+}
+
+// once per device and precision, from any host thread
+template <typename T>
+int set_large_attrs() {
+  static PerDeviceOnce once;
+  return once.run(set_large_attrs_dev<T>) == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
 }
 
 // Blocked Cholesky of the working matrix; returns 0 or (failing column + 1).

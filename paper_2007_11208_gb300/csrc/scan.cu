@@ -549,13 +549,8 @@ size_t scan_slot_bytes(int nmax) {
 namespace asv {
 cudaError_t launch_scan_batched(const BatchDesc* d, int grid, cudaStream_t st) {
   size_t sm = scan_batched_smem(kBatchNMax);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_scan_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = ASV_SMEM_LIMIT_ONCE(k_scan_batched, sm);
+  if (e != cudaSuccess) return e;
   k_scan_batched<<<grid, kScanThreads, sm, st>>>(d);
   return cudaGetLastError();
 }
@@ -584,12 +579,8 @@ cudaError_t launch_scan_large(const double* A, int64_t n, const double* B, int64
   if (g < 1) g = 1;
   k_scan_large_diag<<<g, kScanThreads, 0, st>>>(A, n, diag, state);
   size_t sm = scan_large_smem();
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k_scan_large_pairs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  e = ASV_SMEM_LIMIT_ONCE(k_scan_large_pairs, sm);
+  if (e != cudaSuccess) return e;
   int64_t npairs = (int64_t)T * (T + 1) / 2;
   int64_t grid = (npairs + kScanWarps - 1) / kScanWarps;
   int64_t cap = (int64_t)num_sms * 3;
