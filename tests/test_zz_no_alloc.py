@@ -5,7 +5,9 @@ a fixed array inside the library.  This file is collected last on purpose:
 a failure here leaves every other test already run.  The test calls the
 entry point through the C ABI twice in a row (the second call reuses the
 shared array left over by the first) and checks both results against the
-existing, context-owning asolve_scan.
+existing, context-owning asolve_scan and against the oracle's scan of the
+same matrix (class, kl/ku and flags bit-exact, norms within the scan's
+stated accuracy), up to n = 2048, the entry point's limit.
 """
 import ctypes as C
 
@@ -29,10 +31,13 @@ def _matrices():
     for d in (-3, -1, 0, 2, 5):
         band += np.diag(rng.standard_normal(n2 - abs(d)), d)
     general = rng.standard_normal((1000, 1000))
-    return [sympd, band, general]
+    G2 = rng.standard_normal((n2, n2))
+    S2 = G2.T @ G2 / n2 + np.eye(n2)
+    sympd2 = np.tril(S2) + np.tril(S2, -1).T
+    return [sympd, band, general, sympd2]
 
 
-def test_noalloc_scan_matches_asolve_scan():
+def test_noalloc_scan_matches_asolve_scan(orc):
     from paper_2007_11208_gb300 import asolve, build
     build.build()
     L = asolve.lib()
@@ -42,6 +47,9 @@ def test_noalloc_scan_matches_asolve_scan():
         n = A.shape[0]
         dA = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
         ref = ctx.scan(dA, n)
+        oref = orc.scan(A)
+        for k in ("kl", "ku", "lower", "upper", "sympd", "banded", "nonfinite", "cls"):
+            assert int(ref[k]) == int(oref[k]), (n, k, ref[k], oref[k])
         for call in range(2):  # two calls in a row on the shared workspace
             out.zero_()
             rc = L.asolve_scan_noalloc(C.c_void_p(dA.data_ptr()), n, C.c_void_p(out.data_ptr()), None)
