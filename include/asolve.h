@@ -127,7 +127,8 @@ typedef struct {           /* 64 bytes, one per system */
                               bit 1: refinement stalled, bit 2: FP32 Cholesky failed,
                               bit 3: factorisation reused from an earlier resident request,
                               bit 4: band system solved by the partitioned route for
-                              diagonally dominant bands (environment ASOLVE_BAND_SPIKE=1) */
+                              diagonally dominant bands (the default for n >= 4096;
+                              environment ASOLVE_BAND_SPIKE=0 turns it off) */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */
@@ -307,6 +308,24 @@ int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const fl
  * Buckets past `count` revert to the built-in rule.  Applies to calls made
  * after it returns.  Errors: E_INVALID. */
 int asolve_set_panel_widths(asolve_ctx* ctx, int kind, const int32_t* nb, int count);
+
+/* Issue-rate probe of one arithmetic pipe on the current device (the paper
+ * has no counterpart: it measures the roofline denominators of this
+ * implementation's FP32-factor and FP64-refinement kernels, which no copy
+ * or library-GEMM measurement bounds).  pipe: ASOLVE_PIPE_FFMA (FP32 fused
+ * multiply-add), ASOLVE_PIPE_DFMA (FP64 fused multiply-add) or
+ * ASOLVE_PIPE_DMMA (the FP64 tensor instruction mma.sync m8n8k4).  Runs a
+ * grid of 8 CTAs x 256 threads per SM, each thread (each warp for DMMA)
+ * with 8 independent accumulator chains, `iters` rounds of 16 FMAs (4 DMMA)
+ * per chain, after a shorter warm-up launch, and returns the rate in
+ * *tflops (2 flops per FMA, 512 per m8n8k4) and the timed launch's duration
+ * in *ms (may be NULL), measured with CUDA events on the legacy default
+ * stream.  Allocates and frees a small device buffer.  Errors: E_INVALID
+ * (unknown pipe, iters < 1, tflops NULL), E_NOMEM, E_CUDA. */
+#define ASOLVE_PIPE_FFMA  1
+#define ASOLVE_PIPE_DFMA  2
+#define ASOLVE_PIPE_DMMA  3
+int asolve_pipe_peak(int pipe, int iters, double* tflops, double* ms);
 
 /* Per-kernel timing with CUDA events on the context stream (off by default). */
 int asolve_set_profiling(asolve_ctx* ctx, int on);

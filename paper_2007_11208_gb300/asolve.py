@@ -78,7 +78,8 @@ EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve
            "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
            "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc",
            "asolve_gemm_sub", "asolve_solve_batched_ptrs", "asolve_submit", "asolve_poll",
-           "asolve_get_serve_stats", "asolve_set_panel_widths")
+           "asolve_get_serve_stats", "asolve_set_panel_widths", "asolve_pipe_peak")
+PIPE_FFMA, PIPE_DFMA, PIPE_DMMA = 1, 2, 3
 
 
 def lib():
@@ -113,6 +114,7 @@ def lib():
     L.asolve_poll.argtypes = [vp, C.c_uint64, i64, P(Info), P(C.c_double)]
     L.asolve_get_serve_stats.argtypes = [vp, P(ServeStats)]
     L.asolve_set_panel_widths.argtypes = [vp, i32, vp, i32]
+    L.asolve_pipe_peak.argtypes = [i32, i32, P(C.c_double), P(C.c_double)]
     for f in EXPORTS:
         if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
             getattr(L, f).restype = i32
@@ -320,3 +322,12 @@ class Context:
         p = Profile()
         lib().asolve_get_profile(self._h, C.byref(p))
         return {p.k[i].name.decode(): (p.k[i].launches, p.k[i].total_ms) for i in range(p.count)}
+
+
+def pipe_peak(pipe: int, iters: int = 4096):
+    """(TFLOP/s, ms) of one arithmetic pipe's issue-rate probe on the current device."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    rc = lib().asolve_pipe_peak(pipe, iters, C.byref(tf), C.byref(ms))
+    if rc != OK:
+        raise RuntimeError(f"asolve_pipe_peak: {strerror(rc)}")
+    return tf.value, ms.value
