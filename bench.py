@@ -650,8 +650,8 @@ def band_workload(args):
     sum, nrhs right-hand sides; time of one asolve_solve_band call (scan of
     the band, GBTRF-equivalent factorisation, solve, rcond estimate,
     backward error) with CUDA events."""
-    if args.band_spike:  # read by the library at its first band solve
-        os.environ["ASOLVE_BAND_SPIKE"] = "1"
+    if args.band_gbtrf_only:  # read by the library at its first band solve
+        os.environ["ASOLVE_BAND_SPIKE"] = "0"
     from paper_2007_11208_gb300 import asolve, build, synth
     build.build()
     torch.cuda.set_device(0)
@@ -713,7 +713,7 @@ def band_workload(args):
         "steps": args.steps, "warmup": 1, "ms_per_step": head["ms"], "higher_is_better": True,
         "scaling": "replicas only", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"band: n={n}, kl=ku in {ks}, nrhs in {nrhs_list}, diagonally dominant, "
-                               "band storage" + (", partitioned route enabled" if args.band_spike else ""),
+                               "band storage" + (", partitioned route off" if args.band_gbtrf_only else ""),
                    "l2": "inputs larger than L2"},
         "cpu_baseline": ({"value": 1000.0 / cpu_ms[ks[0]], "unit": "solves/s", "cores": 1, "kind": "oracle",
                           "sample": "one solve of the same system per k, one right-hand side, one host core",
@@ -1067,8 +1067,8 @@ def main():
                     help="systems per GPU (smaller values are for profiling runs only)")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "large", "serve", "plain", "band", "replica"])
-    ap.add_argument("--band-spike", action="store_true",
-                    help="band: enable the partitioned route for dominant bands (ASOLVE_BAND_SPIKE=1)")
+    ap.add_argument("--band-gbtrf-only", action="store_true",
+                    help="band: turn the partitioned route for dominant bands off (ASOLVE_BAND_SPIKE=0)")
     ap.add_argument("--replica-sizes", default="100,250,500,1000")
     ap.add_argument("--replica-count", type=int, default=1000)
     ap.add_argument("--replica-prec", default="fp64", choices=["fp64", "mixed"])

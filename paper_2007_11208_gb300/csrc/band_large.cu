@@ -24,9 +24,9 @@
 // routines that work on global memory directly (band_warp.cuh).  Scan,
 // packing and the FP64 backward error are ordinary data-parallel kernels.
 //
-// With ASOLVE_BAND_SPIKE=1 in the environment, long systems (n >= 4096)
-// that are diagonally dominant by rows or by columns take a partitioned
-// route instead (band_spike.cuh, k_spk_*): blocks factored in parallel
+// Long systems (n >= 4096) that are diagonally dominant by rows or by
+// columns take a partitioned route instead (unless ASOLVE_BAND_SPIKE=0 is
+// set in the environment) (band_spike.cuh, k_spk_*): blocks factored in parallel
 // without pivoting, one small system per block boundary, and solves with A
 // and A^T in three block-parallel steps; a zero pivot, a singular boundary
 // system or spikes that have not decayed across a block send the system
@@ -715,8 +715,8 @@ double rcond_from_est(double anorm, double est) {
 // ------------------------------------------- partitioned route (dominant)
 // Long band systems that are diagonally dominant by rows or by columns can
 // be solved block-parallel without pivoting (band_spike.cuh).  The route is
-// taken only when the environment variable ASOLVE_BAND_SPIKE is 1; without
-// it every band system keeps the GBTRF-order path below.
+// on by default; the environment variable ASOLVE_BAND_SPIKE=0 turns it off,
+// and every band system then keeps the GBTRF-order path below.
 constexpr int64_t kSpkMinN = 4096;      // shorter systems: the one-warp path
 constexpr int64_t kSpkBlocks = 2432;    // target number of blocks (16 per SM)
 constexpr double kSpkFarTol = 8.67e-19; // 2^-60: far spike tips dropped below this
@@ -726,7 +726,7 @@ bool spike_enabled() {
   static int on = -1;
   if (on < 0) {
     const char* e = getenv("ASOLVE_BAND_SPIKE");
-    on = (e && e[0] == '1' && e[1] == 0) ? 1 : 0;
+    on = (e && e[0] == '0' && e[1] == 0) ? 0 : 1;
   }
   return on == 1;
 }

@@ -96,3 +96,50 @@ def test_large_configuration_full_size(orc, kind, n):
     assert berr.max() <= BERR, berr
     assert np.abs(x - x_true).max() / np.abs(x_true).max() <= EPS * n * (n * kappa)
     ctx.close()
+
+
+@pytest.mark.parametrize("k", [2, 8, 32])
+def test_band_configuration_full_size(orc, k):
+    """The band configuration exactly as bench.py times it (n = 10^6 in band
+    storage, kl = ku = k, the bench's seed, diagonally dominant, default
+    route): class, route and bandwidths equal to the oracle's band driver,
+    X within the forward-error bound of the oracle's X (kappa_inf estimated
+    from the oracle's rcond, times n), rcond within 1e-5 relative, backward
+    error <= 1e-13 by the oracle's compensated residual over the band."""
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    n = 1_000_000
+    g = synth.gen(1000 + k, dev)
+    AB = synth.band_storage_dd(n, k, k, g, device=dev)   # row j = column j of the band layout
+    Bm = synth.rhs(n, 1, g, dev)
+    X = torch.zeros_like(Bm)
+    ctx = asolve.Context()
+    rc, info = ctx.solve_band(AB, 2 * k + 1, k, k, Bm, n, 1, X, asolve.BERR)
+    torch.cuda.synchronize()
+    ABh = np.asfortranarray(AB.cpu().numpy().T)         # LAPACK layout (2k+1, n)
+    bh = Bm.cpu().numpy().reshape(n, 1)
+    Xo, io = orc.solve_band(ABh, k, k, bh)
+    assert rc == io["status"] == 0, (rc, info, io)
+    assert (info["cls"], info["route"], info["kl"], info["ku"]) == \
+        (io["cls"], io["route"], io["kl"], io["ku"]), (info, io)
+    assert info["detail"] & 16, info                      # the partitioned route took it
+    x = X.cpu().numpy().reshape(n, 1)
+    kinf = n / io["rcond"]                                # kappa_inf <= n kappa_1
+    assert np.abs(x - Xo).max() / np.abs(Xo).max() <= EPS * n * kinf
+    assert abs(info["rcond"] - io["rcond"]) <= 1e-5 * io["rcond"], (info["rcond"], io["rcond"])
+    assert info["berr"] <= BERR, info
+    # the oracle's own backward error of the GPU's X, from the band
+    rows = np.zeros(n)
+    absrow = np.zeros(n)
+    for r in range(2 * k + 1):
+        j = np.arange(n)
+        i = r - k + j
+        ok = (i >= 0) & (i < n)
+        v = ABh[r, j[ok]] * x[j[ok], 0]
+        np.add.at(rows, i[ok], v)
+        np.add.at(absrow, i[ok], np.abs(ABh[r, j[ok]]))
+    resid = np.abs(bh[:, 0] - rows).max()
+    berr = resid / (absrow.max() * np.abs(x).max() + np.abs(bh).max())
+    assert berr <= BERR, berr
+    ctx.close()
