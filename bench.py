@@ -62,11 +62,13 @@ METRIC = "solves/s at backward err <=1e-13 (batched adaptive solve)"
 UNIT = "solves/s"
 WORKLOAD = "batched-10000: n~U[16,512], nrhs~U[1,8], mix 40% general/25% spd/15% banded/15% tri/5% ill"
 BERR_BAR = 1e-13
-# arithmetic peaks of one GB300 (FP32 from the unit counts and the maximum
-# SM clock; the FP64 rates measured with a microbenchmark on this machine)
-PEAK_FP32 = 152 * 128 * 2 * 2.07e9
-PEAK_DFMA = 1.0e12
-PEAK_DMMA = 4.1e12
+# arithmetic peaks of one GB300: measured by the library's pipe probes
+# (paper_2007_11208_gb300/peaks.py -> pipe_peaks.json); these defaults are
+# that file's values, used only if it is missing
+PIPE_PEAKS = os.path.join(ROOT, "paper_2007_11208_gb300", "pipe_peaks.json")
+PEAK_FP32 = 78.46e12
+PEAK_DFMA = 1.254e12
+PEAK_DMMA = 1.095e12
 COUNT = 10000  # systems per GPU per step (--count overrides, for small profiling runs)
 # dram__bytes_read.sum + dram__bytes_write.sum of k_lu_class on the
 # 1,000-system batch (3.393513 GB + 1.088180 GB)
@@ -178,36 +180,63 @@ def verified_count(infos_list):
     return ok, hist
 
 
+def pipe_peaks():
+    """FP32 FMA, FP64 FMA and FP64 mma.sync peaks (FLOP/s) and their source."""
+    if os.path.exists(PIPE_PEAKS):
+        d = json.load(open(PIPE_PEAKS))
+        return (d["ffma_tflops"] * 1e12, d["dfma_tflops"] * 1e12, d["dmma_tflops"] * 1e12,
+                "measured (pipe_peaks.json: asolve_pipe_peak probes)")
+    return PEAK_FP32, PEAK_DFMA, PEAK_DMMA, "measured (defaults copied from pipe_peaks.json)"
+
+
+# Triangular solves the 1-norm estimate takes per system (Hager/Higham:
+# x = inv(A) e/n, a transposed solve, then usually one more pair, and the
+# final alternating-sign vector): counted as 5 solves of 2 n^2 flops.
+EST_SOLVES = 5
+
+
 def flops_model(specs, infos_list):
-    """Algorithmic work of the dominant class kernels, per step, and the
-    minimum time the kernels' arithmetic needs on the pipes it runs on."""
-    lu32 = chol32 = lu64 = chol64 = res64 = 0.0
-    t_min = {"k_lu_class": 0.0, "k_chol_class": 0.0}
+    """Algorithmic arithmetic of the dense class kernels per step, split by
+    the pipe it runs on, and the time floor it sets.
+
+    Mixed route: FP32 factorisation (LU 2n^3/3, Cholesky n^3/3), FP32
+    solves (2 n^2 nrhs per refinement step, the estimate's solves) and FP64
+    residuals (2 n^2 nrhs per refinement step plus the converged check).
+    FP64 route (rcond gate or stall): FP64 factorisation, solve, estimate
+    and the backward-error residual.  The FP64 tensor instruction runs at
+    the DFMA rate on this GPU (measured), so every FP64 flop is charged at
+    the larger of the two measured FP64 rates; the floor of a kernel is the
+    larger of its FP32 and FP64 times (the pipes run concurrently)."""
+    p32, pdfma, pdmma, src = pipe_peaks()
+    p64 = max(pdfma, pdmma)
+    out = {"lu32": 0.0, "chol32": 0.0, "lu64": 0.0, "chol64": 0.0, "res64": 0.0}
+    per = {"k_lu_class": [0.0, 0.0], "k_chol_class": [0.0, 0.0]}  # [fp32, fp64] flops
     for (kind, n, r, *_), inf in zip(specs, infos_list):
         route, prec, it = inf["route"], inf["precision"], inf["ir_iters"]
         kern = "k_lu_class" if route in (6, 5) else ("k_chol_class" if route == 4 else None)
         if kern is None:
             continue
         f = (2.0 / 3.0 if kern == "k_lu_class" else 1.0 / 3.0) * n ** 3
+        solves = 2.0 * n * n * (r * (it + 1) + EST_SOLVES)
         if prec == 1:
             res = 2.0 * n * n * r * (it + 1)
-            res64 += res
-            # FP64 residual: DFMA for one or two right-hand sides, else
-            # mma.sync f64 with the columns padded to 8
-            res_rate = PEAK_DFMA if r <= 2 else PEAK_DMMA * r / 8.0
-            t_min[kern] += f / PEAK_FP32 + res / res_rate
-            if kern == "k_lu_class":
-                lu32 += f
-            else:
-                chol32 += f
+            out["res64"] += res
+            out["lu32" if kern == "k_lu_class" else "chol32"] += f
+            per[kern][0] += f + solves
+            per[kern][1] += res
         else:
-            t_min[kern] += f / PEAK_DMMA
-            if kern == "k_lu_class":
-                lu64 += f
-            else:
-                chol64 += f
-    return dict(lu32=lu32, chol32=chol32, lu64=lu64, chol64=chol64, res64=res64,
-                t_min_ms={k: v * 1e3 for k, v in t_min.items()})
+            # a rejected FP32 attempt (gate) was paid for as well
+            if inf["detail"] & 3:
+                per[kern][0] += f + 2.0 * n * n * EST_SOLVES
+            out["lu64" if kern == "k_lu_class" else "chol64"] += f
+            res = 2.0 * n * n * r
+            out["res64"] += res
+            per[kern][1] += f + 2.0 * n * n * (r + EST_SOLVES) + res
+    t_min = {k: max(v[0] / p32, v[1] / p64) * 1e3 for k, v in per.items()}
+    out.update(t_min_ms=t_min, flops_fp32={k: v[0] for k, v in per.items()},
+               flops_fp64={k: v[1] for k, v in per.items()},
+               peaks_tflops={"fp32": p32 / 1e12, "fp64": p64 / 1e12}, peaks_src=src)
+    return out
 
 
 def load_peaks():
@@ -225,8 +254,8 @@ def large_case_roofline(kind, prec, n, nrhs, ms, peaks):
 
     Flops: LU 2n^3/3, Cholesky n^3/3 (plus 2 n^2 nrhs for the two
     triangular solves), triangular route n^2 nrhs.  Peaks: the FP64 path and
-    the triangular route at the mma.sync f64 rate measured on this GPU
-    (PEAK_DMMA); the mixed path's trailing updates at the 3xTF32 rate
+    the triangular route at the FP64 pipe rate measured on this GPU (the
+    larger of the DFMA and mma.sync f64 probes); the mixed path's trailing updates at the 3xTF32 rate
     (three TF32 products, TF32 = half the measured bf16 burst rate); the
     BF16 / FP16 updates at the measured bf16 burst rate."""
     flops = {"general": 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs,
@@ -234,7 +263,8 @@ def large_case_roofline(kind, prec, n, nrhs, ms, peaks):
              "lower": float(n) * n * nrhs}[kind]
     bf16 = peaks["bf16_tflops"] * 1e12
     if kind == "lower" or prec == "fp64":
-        peak, unit_src = PEAK_DMMA, "FP64 mma.sync (measured 4.1 TFLOP/s)"
+        p32, pdfma, pdmma, src = pipe_peaks()
+        peak, unit_src = max(pdfma, pdmma), "FP64 pipe, " + src
     elif prec == "mixed":
         peak, unit_src = bf16 / 6.0, f"3xTF32 = bf16 {peaks['src']} / 6"
     else:
@@ -430,7 +460,6 @@ def ours(args):
         result["kernel_ms"] = per
         dom = max(per, key=per.get)
         fm = flops_model(specs, inf_mixed)
-        fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         if dom == "k_scan_batched":
             byt = algorithmic_bytes_scan(specs)
             ach = byt / (per[dom] / 1e3) / 1e9
@@ -438,28 +467,30 @@ def ours(args):
                                   "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
                                   "peak_src": peaks["src"]}
         else:
-            key32 = "lu32" if dom == "k_lu_class" else "chol32"
-            fl = fm[key32]
-            ach = fl / (per[dom] / 1e3) / 1e12
-            t_min = fm["t_min_ms"].get(dom, 0.0)
+            # the class kernels are bound by their arithmetic: the FP64 pipe
+            # (residuals, FP64 factorisations) is the scarcer of the two
+            f64 = fm["flops_fp64"].get(dom, 0.0)
+            f32 = fm["flops_fp32"].get(dom, 0.0)
+            p64 = fm["peaks_tflops"]["fp64"]
+            p32 = fm["peaks_tflops"]["fp32"]
+            sec = per[dom] / 1e3
+            ach = f64 / sec / 1e12
             traffic = None
             if dom == "k_lu_class" and COUNT > 0:
                 # DRAM bytes (read + write) of one k_lu_class launch from an ncu
-                # capture of a 1,000-system batch of the same generator
-                # (profiles/batched-1000_k_lu_class_k_chol_class_full.md),
+                # capture of a 1,000-system batch of the same generator,
                 # scaled by the number of systems
                 traffic = LU_CLASS_DRAM_BYTES_1000 * COUNT / 1000.0
-            result["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
-                                  "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": traffic,
+            t_min = fm["t_min_ms"].get(dom, 0.0)
+            result["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": p64,
+                                  "unit": "TFLOP/s", "frac": ach / p64, "traffic": traffic,
                                   "traffic_unit": "bytes per launch",
-                                  "peak_src": "FP32 FMA: 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
-                                  "note": "FP32 factor flops only; the FP64 refinement of the same "
-                                          "kernel is not counted",
-                                  "alu_time_model": {
-                                      "min_ms": t_min, "measured_ms": per[dom], "frac": t_min / per[dom],
-                                      "note": "FP32 factor flops at the FP32 peak + FP64 factor flops at "
-                                              "the mma.sync f64 rate (4.1 TFLOP/s) + FP64 residual flops at "
-                                              "the DFMA (1.0) or mma.sync f64 rate, per system"}}
+                                  "peak_src": "FP64 pipe, " + fm["peaks_src"],
+                                  "fp32": {"flops": f32, "achieved": f32 / sec / 1e12, "peak": p32,
+                                           "frac": f32 / sec / 1e12 / p32},
+                                  "fp64_flops": f64,
+                                  "alu_time_model": {"min_ms": t_min, "measured_ms": per[dom],
+                                                     "frac": t_min / per[dom]}}
         result["flops_model"] = fm
     if rank == 0 and args.cpu_baseline:
         result["cpu_baseline"] = oracle_sample(pk, budget_s=args.cpu_seconds)

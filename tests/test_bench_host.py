@@ -8,13 +8,18 @@ import bench
 PEAKS = {"hbm_gbs": 6783.5, "bf16_tflops": 1917.9, "src": "measured"}
 
 
-def test_fp64_lu_is_alu_bound_at_the_dmma_rate():
+def fp64_peak():
+    _, dfma, dmma, _ = bench.pipe_peaks()
+    return max(dfma, dmma)
+
+
+def test_fp64_lu_is_alu_bound_at_the_fp64_pipe_rate():
     n, ms = 8192, 444.6
     r = bench.large_case_roofline("general", "fp64", n, 1, ms, PEAKS)
     flops = 2.0 / 3.0 * n ** 3 + 2.0 * n * n
     assert r["bound"] == "alu"
     assert r["flops"] == pytest.approx(flops)
-    assert r["floor_ms"] == pytest.approx(flops / bench.PEAK_DMMA * 1e3)
+    assert r["floor_ms"] == pytest.approx(flops / fp64_peak() * 1e3)
     assert r["frac"] == pytest.approx(r["floor_ms"] / ms)
     assert r["achieved_tflops"] / r["peak_tflops"] == pytest.approx(r["frac"])
 
@@ -33,7 +38,7 @@ def test_precision_selects_the_peak():
 def test_triangular_route_is_fp64_whatever_the_precision():
     for prec in ("mixed", "fp64", "bf16"):
         r = bench.large_case_roofline("lower", prec, 16384, 256, 285.8, PEAKS)
-        assert r["peak_tflops"] == pytest.approx(bench.PEAK_DMMA / 1e12)
+        assert r["peak_tflops"] == pytest.approx(fp64_peak() / 1e12)
         assert r["flops"] == pytest.approx(16384.0 ** 2 * 256)
 
 
@@ -109,3 +114,21 @@ def test_oracle_reproduces_the_papers_band_and_triangular_savings(orc):
     for kind in ("band5", "lower"):
         for row in r[kind]:
             assert row["reduction_pct"] > 50.0, (kind, row)
+
+
+def test_flops_model_charges_each_pipe():
+    """Mixed-route systems: FP32 factor + solves on the FP32 pipe, FP64
+    residuals on the FP64 pipe; FP64-route systems: everything FP64."""
+    specs = [("general", 100, 2), ("spd", 64, 1), ("ill", 50, 3)]
+    infos = [dict(route=6, precision=1, ir_iters=1, detail=0),
+             dict(route=4, precision=1, ir_iters=2, detail=0),
+             dict(route=6, precision=0, ir_iters=0, detail=1)]
+    fm = bench.flops_model(specs, infos)
+    e = bench.EST_SOLVES
+    lu32 = 2 / 3 * 100 ** 3 + 2 * 100 ** 2 * (2 * 2 + e) + 2 / 3 * 50 ** 3 + 2 * 50 ** 2 * e
+    lu64 = 2 * 100 ** 2 * 2 * 2 + 2 / 3 * 50 ** 3 + 2 * 50 ** 2 * (3 + e) + 2 * 50 ** 2 * 3
+    assert fm["flops_fp32"]["k_lu_class"] == pytest.approx(lu32)
+    assert fm["flops_fp64"]["k_lu_class"] == pytest.approx(lu64)
+    assert fm["flops_fp64"]["k_chol_class"] == pytest.approx(2 * 64 ** 2 * 1 * 3)
+    p32, p64 = fm["peaks_tflops"]["fp32"] * 1e12, fm["peaks_tflops"]["fp64"] * 1e12
+    assert fm["t_min_ms"]["k_lu_class"] == pytest.approx(max(lu32 / p32, lu64 / p64) * 1e3)
