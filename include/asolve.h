@@ -187,6 +187,13 @@ int asolve_scan(asolve_ctx* ctx, const double* A, int64_t n, asolve_scan_result*
 /* The adaptive solve of one system A X = B (Sec. 2, Fig. 2):
  *   A: n x n, B: n x nrhs, X: n x nrhs (device unless ASOLVE_HOST_BUFFERS);
  *   info: host pointer (may be NULL).  Synchronous.  n = 0 returns OK.
+ * When the routed solver fails or its rcond is below the threshold, X is
+ * the minimum-norm solution through the SVD (Sec. 2.5, status W_APPROX)
+ * for n <= 8192; above that order the SVD fallback is not available (a
+ * dense one-sided Jacobi SVD of a larger matrix is not offered): a failed
+ * solver returns E_SINGULAR with X zeroed, a low rcond W_ILLCOND with the
+ * solver's X, and FORCE_SVD returns E_UNSUPPORTED.  With NO_APPROX the
+ * same two codes are returned at any order.
  * Returns the system's status (the value also stored in info->status). */
 int asolve_solve(asolve_ctx* ctx, const double* A, const double* B, int64_t n,
                  int64_t nrhs, uint32_t flags, double* X, asolve_info* info);
@@ -195,9 +202,8 @@ int asolve_solve(asolve_ctx* ctx, const double* A, const double* B, int64_t n,
  * AB is ldab x n column-major with A(i,j) at AB[(ku+i-j) + j*ldab],
  * ldab >= kl+ku+1, for the declared bandwidths kl, ku.  The system always
  * takes the banded route, with the true bandwidths found inside the band.
- * The SVD fallback is available for n <= 1024 only (it runs on a dense
- * copy); above that a failure returns E_SINGULAR and a low rcond
- * W_ILLCOND.  Synchronous. */
+ * The SVD fallback runs on a dense copy of A, for n <= 8192; above that
+ * a failure returns E_SINGULAR and a low rcond W_ILLCOND.  Synchronous. */
 int asolve_solve_band(asolve_ctx* ctx, const double* AB, int64_t ldab, int64_t kl,
                       int64_t ku, const double* B, int64_t n, int64_t nrhs,
                       uint32_t flags, double* X, asolve_info* info);

@@ -468,7 +468,7 @@ extern "C" int asolve_solve(asolve_ctx* c, const double* A, const double* B, int
     CK(c->large.ensure(wsb));
     LargeArgs la{dA, dB, dX, n, nrhs, flags, c->cfg.precision, c->cfg.rcond_threshold, c->cfg.sympd_tol,
                  c->cfg.band_frac, c->cfg.ir_target_berr, c->cfg.ir_kappa_limit, c->cfg.ir_max_iter,
-                 c->num_sms, st, nullptr};
+                 c->num_sms, st, nullptr, c->cfg.svd_trunc_rel};
     asolve_info li;
     const int rc = large_solve(la, c->large.p, c->large.bytes, &li);
     if (rc < 0 && rc != li.status) {  // an error before the solve produced a status
@@ -584,7 +584,7 @@ extern "C" int asolve_solve_band(asolve_ctx* c, const double* AB, int64_t ldab, 
   int rc = band_solve(ba, c->large.p, c->large.bytes, &li);
   if (rc == ASOLVE_PENDING) {
     // solver failed or rcond below the threshold: the SVD fallback of
-    // Sec. 2.5 on a dense copy (n <= 1024 here)
+    // Sec. 2.5 on a dense copy (n <= kSvdLargeMax here)
     CK(c->bandDense.ensure(sizeof(double) * (size_t)(n * n)));
     int r2 = band_to_dense(dAB, ldab, kl, ku, n, (double*)c->bandDense.p, st);
     if (r2 != ASOLVE_OK) return r2;

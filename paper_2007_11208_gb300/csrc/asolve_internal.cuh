@@ -149,7 +149,13 @@ struct LargeArgs {
   int num_sms;
   cudaStream_t st;
   LargeReuse* reuse;       // optional
+  double svd_trunc_rel;    // SVD fallback cut-off: sigma <= svd_trunc_rel * sigma_max dropped (0: n eps)
 };
+// The SVD fallback for one large system (svd_large.cu), up to this order.
+constexpr int64_t kSvdLargeMax = 8192;
+size_t large_svd_ws_bytes(int64_t n, int64_t nrhs);
+int large_svd(const double* A, int64_t n, const double* B, double* X, int64_t nrhs, double trunc_rel,
+              double* G, void* ws, int64_t* rank, int* sweeps, cudaStream_t st);
 size_t large_ws_bytes(int64_t n, int64_t nrhs);
 int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
 

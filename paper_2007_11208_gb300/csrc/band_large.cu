@@ -995,7 +995,8 @@ size_t band_ws_bytes_declared(int64_t n, int64_t kld, int64_t kud, int64_t nrhs)
 
 // The banded route for one system.  Returns the status (also in info).
 // status ASOLVE_PENDING means: the factor failed or rcond is below the
-// threshold, the SVD fallback is allowed and n <= 1024 -- the caller runs it.
+// threshold, the SVD fallback is allowed and n <= kSvdLargeMax -- the
+// caller runs it on a dense copy.
 int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) {
   cudaStream_t st = a.st;
   const int64_t n = a.n, nrhs = a.nrhs;
@@ -1048,7 +1049,7 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   k_bpack<<<4 * 152, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, F);
   BCK(cudaGetLastError());
   const bool no_rcond = (a.flags & ASOLVE_NO_RCOND) != 0;
-  const bool svd_ok = !(a.flags & ASOLVE_NO_APPROX) && n <= 1024;
+  const bool svd_ok = !(a.flags & ASOLVE_NO_APPROX) && n <= kSvdLargeMax;
   char* region = reinterpret_cast<char*>(exi + ((n + 31) & ~(int64_t)31));
   region = reinterpret_cast<char*>(((uintptr_t)region + 255) & ~(uintptr_t)255);
   double rc = NAN;

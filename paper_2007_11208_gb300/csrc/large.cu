@@ -1259,6 +1259,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += 2 * sizeof(double) * 1024 * (kLB + 4) + 2 * sizeof(double) * kLB + 1024;  // panel buffers (G <= 1024)
   b += scan_large_workspace(n) + 4096;
   b += sizeof(int) * (size_t)(((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR)) + 1024;  // wave flags
+  if (n <= kSvdLargeMax) b += large_svd_ws_bytes(n, nrhs) + 4096;  // SVD fallback (V, sigma, coefficients)
   return b + (1 << 20);
 }
 
@@ -1321,10 +1322,14 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   info->kl = sr.kl;
   info->ku = sr.ku;
   if (sr.flags & (SF_NONFINITE | SF_B_NONFINITE)) return info->status = ASOLVE_E_NONFINITE;
-  if (a.flags & ASOLVE_FORCE_SVD) return info->status = ASOLVE_E_UNSUPPORTED;
+  // the SVD fallback of Sec. 2.5 (dense, one-sided Jacobi) up to kSvdLargeMax
+  const bool svd_allowed = !(a.flags & ASOLVE_NO_APPROX) && n <= kSvdLargeMax;
+  const bool force_svd = (a.flags & ASOLVE_FORCE_SVD) != 0;
+  if (force_svd && n > kSvdLargeMax) return info->status = ASOLVE_E_UNSUPPORTED;
   int cls = (a.flags & ASOLVE_FORCE_LU || reuse_hit) ? ASOLVE_CLS_GENERAL : sr.cls;
   bool band_as_dense = false;
-  if (cls == ASOLVE_CLS_BANDED) {
+  bool band_pending = false;  // the band route asks for the SVD fallback
+  if (cls == ASOLVE_CLS_BANDED && !force_svd) {
     // Sec. 2.1 banded route.  Bandwidths beyond the band kernels' windows run
     // the dense LU below, which makes the same pivot choices (the entries
     // outside the band stay exactly zero), and report the banded route.
@@ -1335,12 +1340,12 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       BandArgs ba{nullptr, 0, 0, 0, a.A, a.B, a.X, n, nrhs, a.flags, a.rcond_threshold, sr.kl, sr.ku,
                   sr.norm1, sr.norminf, st};
       const int brc = band_solve(ba, bws, need, info);
-      // no SVD fallback above n = 1024
-      if (brc == ASOLVE_PENDING) info->status = ASOLVE_E_UNSUPPORTED;
-      return info->status;
+      if (brc != ASOLVE_PENDING) return info->status;
+      band_pending = true;  // solver failed or rcond below the threshold: SVD below
+    } else {
+      band_as_dense = true;
+      cls = ASOLVE_CLS_GENERAL;
     }
-    band_as_dense = true;
-    cls = ASOLVE_CLS_GENERAL;
   }
   // dynamic shared memory limits of every kernel below (the triangular
   // route uses the FP64 kernels even in mixed precision)
@@ -1356,6 +1361,60 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   void* exi = ar.take(sizeof(double) * (size_t)n);
   unsigned long long* colmax = static_cast<unsigned long long*>(ar.take(sizeof(unsigned long long) * 3 * nrhs));
   if (!R || !Pres || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
+  // FP64 normwise backward error of X, the maximum over the columns
+  auto backward_error = [&](double& be) -> int {
+    LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    {
+      const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+      if (rr_) return rr_;
+    }
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+    std::vector<unsigned long long> hm((size_t)3 * nrhs);
+    LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    be = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      double rm, xm, bm;
+      memcpy(&rm, &hm[c], 8);
+      memcpy(&xm, &hm[nrhs + c], 8);
+      memcpy(&bm, &hm[2 * nrhs + c], 8);
+      const double den = sr.norminf * xm + bm;
+      const double b1 = den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+      if (!(b1 <= be)) be = b1;
+    }
+    return ASOLVE_OK;
+  };
+  // Sec. 2.5: the routed solver failed, its rcond is below the threshold,
+  // or FORCE_SVD: X is the minimum-norm solution through the SVD of A.  The
+  // working matrix W (factors no longer needed) becomes the SVD's G; the
+  // route and rcond already in info stay (the primary solver's).
+  auto svd_fallback = [&]() -> int {
+    if (kept) kept->valid = 0;
+    void* vws = ar.take(large_svd_ws_bytes(n, nrhs));
+    if (!vws) return info->status = ASOLVE_E_NOMEM;
+    int64_t rank = 0;
+    int sweeps = 0;
+    const int r2 = large_svd(a.A, n, a.B, a.X, nrhs, a.svd_trunc_rel, static_cast<double*>(Wv), vws, &rank,
+                             &sweeps, st);
+    if (r2) return info->status = r2;
+    info->svd_rank = rank;
+    info->precision = ASOLVE_PREC_FP64;
+    if (a.flags & ASOLVE_BERR) {
+      double be;
+      const int r3 = backward_error(be);
+      if (r3) return info->status = r3;
+      info->berr = be;
+    }
+    LCK(cudaStreamSynchronize(st));
+    return info->status = ASOLVE_W_APPROX;
+  };
+  if (force_svd) {
+    info->route = ASOLVE_ROUTE_SVD;
+    info->precision = ASOLVE_PREC_FP64;
+    return svd_fallback();
+  }
+  if (band_pending) return svd_fallback();
   // ---- triangular route (Sec. 2.2): FP64 substitution on A itself
   if (cls == ASOLVE_CLS_LOWER || cls == ASOLVE_CLS_UPPER) {
     const bool lower = cls == ASOLVE_CLS_LOWER;
@@ -1369,10 +1428,11 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
                             cudaMemcpyDeviceToHost, st));
       LCK(cudaStreamSynchronize(st));
       for (int i = 0; i < n; ++i)
-        if (diag[(size_t)i] == 0.0) {
+        if (diag[(size_t)i] == 0.0) {  // the substitution fails (Sec. 2.2)
+          if (svd_allowed) return svd_fallback();
           LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
-          info->status = (a.flags & ASOLVE_NO_APPROX) ? ASOLVE_E_SINGULAR : ASOLVE_E_UNSUPPORTED;
-          return info->status;
+          LCK(cudaStreamSynchronize(st));
+          return info->status = ASOLVE_E_SINGULAR;
         }
     }
     LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
@@ -1430,6 +1490,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     }
     if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
     const bool poor = !no_rcond && !(rc_val >= a.rcond_threshold);
+    if (poor && svd_allowed) return svd_fallback();
     info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
     return info->status;
   }
@@ -1585,6 +1646,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     LCK(cudaStreamSynchronize(st));
     if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
     const bool poor = !no_rcond && !(kept->rcond >= a.rcond_threshold);
+    if (poor && svd_allowed) return svd_fallback();
     return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
   }
   // ---- mixed precision: FP32 factors (trailing updates as 3xTF32, BF16 or
@@ -1669,10 +1731,11 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if ((rc = lu_large<double>(f, n, a.num_sms, &fcol, st))) return rc;
   }
   if (band_as_dense) info->route = ASOLVE_ROUTE_BAND_LU;
-  if (fcol) {
+  if (fcol) {  // the factorisation failed (an exact zero pivot)
+    if (svd_allowed) return svd_fallback();
     LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
     LCK(cudaStreamSynchronize(st));
-    return info->status = ASOLVE_E_SINGULAR;  // the SVD fallback is limited to n <= 1024
+    return info->status = ASOLVE_E_SINGULAR;
   }
   LCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
   if ((rc = apply_large<double, double>(f, lu, n, a.X, nrhs, false, (double*)tmp, st))) return rc;
@@ -1710,6 +1773,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   LCK(cudaStreamSynchronize(st));
   if (wave_failed()) return info->status = ASOLVE_E_TIMEOUT;
   const bool poor = !no_rcond && !(rcv >= a.rcond_threshold);
+  if (poor && svd_allowed) return svd_fallback();
   keep(ASOLVE_PREC_FP64, lu);
   return info->status = poor ? ASOLVE_W_ILLCOND : ASOLVE_OK;
 }

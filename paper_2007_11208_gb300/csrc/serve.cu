@@ -335,7 +335,7 @@ void Server::solve_large(Request& r) {
   if (ok) {
     LargeArgs la{A, B, X, r.n, r.nrhs, r.flags & kSolverFlags, cfg.precision, cfg.rcond_threshold,
                  cfg.sympd_tol, cfg.band_frac, cfg.ir_target_berr, cfg.ir_kappa_limit, cfg.ir_max_iter,
-                 num_sms, stl, resident ? &kept : nullptr};
+                 num_sms, stl, resident ? &kept : nullptr, cfg.svd_trunc_rel};
     rc = large_solve(la, dblk, ws, &info);
     if (rc < 0 && rc != info.status) info.status = rc;
     if (hm && info.status >= 0)
