@@ -27,10 +27,11 @@ _lib = None
 
 CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
 (ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
- ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD) = range(8)
+ ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD, ROUTE_TRIDIAG) = range(9)
 OK, W_APPROX, W_ILLCOND = 0, 1, 2
 E_INVALID, E_NONFINITE, E_SINGULAR = -1, -2, -3
 NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND = 1, 2, 4, 8
+TRIDIAG = 256  # tridiagonal specialisation (opt-in route for kl = ku = 1)
 
 
 class Scan(C.Structure):
@@ -95,6 +96,10 @@ def lib():
                   "or_est_inv_norm1_band", "or_rcond_from"):
             getattr(L, f).restype = d
         L.or_rcond_from.argtypes = [d, d]
+        L.or_gt_factor.argtypes = [pd, pd, pd, pd, pi64, i64]
+        L.or_gt_solve.argtypes = [pd, pd, pd, pd, pi64, i64, pd, i64, i32]
+        L.or_est_inv_norm1_gt.argtypes = [pd, pd, pd, pd, pi64, i64]
+        L.or_est_inv_norm1_gt.restype = d
         L.or_jacobi_svd.argtypes = [pd, pd, pd, i64, i32]
         L.or_svd_solve.argtypes = [pd, i64, pd, i64, d, pd]
         L.or_svd_solve.restype = i64
@@ -220,6 +225,36 @@ def band_lu_solve(F, kl, ku, ipiv, B, trans=False):
                            _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), _p(X),
                            X.shape[1], int(trans))
     return X
+
+
+def gt_factor(dl, d, du):
+    """Tridiagonal LU with partial pivoting (xGTTRF semantics) of the
+    diagonals dl (n-1), d (n), du (n-1).  Returns (dl, d, du, du2, ipiv, info)."""
+    d = np.array(d, dtype=np.float64)
+    n = d.shape[0]
+    dl = np.array(dl, dtype=np.float64).reshape(max(n - 1, 0))
+    du = np.array(du, dtype=np.float64).reshape(max(n - 1, 0))
+    dlp, dup = np.zeros(max(n - 1, 1)), np.zeros(max(n - 1, 1))
+    dlp[:n - 1], dup[:n - 1] = dl, du
+    du2 = np.zeros(max(n - 2, 1))
+    ipiv = np.zeros(max(n, 1), dtype=np.int64)
+    info = lib().or_gt_factor(_p(dlp), _p(d), _p(dup), _p(du2), _pi(ipiv), n)
+    return dlp, d, dup, du2, ipiv[:n], info
+
+
+def gt_solve(fac, B, trans=False):
+    dl, d, du, du2, ipiv, _ = fac
+    n = d.shape[0]
+    X = _f64(np.array(B, dtype=np.float64, ndmin=2).reshape(n, -1)).copy(order="F")
+    lib().or_gt_solve(_p(dl), _p(d), _p(du), _p(du2), _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), n,
+                      _p(X), X.shape[1], int(trans))
+    return X
+
+
+def est_inv_norm1_gt(fac):
+    dl, d, du, du2, ipiv, _ = fac
+    return lib().or_est_inv_norm1_gt(_p(dl), _p(d), _p(du), _p(du2),
+                                     _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), d.shape[0])
 
 
 def norm1(A):

@@ -354,6 +354,84 @@ void or_band_lu_solve(const double* AB, int64_t ldab, int64_t n, int64_t kl, int
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tridiagonal systems, the closing remarks' specialisation of the banded
+ * case: Gaussian elimination with partial pivoting on the three diagonals
+ * (xGTTRF semantics).  At step i only rows i and i+1 hold entries of column
+ * i; they are interchanged when |dl[i]| > |d[i]| (a tie keeps row i, the
+ * first maximum).  An interchange brings the second super-diagonal entry
+ * du2[i] of the new row i.  The multiplier is the entry divided by the
+ * pivot.  Returns 0, or i+1 at the first exact zero pivot d[i]. */
+int or_gt_factor(double* dl, double* d, double* du, double* du2, int64_t* ipiv, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) ipiv[i] = i;
+  for (int64_t i = 0; i + 2 < n; ++i) du2[i] = 0.0;
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    if (fabs(d[i]) >= fabs(dl[i])) { /* no interchange */
+      if (d[i] != 0.0) {
+        double l = dl[i] / d[i];
+        dl[i] = l;
+        d[i + 1] = d[i + 1] - l * du[i];
+      }
+    } else { /* rows i and i+1 interchanged */
+      double l = d[i] / dl[i];
+      d[i] = dl[i];
+      dl[i] = l;
+      double t = du[i];
+      du[i] = d[i + 1];
+      d[i + 1] = t - l * d[i + 1];
+      if (i + 2 < n) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -(l * du[i + 1]);
+      }
+      ipiv[i] = i + 1;
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (d[i] == 0.0) return (int)(i + 1);
+  return 0;
+}
+
+/* Solve with the tridiagonal factors (xGTTRS semantics; trans: A^T x = b). */
+void or_gt_solve(const double* dl, const double* d, const double* du, const double* du2,
+                 const int64_t* ipiv, int64_t n, double* B, int64_t nrhs, int trans) {
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* b = B + (size_t)c * n;
+    if (!trans) {
+      for (int64_t i = 0; i + 1 < n; ++i) { /* L y = P b */
+        if (ipiv[i] == i) {
+          b[i + 1] = b[i + 1] - dl[i] * b[i];
+        } else {
+          double t = b[i];
+          b[i] = b[i + 1];
+          b[i + 1] = t - dl[i] * b[i];
+        }
+      }
+      for (int64_t i = n - 1; i >= 0; --i) { /* U x = y: d, du, du2 */
+        double s = b[i];
+        if (i + 1 < n) s = s - du[i] * b[i + 1];
+        if (i + 2 < n) s = s - du2[i] * b[i + 2];
+        b[i] = s / d[i];
+      }
+    } else {
+      for (int64_t i = 0; i < n; ++i) { /* U^T z = b */
+        double s = b[i];
+        if (i >= 1) s = s - du[i - 1] * b[i - 1];
+        if (i >= 2) s = s - du2[i - 2] * b[i - 2];
+        b[i] = s / d[i];
+      }
+      for (int64_t i = n - 2; i >= 0; --i) { /* L^T then P^T, in reverse */
+        if (ipiv[i] == i) {
+          b[i] = b[i] - dl[i] * b[i + 1];
+        } else {
+          double t = b[i + 1];
+          b[i + 1] = b[i] - dl[i] * t;
+          b[i] = t;
+        }
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* 1-norm estimate of inv(A) (Hager 1984; Higham 1988, the estimator LAPACK's
  * xGECON/xPOCON/xGBCON/xTRCON use).  apply(ctx, x, trans) overwrites x with
  * inv(A) x (trans = 0) or inv(A)^T x (trans = 1). */
@@ -436,6 +514,17 @@ static void apply_tri(const void* c, double* x, int trans) {
 static void apply_band(const void* c, double* x, int trans) {
   const fac_ctx* f = (const fac_ctx*)c;
   or_band_lu_solve(f->F, f->ldab, f->n, f->kl, f->ku, f->ipiv, x, 1, trans);
+}
+
+typedef struct { const double *dl, *d, *du, *du2; const int64_t* ipiv; int64_t n; } gt_ctx;
+static void apply_gt(const void* c, double* x, int trans) {
+  const gt_ctx* f = (const gt_ctx*)c;
+  or_gt_solve(f->dl, f->d, f->du, f->du2, f->ipiv, f->n, x, 1, trans);
+}
+double or_est_inv_norm1_gt(const double* dl, const double* d, const double* du,
+                           const double* du2, const int64_t* ipiv, int64_t n) {
+  gt_ctx f = {dl, d, du, du2, ipiv, n};
+  return est_inv_norm1(n, apply_gt, &f);
 }
 
 double or_est_inv_norm1_lu(const double* LU, const int64_t* ipiv, int64_t n) {
@@ -630,6 +719,33 @@ static int solve_lu_route(const double* A, int64_t n, int64_t nrhs, uint32_t fla
   return failed;
 }
 
+/* The tridiagonal route: the three diagonals of A taken from dense storage
+ * (dense != 0: A(i,j) at M[i + j*n]) or from band storage with leading
+ * dimension ld and declared super-diagonal count kud (A(i,j) at
+ * M[(kud + i - j) + j*ld]); factor, solve X in place, estimate. */
+static int solve_gt_route(const double* M, int dense, int64_t ld, int64_t kud, int64_t n, double* X,
+                          int64_t nrhs, uint32_t flags, double anorm, or_info_t* info) {
+  double* dl = (double*)calloc((size_t)(n > 1 ? n - 1 : 1), sizeof(double));
+  double* d = (double*)calloc((size_t)n, sizeof(double));
+  double* du = (double*)calloc((size_t)(n > 1 ? n - 1 : 1), sizeof(double));
+  double* du2 = (double*)calloc((size_t)(n > 2 ? n - 2 : 1), sizeof(double));
+  int64_t* ipiv = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) {
+    d[i] = dense ? M[(size_t)i + (size_t)i * n] : M[(size_t)kud + (size_t)i * ld];
+    if (i + 1 < n) {
+      dl[i] = dense ? M[(size_t)(i + 1) + (size_t)i * n] : M[(size_t)(kud + 1) + (size_t)i * ld];
+      du[i] = dense ? M[(size_t)i + (size_t)(i + 1) * n] : M[(size_t)(kud - 1) + (size_t)(i + 1) * ld];
+    }
+  }
+  int failed = or_gt_factor(dl, d, du, du2, ipiv, n) != 0;
+  if (!failed) {
+    or_gt_solve(dl, d, du, du2, ipiv, n, X, nrhs, 0);
+    if (!(flags & OR_NO_RCOND)) info->rcond = or_rcond_from(anorm, or_est_inv_norm1_gt(dl, d, du, du2, ipiv, n));
+  }
+  free(dl); free(d); free(du); free(du2); free(ipiv);
+  return failed;
+}
+
 int or_solve(const double* A, const double* B, int64_t n, int64_t nrhs, uint32_t flags,
              const or_config_t* cfg_in, double* X, or_info_t* info) {
   or_config_t cfg;
@@ -656,7 +772,11 @@ int or_solve(const double* A, const double* B, int64_t n, int64_t nrhs, uint32_t
   }
   int failed = 0;
   int cls = (flags & OR_FORCE_LU) ? OR_CLS_GENERAL : sc.cls;
-  if (cls == OR_CLS_BANDED) { /* Sec. 2.1 */
+  if (cls == OR_CLS_BANDED && (flags & OR_TRIDIAG) && sc.kl == 1 && sc.ku == 1) {
+    /* the tridiagonal specialisation: the three diagonals */
+    info->route = OR_ROUTE_TRIDIAG;
+    failed = solve_gt_route(A, 1, n, 0, n, X, nrhs, flags, sc.norm1, info);
+  } else if (cls == OR_CLS_BANDED) { /* Sec. 2.1 */
     info->route = OR_ROUTE_BAND_LU;
     int64_t kl = sc.kl, ku = sc.ku, ldab = 2 * kl + ku + 1;
     double* AB = (double*)malloc(sizeof(double) * (size_t)ldab * n);
@@ -730,6 +850,22 @@ int or_solve_band(const double* AB, int64_t ldab, int64_t kl, int64_t ku, const 
   info->route = OR_ROUTE_BAND_LU;
   info->kl = tkl;
   info->ku = tku;
+  if ((flags & OR_TRIDIAG) && tkl == 1 && tku == 1) { /* the tridiagonal specialisation */
+    info->route = OR_ROUTE_TRIDIAG;
+    memcpy(X, B, sizeof(double) * (size_t)n * nrhs);
+    int gfail = solve_gt_route(AB, 0, ldab, ku, n, X, nrhs, flags, norm1, info);
+    double* dense = NULL;
+    int poor = !gfail && !(flags & OR_NO_RCOND) && !(info->rcond >= cfg.rcond_threshold);
+    if ((gfail || poor) && !(flags & OR_NO_APPROX) && n <= 4096) {
+      dense = (double*)calloc((size_t)n * n, sizeof(double));
+      for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < n; ++i)
+          dense[(size_t)i + (size_t)j * n] = AB[(size_t)(ku + i - j) + (size_t)j * ldab];
+    }
+    int st = finish(dense, B, n, nrhs, flags, &cfg, gfail, X, info);
+    free(dense);
+    return st;
+  }
   int64_t fld = 2 * tkl + tku + 1, kv = tkl + tku;
   double* F = (double*)calloc((size_t)fld * n, sizeof(double));
   int64_t* ipiv = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);

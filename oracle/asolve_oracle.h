@@ -29,12 +29,16 @@ enum { OR_CLS_NONE = 0, OR_CLS_BANDED = 1, OR_CLS_LOWER = 2, OR_CLS_UPPER = 3,
 /* Primary (factorisation) route actually taken. */
 enum { OR_ROUTE_NONE = 0, OR_ROUTE_BAND_LU = 1, OR_ROUTE_TRI_LOWER = 2,
        OR_ROUTE_TRI_UPPER = 3, OR_ROUTE_CHOL = 4, OR_ROUTE_CHOL_FAIL_LU = 5,
-       OR_ROUTE_LU = 6, OR_ROUTE_SVD = 7 };
+       OR_ROUTE_LU = 6, OR_ROUTE_SVD = 7, OR_ROUTE_TRIDIAG = 8 };
 /* Status codes: negative = error (X not a solution), positive = warning. */
 enum { OR_OK = 0, OR_W_APPROX = 1, OR_W_ILLCOND = 2, OR_E_INVALID = -1,
        OR_E_NONFINITE = -2, OR_E_SINGULAR = -3 };
 /* Flags. */
-enum { OR_NO_APPROX = 1, OR_FORCE_LU = 2, OR_FORCE_SVD = 4, OR_NO_RCOND = 8 };
+enum { OR_NO_APPROX = 1, OR_FORCE_LU = 2, OR_FORCE_SVD = 4, OR_NO_RCOND = 8,
+       /* the closing remarks' tridiagonal specialisation: banded systems with
+        * kl = ku = 1 take the tridiagonal route (opt-in; off, they take the
+        * band LU of Sec. 2.1) */
+       OR_TRIDIAG = 256 };
 
 typedef struct {
   int64_t kl, ku;          /* sub/super-diagonal counts (Sec. 2.1)            */
@@ -87,6 +91,14 @@ void    or_band_lu_solve(const double* AB, int64_t ldab, int64_t n, int64_t kl,
                          int64_t ku, const int64_t* ipiv, double* B, int64_t nrhs,
                          int trans);
 
+/* Tridiagonal LU with partial pivoting on the three diagonals (xGTTRF
+ * semantics): dl[0..n-2] sub-, d[0..n-1] main, du[0..n-2] super-diagonal,
+ * du2[0..n-3] the second super-diagonal the interchanges fill in, ipiv[i] = i
+ * or i+1.  Returns 0, or i+1 at the first exact zero pivot d[i]. */
+int     or_gt_factor(double* dl, double* d, double* du, double* du2, int64_t* ipiv, int64_t n);
+void    or_gt_solve(const double* dl, const double* d, const double* du, const double* du2,
+                    const int64_t* ipiv, int64_t n, double* B, int64_t nrhs, int trans);
+
 /* Reciprocal condition estimate (1-norm). */
 double  or_norm1(const double* A, int64_t n);
 double  or_norminf(const double* A, int64_t n);
@@ -95,6 +107,8 @@ double  or_est_inv_norm1_chol(const double* L, int64_t n);
 double  or_est_inv_norm1_tri(const double* T, int64_t n, int lower);
 double  or_est_inv_norm1_band(const double* AB, int64_t ldab, int64_t n, int64_t kl,
                               int64_t ku, const int64_t* ipiv);
+double  or_est_inv_norm1_gt(const double* dl, const double* d, const double* du,
+                            const double* du2, const int64_t* ipiv, int64_t n);
 double  or_rcond_from(double anorm, double ainvnm);
 
 /* One-sided Jacobi SVD: on return G = A V (columns u_i*sigma_i), V orthogonal,
