@@ -92,7 +92,6 @@ extern "C" {
                                        a later resident request with the same A pointer (A
                                        unchanged) solves with them (systems above n = 1024 or
                                        8 right-hand sides) */
-
 typedef struct asolve_ctx asolve_ctx;
 
 typedef struct {
@@ -126,6 +125,7 @@ typedef struct {           /* 64 bytes, one per system */
   int32_t detail;          /* bit 0: FP32 factor rejected by the rcond gate,
                               bit 1: refinement stalled, bit 2: FP32 Cholesky failed,
                               bit 3: factorisation reused from an earlier resident request,
+                              bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes),
                               bit 4: band system solved by the partitioned route for
                               diagonally dominant bands (the default for n >= 4096;
                               environment ASOLVE_BAND_SPIKE=0 turns it off) */

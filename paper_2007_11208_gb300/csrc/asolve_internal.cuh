@@ -59,6 +59,11 @@ constexpr int kGemmFp16 = ASOLVE_GEMM_FP16;
 // 2^-8 for BF16, 2^-11 for FP16, times a margin for the growth of |L||U|)
 constexpr double kKappaLimitBf16 = 1e3;
 constexpr double kKappaLimitFp16 = 1e4;
+// kappa limits of GMRES-IR with the same factors as preconditioner (the
+// large path's 16-bit modes): GMRES on inv(LU) A absorbs the factors' error
+// far beyond the classical refinement's limit
+constexpr double kKappaLimitGmresBf16 = 1e7;
+constexpr double kKappaLimitGmresFp16 = 1e8;
 
 // Scan flags (Sec. 2.1, 2.2, Fig. 4).
 enum : int32_t {

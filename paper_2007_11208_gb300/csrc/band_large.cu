@@ -718,7 +718,8 @@ double rcond_from_est(double anorm, double est) {
 // on by default; the environment variable ASOLVE_BAND_SPIKE=0 turns it off,
 // and every band system then keeps the GBTRF-order path below.
 constexpr int64_t kSpkMinN = 4096;      // shorter systems: the one-warp path
-constexpr int64_t kSpkBlocks = 2432;    // target number of blocks (16 per SM)
+constexpr int64_t kSpkBlocks = 19456;   // target number of blocks (128 per SM: the block steps run a
+                                        // thread, or a warp, per block)
 constexpr double kSpkFarTol = 8.67e-19; // 2^-60: far spike tips dropped below this
 constexpr int kSpkThreads = 128;
 
@@ -731,13 +732,13 @@ bool spike_enabled() {
   return on == 1;
 }
 
-// Block length and count at attempt `level`: at least 16 (kl+ku) and 256
+// Block length and count at attempt `level`: at least 16 (kl+ku) and 64
 // rows per block (on the band workload's matrices the far tips fell below
 // 2^-60 from about 16 (kl+ku) rows), doubled at each further attempt.
 bool spike_shape(int64_t n, int kl, int ku, int level, int64_t* m, int64_t* P) {
   int64_t mm = n / kSpkBlocks;
   if (mm < 16 * (int64_t)(kl + ku)) mm = 16 * (int64_t)(kl + ku);
-  if (mm < 256) mm = 256;
+  if (mm < 64) mm = 64;
   mm <<= level;
   *m = mm;
   *P = n / mm;
@@ -1013,7 +1014,7 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   char* base = static_cast<char*>(ws);
   char* tail = base + ((ws_bytes - kTailBytes) & ~(size_t)255);
   BandScan* dscan = reinterpret_cast<BandScan*>(tail);
-  double* dscal = reinterpret_cast<double*>(tail + 256);
+  double* dscal = reinterpret_cast<double*>(tail + 256);  // 32 doubles: estimator scalars and partials
   int* dint = reinterpret_cast<int*>(tail + 512);
   unsigned long long* colmax = reinterpret_cast<unsigned long long*>(tail + 1024);
   int kl, ku;

@@ -19,44 +19,72 @@ namespace {
     if (_e != cudaSuccess) return ASOLVE_E_CUDA;    \
   } while (0)
 
-// estimator helpers (one CTA of 1024 threads each)
+// Estimator reductions over a device vector, spread over kEstBlocks CTAs
+// and deterministic: the sum of |x| from per-CTA partials (a fixed split of
+// the index range, a fixed order inside each CTA) added in CTA order; the
+// first index of max |x| from an atomic maximum of the magnitudes' bit
+// patterns (order-free: the integer order of non-negative doubles is their
+// numeric order) and then an atomic minimum over the indices that reach it.
+// Scratch: dscal[0] the sum, dscal[1..2] the values of the argmax step,
+// dscal[3] the maximum's bits, dscal[8 .. 8 + kEstBlocks) the partials;
+// dint[1] the index.
+constexpr int kEstBlocks = 24;
+constexpr int kEstThreads = 1024;
+
 template <typename V>
-__global__ void k_vec_sumabs(const V* x, int n, double* out) {
+__global__ void __launch_bounds__(kEstThreads) k_vec_sumabs_part(const V* x, int n, double* part) {
   __shared__ double red[32];
+  const int per = (n + kEstBlocks - 1) / kEstBlocks;
+  const int lo = blockIdx.x * per, hi = min(n, lo + per);
   double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += fabs((double)x[i]);
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) s += fabs((double)x[i]);
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[blockIdx.x] = t;
+  }
+}
+__global__ void k_vec_sum_final(const double* part, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < kEstBlocks; ++b) t += part[b];
     *out = t;
   }
 }
 template <typename V>
-__global__ void k_vec_argmax(const V* x, int n, int* out, double* vals, int jprev) {
-  __shared__ double rv[32];
-  __shared__ int ri[32];
-  double best = -1.0;
-  int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+__global__ void __launch_bounds__(kEstThreads) k_vec_absmax_bits(const V* x, int n, unsigned long long* mbits) {
+  unsigned long long m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double a = fabs((double)x[i]);
-    if (a > best) { best = a; bi = i; }
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    if (a == a && b > m) m = b;  // NaN entries never win
   }
-  warp_argmax_first(best, bi);
-  if ((threadIdx.x & 31) == 0) { rv[threadIdx.x >> 5] = best; ri[threadIdx.x >> 5] = bi; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = rv[0];
-    int ii = ri[0];
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k)
-      if (rv[k] > b || (rv[k] == b && ri[k] < ii)) { b = rv[k]; ii = ri[k]; }
-    *out = ii;
-    vals[0] = (ii >= 0 && ii < n) ? fabs((double)x[ii]) : 0.0;
-    vals[1] = (jprev >= 0 && jprev < n) ? (double)x[jprev] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mbits, m);
+}
+template <typename V>
+__global__ void __launch_bounds__(kEstThreads) k_vec_first_at(const V* x, int n, const unsigned long long* mbits,
+                                                              int* idx) {
+  const unsigned long long m = *mbits;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = fabs((double)x[i]);
+    if ((unsigned long long)__double_as_longlong(a) == m) atomicMin(idx, i);
   }
 }
+template <typename V>
+__global__ void k_vec_argmax_fin(const V* x, int n, int* out, double* vals, int jprev) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int ii = *out;
+  vals[0] = (ii >= 0 && ii < n) ? fabs((double)x[ii]) : 0.0;
+  vals[1] = (jprev >= 0 && jprev < n) ? (double)x[jprev] : 0.0;
+}
+
 // mode 0: x = 1/n; 1: x = e_j; 2: alternating test vector;
 // 3: xi = sign(x), x = xi, flag[0] |= (sign changed)
 template <typename V>
@@ -79,9 +107,20 @@ __global__ void k_vec_set(V* x, V* xi, int n, int mode, int j, int* flag) {
 template <typename V, typename Apply>
 int est_host(int n, V* v, V* xi, double* dscal, int* dint, Apply apply, cudaStream_t st, double* out) {
   auto sumabs = [&](double* r) -> int {
-    k_vec_sumabs<V><<<1, 1024, 0, st>>>(v, n, dscal);
+    k_vec_sumabs_part<V><<<kEstBlocks, kEstThreads, 0, st>>>(v, n, dscal + 8);
+    k_vec_sum_final<<<1, 32, 0, st>>>(dscal + 8, dscal);
     ECK(cudaMemcpyAsync(r, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
     ECK(cudaStreamSynchronize(st));
+    return ASOLVE_OK;
+  };
+  // first index of max |v| into dint[1]; |v[j]| and v[jprev] into dscal[1..2]
+  auto argmax = [&](int jp) -> int {
+    unsigned long long* mb = reinterpret_cast<unsigned long long*>(dscal + 3);
+    ECK(cudaMemsetAsync(mb, 0, sizeof(unsigned long long), st));
+    ECK(cudaMemsetAsync(dint + 1, 0x7f, sizeof(int), st));  // 0x7f7f7f7f: above any index
+    k_vec_absmax_bits<V><<<kEstBlocks, kEstThreads, 0, st>>>(v, n, mb);
+    k_vec_first_at<V><<<kEstBlocks, kEstThreads, 0, st>>>(v, n, mb, dint + 1);
+    k_vec_argmax_fin<V><<<1, 32, 0, st>>>(v, n, dint + 1, dscal + 1, jp);
     return ASOLVE_OK;
   };
   const int g = (n + 255) / 256;
@@ -103,7 +142,7 @@ int est_host(int n, V* v, V* xi, double* dscal, int* dint, Apply apply, cudaStre
   int jprev = -1;
   for (;;) {
     int j;
-    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, jprev);
+    if ((rc = argmax(jprev))) return rc;
     ECK(cudaMemcpyAsync(&j, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     ECK(cudaStreamSynchronize(st));
     if (j < 0 || j >= n) { est = NAN; break; }
@@ -120,7 +159,7 @@ int est_host(int n, V* v, V* xi, double* dscal, int* dint, Apply apply, cudaStre
     if ((rc = apply(v, true))) return rc;
     double vals[2];
     int jn;
-    k_vec_argmax<V><<<1, 1024, 0, st>>>(v, n, dint + 1, dscal + 1, j);
+    if ((rc = argmax(j))) return rc;
     ECK(cudaMemcpyAsync(&jn, dint + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
     ECK(cudaMemcpyAsync(vals, dscal + 1, sizeof(vals), cudaMemcpyDeviceToHost, st));
     ECK(cudaStreamSynchronize(st));

@@ -36,6 +36,8 @@ cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const flo
                            int K, int passes, int* err, cudaStream_t st, bool trans_b, bool lower);
 
 constexpr int kLB = 128;  // panel / block width of the large path
+constexpr int kGmresM = 30;         // GMRES-IR: Krylov basis size of one inner solve
+constexpr double kGmresTol = 1e-4;  // inner solve: preconditioned residual reduced by this factor
 
 // ------------------------------------------------------------ utilities
 // Bounded grid-wide barrier for cooperatively launched kernels (all CTAs
@@ -911,6 +913,49 @@ __global__ void k_scale_add(double* __restrict__ x, int n, int nrhs, const doubl
   }
 }
 
+// ---- GMRES-IR kernels: the Krylov basis V (columns of n doubles, ld ldv)
+// h[j] = V_j . w for j < m: a CTA per column, a fixed-order block sum.
+__global__ void __launch_bounds__(256) k_krylov_dots(const double* __restrict__ V, int64_t ldv, int n, int m,
+                                                     const double* __restrict__ w, double* __restrict__ h) {
+  __shared__ double red[8];
+  const int j = blockIdx.x;
+  if (j >= m) return;
+  const double* v = V + (size_t)j * ldv;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s = fma(v[i], w[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < 8; ++k) t += red[k];
+    h[j] = t;
+  }
+}
+
+// w += sign * sum_{j < m} V_j h[j], a thread per row.
+__global__ void k_krylov_comb(double* __restrict__ w, const double* __restrict__ V, int64_t ldv, int n, int m,
+                              const double* __restrict__ h, double sign) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s = fma(V[(size_t)j * ldv + i], h[j], s);
+    w[i] += sign * s;
+  }
+}
+
+// dst = (float)(src * inv)  and  dst = (double)src * s
+__global__ void k_vec_to_f32(const double* __restrict__ src, int n, double inv, float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = (float)(src[i] * inv);
+}
+__global__ void k_vec_from_f32(const float* __restrict__ src, int n, double s, double* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    dst[i] = (double)src[i] * s;
+}
+__global__ void k_vec_scale(double* __restrict__ dst, const double* __restrict__ src, int n, double s) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] * s;
+}
+
 // permutation: dst[k] = src[perm[k]] (forward) or dst[perm[k]] = src[k]
 template <typename V>
 __global__ void k_permute(const V* __restrict__ src, V* __restrict__ dst, int n, int nrhs, const int* perm, int inverse) {
@@ -1260,6 +1305,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += scan_large_workspace(n) + 4096;
   b += sizeof(int) * (size_t)(((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR)) + 1024;  // wave flags
   if (n <= kSvdLargeMax) b += large_svd_ws_bytes(n, nrhs) + 4096;  // SVD fallback (V, sigma, coefficients)
+  b += sizeof(double) * (size_t)n * (kGmresM + 4) + sizeof(double) * (kGmresM + 2) + 2048;  // GMRES-IR
   return b + (1 << 20);
 }
 
@@ -1291,7 +1337,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   // ---- scan (Sec. 2.1, 2.2, Fig. 4)
   void* sws = ar.take(scan_large_workspace(n));
   ScanRes* dsr = static_cast<ScanRes*>(ar.take(sizeof(ScanRes)));
-  double* dscal = static_cast<double*>(ar.take(sizeof(double) * 8));
+  double* dscal = static_cast<double*>(ar.take(sizeof(double) * 32));  // estimator scalars and partials
   int* dint = static_cast<int*>(ar.take(sizeof(int) * 8));
   const int wcap = ((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR);
   int* wflags = static_cast<int*>(ar.take(sizeof(int) * (size_t)wcap));
@@ -1567,6 +1613,151 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     LCK(cudaStreamSynchronize(st));
     return ok;
   };
+  // GMRES-IR (Carson & Higham): the correction solve A d = r of each
+  // refinement step is GMRES in FP64 on inv(M) A d = inv(M) r, M the
+  // low-precision factors applied in FP32 (left preconditioning), a Krylov
+  // basis of at most kGmresM vectors, classical Gram-Schmidt done twice,
+  // Givens rotations on the host's small Hessenberg matrix; one inner solve
+  // per right-hand side and step.  Returns 1 converged, 0 stalled, < 0 error;
+  // *inner: the inner iterations (products with A) over all steps.
+  double* gV = static_cast<double*>(ar.take(sizeof(double) * (size_t)n * (kGmresM + 1)));
+  double* gw = static_cast<double*>(ar.take(sizeof(double) * (size_t)n));
+  double* gt = static_cast<double*>(ar.take(sizeof(double) * (size_t)n));
+  double* gzero = static_cast<double*>(ar.take(sizeof(double) * (size_t)n));
+  double* gh = static_cast<double*>(ar.take(sizeof(double) * (kGmresM + 2)));
+  if (!gV || !gw || !gt || !gzero || !gh) return ASOLVE_E_NOMEM;
+  auto gmres_ir = [&](Fac<float>& f, bool lu, int& iters, int& inner, double& berr) -> int {
+    const unsigned gv = (unsigned)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    float* xf = static_cast<float*>(xs);
+    float* tf = static_cast<float*>(tmp);
+    const double anrm = sr.norminf > 0.0 ? sr.norminf : 1.0;
+    std::vector<double> H((size_t)(kGmresM + 1) * kGmresM), cs(kGmresM), sn(kGmresM), g(kGmresM + 1),
+        hv(kGmresM + 1), y(kGmresM);
+    LCK(cudaMemsetAsync(gzero, 0, sizeof(double) * (size_t)n, st));
+    // out = s_out * inv(M) (v / s_in): v in FP64, brought into FP32 range by
+    // s_in (a power-of-two-free scale; the product with s_out undoes it)
+    auto precond = [&](const double* v, double s_in, double s_out, double* out) -> int {
+      k_vec_to_f32<<<gv, 256, 0, st>>>(v, n, 1.0 / s_in, xf);
+      const int r2 = apply_large<float, float>(f, lu, n, xf, 1, false, tf, st);
+      if (r2) return r2;
+      k_vec_from_f32<<<gv, 256, 0, st>>>(xf, n, s_out, out);
+      return ASOLVE_OK;
+    };
+    auto dots = [&](const double* V, int m, const double* w, double* hh) -> int {
+      k_krylov_dots<<<m, 256, 0, st>>>(V, n, n, m, w, gh);
+      LCK(cudaMemcpyAsync(hh, gh, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      return ASOLVE_OK;
+    };
+    // one inner GMRES solve for column c of R (max |r| = rm); d added to X
+    auto solve_col = [&](int c, double rm) -> int {
+      int r2;
+      const double rs = rm > 0.0 ? rm : 1.0;
+      if ((r2 = precond(R + (size_t)c * n, rs, rs, gw))) return r2;
+      double nb;
+      if ((r2 = dots(gw, 1, gw, &nb))) return r2;
+      const double beta = sqrt(nb);
+      if (!(beta > 0.0) || !(beta <= DBL_MAX)) return ASOLVE_OK;
+      k_vec_scale<<<gv, 256, 0, st>>>(gV, gw, n, 1.0 / beta);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      for (int j = 0; j < kGmresM; ++j) {
+        double* vj = gV + (size_t)j * n;
+        // w = inv(M) A v_j: the residual kernel gives t = 0 - A v_j
+        LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2, st));
+        if ((r2 = residual_large(a.A, n, gzero, vj, 1, gt, colmax, Pres, a.num_sms, st))) return r2;
+        if ((r2 = precond(gt, anrm, -anrm, gw))) return r2;  // w = inv(M) A v_j
+        // classical Gram-Schmidt, twice
+        if ((r2 = dots(gV, j + 1, gw, hv.data()))) return r2;
+        LCK(cudaMemcpyAsync(gh, hv.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+        k_krylov_comb<<<gv, 256, 0, st>>>(gw, gV, n, n, j + 1, gh, -1.0);
+        std::vector<double> h2((size_t)j + 1);
+        if ((r2 = dots(gV, j + 1, gw, h2.data()))) return r2;
+        LCK(cudaMemcpyAsync(gh, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+        k_krylov_comb<<<gv, 256, 0, st>>>(gw, gV, n, n, j + 1, gh, -1.0);
+        for (int i = 0; i <= j; ++i) hv[i] += h2[i];
+        double hn2;
+        if ((r2 = dots(gw, 1, gw, &hn2))) return r2;
+        const double hn = sqrt(hn2);
+        if (!(hn <= DBL_MAX)) return ASOLVE_OK;  // NaN/Inf: give up this inner solve
+        // Hessenberg column j, previous rotations, then a new one
+        for (int i = 0; i <= j; ++i) H[(size_t)j * (kGmresM + 1) + i] = hv[i];
+        H[(size_t)j * (kGmresM + 1) + j + 1] = hn;
+        double* hc = &H[(size_t)j * (kGmresM + 1)];
+        for (int i = 0; i < j; ++i) {
+          const double t0 = cs[i] * hc[i] + sn[i] * hc[i + 1];
+          hc[i + 1] = -sn[i] * hc[i] + cs[i] * hc[i + 1];
+          hc[i] = t0;
+        }
+        const double rr = hypot(hc[j], hc[j + 1]);
+        cs[j] = rr > 0.0 ? hc[j] / rr : 1.0;
+        sn[j] = rr > 0.0 ? hc[j + 1] / rr : 0.0;
+        hc[j] = rr;
+        hc[j + 1] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        ++inner;
+        if (!(fabs(g[j + 1]) > kGmresTol * beta) || !(hn > 0.0)) break;
+        k_vec_scale<<<gv, 256, 0, st>>>(gV + (size_t)(j + 1) * n, gw, n, 1.0 / hn);
+      }
+      // y = H(0:k, 0:k) \ g(0:k), then X(:, c) += V y
+      for (int i = k - 1; i >= 0; --i) {
+        double t0 = g[i];
+        for (int q = i + 1; q < k; ++q) t0 -= H[(size_t)q * (kGmresM + 1) + i] * y[q];
+        y[i] = H[(size_t)i * (kGmresM + 1) + i] != 0.0 ? t0 / H[(size_t)i * (kGmresM + 1) + i] : 0.0;
+      }
+      LCK(cudaMemcpyAsync(gh, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+      k_krylov_comb<<<gv, 256, 0, st>>>(a.X + (size_t)c * n, gV, n, n, k, gh, 1.0);
+      LCK(cudaStreamSynchronize(st));
+      return ASOLVE_OK;
+    };
+    std::vector<unsigned long long> hm((size_t)3 * nrhs);
+    std::vector<double> bmax((size_t)nrhs);
+    LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
+    k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.B, n, nrhs, colmax + 2 * nrhs);
+    LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 3 * nrhs, cudaMemcpyDeviceToHost, st));
+    LCK(cudaStreamSynchronize(st));
+    for (int c = 0; c < nrhs; ++c) {
+      memcpy(&bmax[c], &hm[2 * nrhs + c], 8);
+      if (!(bmax[c] <= DBL_MAX)) return ASOLVE_E_NONFINITE;
+    }
+    // x0 = 0: the first step solves A d = b
+    LCK(cudaMemsetAsync(a.X, 0, sizeof(double) * (size_t)n * nrhs, st));
+    double berr_prev = INFINITY;
+    berr = INFINITY;
+    iters = 0;
+    inner = 0;
+    for (int it = 0;; ++it) {
+      LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
+      {
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        if (rr_) return rr_;
+      }
+      k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
+      LCK(cudaMemcpyAsync(hm.data(), colmax, sizeof(unsigned long long) * 2 * nrhs, cudaMemcpyDeviceToHost, st));
+      LCK(cudaStreamSynchronize(st));
+      berr = 0.0;
+      std::vector<double> rmax((size_t)nrhs);
+      for (int c = 0; c < nrhs; ++c) {
+        double xm;
+        memcpy(&rmax[c], &hm[c], 8);
+        memcpy(&xm, &hm[nrhs + c], 8);
+        const double den = sr.norminf * xm + bmax[c];
+        const double b1 = den > 0.0 ? rmax[c] / den : (rmax[c] > 0.0 ? INFINITY : 0.0);
+        if (!(b1 <= berr)) berr = b1;
+      }
+      if (berr <= a.ir_target_berr) return 1;
+      if (it >= a.ir_max_iter || !(berr < 0.5 * berr_prev)) return 0;  // stalled
+      berr_prev = berr;
+      for (int c = 0; c < nrhs; ++c) {
+        const int r2 = solve_col(c, rmax[c]);
+        if (r2) return r2;
+      }
+      ++iters;
+    }
+  };
   // the kept factorisation fills the fields of a later call's info
   auto keep = [&](int precision, bool lu) {
     if (!kept) return;
@@ -1680,6 +1871,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       f.dinvU = lu ? dinvU : nullptr;
       double rcv = NAN;
       bool gate_ok = true;
+      // the 16-bit modes also have GMRES-IR, which reaches much larger kappa
+      const bool sixteen = a.precision == ASOLVE_PREC_BF16 || a.precision == ASOLVE_PREC_FP16;
+      const double klim_gm = a.precision == ASOLVE_PREC_BF16 ? kKappaLimitGmresBf16 : kKappaLimitGmresFp16;
+      bool gm_ok = sixteen;
       if (!no_rcond) {
         double est;
         auto apply = [&](float* v, bool tr) { return apply_large<float, float>(f, lu, n, v, 1, tr, (float*)tmp, st); };
@@ -1687,12 +1882,23 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         if (rc) return rc;
         rcv = rcond_of(sr.norm1, est);
         gate_ok = rcv >= 1.0 / klim;
+        gm_ok = sixteen && rcv >= 1.0 / fmin(a.ir_kappa_limit, klim_gm);
       }
-      if (!gate_ok) { detail |= 1; break; }
+      if (!gate_ok && !gm_ok) { detail |= 1; break; }
       int iters = 0;
       double berr = NAN;
-      const int okc = mixed_ir(f, lu, iters, berr);
-      if (okc < 0) return info->status = okc;
+      int okc = 0;
+      if (gate_ok) {  // classical refinement first
+        okc = mixed_ir(f, lu, iters, berr);
+        if (okc < 0) return info->status = okc;
+      }
+      if (okc == 0 && gm_ok) {  // beyond its kappa limit, or stalled: GMRES-IR
+        int it2 = 0, inner = 0;
+        okc = gmres_ir(f, lu, it2, inner, berr);
+        if (okc < 0) return info->status = okc;
+        iters += it2;
+        if (okc == 1) detail |= 32;
+      }
       const bool ok = okc == 1;
       if (ok) {
         info->route = try_chol ? ASOLVE_ROUTE_CHOL : (chol ? ASOLVE_ROUTE_CHOL_FAIL_LU : ASOLVE_ROUTE_LU);
