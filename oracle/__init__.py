@@ -27,11 +27,13 @@ _lib = None
 
 CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
 (ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
- ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD, ROUTE_TRIDIAG) = range(9)
+ ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD, ROUTE_TRIDIAG, ROUTE_LDLT, ROUTE_CHOL_FAIL_LDLT) = range(11)
 OK, W_APPROX, W_ILLCOND = 0, 1, 2
 E_INVALID, E_NONFINITE, E_SINGULAR = -1, -2, -3
 NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND = 1, 2, 4, 8
 TRIDIAG = 256  # tridiagonal specialisation (opt-in route for kl = ku = 1)
+SYM_INDEF = 512  # symmetric-indefinite specialisation (opt-in LDL^T route, n <= LDLT_NMAX)
+LDLT_NMAX = 1024
 
 
 class Scan(C.Structure):
@@ -96,6 +98,11 @@ def lib():
                   "or_est_inv_norm1_band", "or_rcond_from"):
             getattr(L, f).restype = d
         L.or_rcond_from.argtypes = [d, d]
+        L.or_is_symmetric.argtypes = [pd, i64, d]
+        L.or_ldlt_factor.argtypes = [pd, i64, pi64]
+        L.or_ldlt_solve.argtypes = [pd, pi64, i64, pd, i64]
+        L.or_est_inv_norm1_ldlt.argtypes = [pd, pi64, i64]
+        L.or_est_inv_norm1_ldlt.restype = d
         L.or_gt_factor.argtypes = [pd, pd, pd, pd, pi64, i64]
         L.or_gt_solve.argtypes = [pd, pd, pd, pd, pi64, i64, pd, i64, i32]
         L.or_est_inv_norm1_gt.argtypes = [pd, pd, pd, pd, pi64, i64]
@@ -225,6 +232,31 @@ def band_lu_solve(F, kl, ku, ipiv, B, trans=False):
                            _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), _p(X),
                            X.shape[1], int(trans))
     return X
+
+
+def is_symmetric(A, tol=None):
+    A = _f64(A)
+    return lib().or_is_symmetric(_p(A), A.shape[0], config().sympd_tol if tol is None else tol)
+
+
+def ldlt_factor(A):
+    """Bunch-Kaufman LDL^T of A's lower triangle: (F, ipiv, info)."""
+    F = _f64(A).copy(order="F")
+    n = F.shape[0]
+    ipiv = np.zeros(max(n, 1), dtype=np.int64)
+    info = lib().or_ldlt_factor(_p(F), n, _pi(ipiv))
+    return F, ipiv[:n], info
+
+
+def ldlt_solve(F, ipiv, B):
+    n = F.shape[0]
+    X = _f64(np.array(B, dtype=np.float64, ndmin=2).reshape(n, -1)).copy(order="F")
+    lib().or_ldlt_solve(_p(F), _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), n, _p(X), X.shape[1])
+    return X
+
+
+def est_inv_norm1_ldlt(F, ipiv):
+    return lib().or_est_inv_norm1_ldlt(_p(F), _pi(np.ascontiguousarray(ipiv, dtype=np.int64)), F.shape[0])
 
 
 def gt_factor(dl, d, du):

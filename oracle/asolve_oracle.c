@@ -432,6 +432,145 @@ void or_gt_solve(const double* dl, const double* d, const double* du, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Plain symmetric (not positive definite) systems, the closing remarks'
+ * other specialisation.  Symmetry is the Fig. 4 test on its own. */
+int or_is_symmetric(const double* A, int64_t n, double tol) {
+  for (int64_t j = 0; j + 1 < n; ++j)
+    for (int64_t i = j + 1; i < n; ++i) {
+      double a_ij = AT(A, n, i, j), a_ji = AT(A, n, j, i);
+      double delta = fabs(a_ij - a_ji);
+      double mx = fabs(a_ij) > fabs(a_ji) ? fabs(a_ij) : fabs(a_ji);
+      if (delta > tol && delta > tol * mx) return 0;
+    }
+  return 1;
+}
+
+static void swap_d(double* a, double* b) { double t = *a; *a = *b; *b = t; }
+
+/* Bunch-Kaufman LDL^T of the lower triangle, column by column (Bunch &
+ * Kaufman 1977, the partial-pivoting variant LAPACK's xSYTRF uses): with
+ * alpha = (1 + sqrt 17)/8, colmax the largest off-diagonal modulus of
+ * column k (at row imax) and rowmax the largest off-diagonal modulus of
+ * row/column imax of the trailing matrix,
+ *   |a_kk| >= alpha colmax                    -> 1 x 1 pivot a_kk;
+ *   |a_kk| rowmax >= alpha colmax^2           -> 1 x 1 pivot a_kk;
+ *   |a_imax,imax| >= alpha rowmax             -> 1 x 1 pivot a_imax,imax (k <-> imax);
+ *   otherwise                                 -> 2 x 2 pivot on (k, imax) (k+1 <-> imax).
+ * After the symmetric interchange the trailing matrix is updated with the
+ * pivot block E: A22 -= C E^-1 C^T, and the multipliers C E^-1 stored as L. */
+int or_ldlt_factor(double* A, int64_t n, int64_t* ipiv) {
+#define LT(i, j) A[(size_t)(i) + (size_t)(j) * (size_t)n]
+  const double alpha = (1.0 + sqrt(17.0)) / 8.0;
+  int info = 0;
+  int64_t k = 0;
+  while (k < n) {
+    int64_t kstep = 1, kp = k, imax = k;
+    const double absakk = fabs(LT(k, k));
+    double colmax = 0.0;
+    for (int64_t i = k + 1; i < n; ++i)
+      if (fabs(LT(i, k)) > colmax) { colmax = fabs(LT(i, k)); imax = i; }
+    if (absakk == 0.0 && colmax == 0.0) { /* a zero column: D(k) = 0 */
+      if (!info) info = (int)(k + 1);
+      ipiv[k] = k;
+      k += 1;
+      continue;
+    }
+    if (absakk < alpha * colmax) {
+      double rowmax = 0.0;
+      for (int64_t j = k; j < imax; ++j) rowmax = fmax(rowmax, fabs(LT(imax, j)));
+      for (int64_t i = imax + 1; i < n; ++i) rowmax = fmax(rowmax, fabs(LT(i, imax)));
+      if (absakk >= alpha * colmax * (colmax / rowmax)) kp = k;
+      else if (fabs(LT(imax, imax)) >= alpha * rowmax) kp = imax;
+      else { kp = imax; kstep = 2; }
+    }
+    const int64_t kk = k + kstep - 1; /* the row/column brought to kp's place */
+    if (kp != kk) { /* symmetric interchange of kk and kp, lower triangle */
+      for (int64_t i = kp + 1; i < n; ++i) swap_d(&LT(i, kk), &LT(i, kp));
+      for (int64_t j = kk + 1; j < kp; ++j) swap_d(&LT(j, kk), &LT(kp, j));
+      swap_d(&LT(kk, kk), &LT(kp, kp));
+      if (kstep == 2) swap_d(&LT(k + 1, k), &LT(kp, k));
+    }
+    if (kstep == 1) {
+      const double d = LT(k, k);
+      for (int64_t j = k + 1; j < n; ++j) {
+        const double lj = LT(j, k) / d;
+        for (int64_t i = j; i < n; ++i) LT(i, j) = LT(i, j) - LT(i, k) * lj;
+      }
+      for (int64_t i = k + 1; i < n; ++i) LT(i, k) = LT(i, k) / d;
+      ipiv[k] = kp;
+    } else {
+      /* E = [a b; b c], E^-1 = [c -b; -b a] / (a c - b^2) */
+      const double a = LT(k, k), b = LT(k + 1, k), c = LT(k + 1, k + 1);
+      const double det = a * c - b * b;
+      for (int64_t j = k + 2; j < n; ++j) {
+        const double w0 = (c * LT(j, k) - b * LT(j, k + 1)) / det;
+        const double w1 = (a * LT(j, k + 1) - b * LT(j, k)) / det;
+        for (int64_t i = j; i < n; ++i) LT(i, j) = LT(i, j) - LT(i, k) * w0 - LT(i, k + 1) * w1;
+        LT(j, k) = w0;
+        LT(j, k + 1) = w1;
+      }
+      ipiv[k] = ipiv[k + 1] = -(kp + 1);
+    }
+    k += kstep;
+  }
+  return info;
+#undef LT
+}
+
+/* Solve with the LDL^T factors: x = P^T L^-T D^-1 L^-1 P b, the
+ * interchanges applied in the factorisation's order on the way in and in
+ * reverse on the way out. */
+void or_ldlt_solve(const double* F, const int64_t* ipiv, int64_t n, double* B, int64_t nrhs) {
+#define LT(i, j) F[(size_t)(i) + (size_t)(j) * (size_t)n]
+  for (int64_t c = 0; c < nrhs; ++c) {
+    double* b = B + (size_t)c * n;
+    int64_t k = 0;
+    while (k < n) { /* L D y = P b */
+      if (ipiv[k] >= 0) {
+        const int64_t kp = ipiv[k];
+        if (kp != k) swap_d(&b[k], &b[kp]);
+        for (int64_t i = k + 1; i < n; ++i) b[i] = b[i] - LT(i, k) * b[k];
+        b[k] = b[k] / LT(k, k);
+        k += 1;
+      } else {
+        const int64_t kp = -ipiv[k] - 1;
+        if (kp != k + 1) swap_d(&b[k + 1], &b[kp]);
+        for (int64_t i = k + 2; i < n; ++i) b[i] = b[i] - LT(i, k) * b[k] - LT(i, k + 1) * b[k + 1];
+        const double a = LT(k, k), bb = LT(k + 1, k), cc = LT(k + 1, k + 1);
+        const double det = a * cc - bb * bb;
+        const double y0 = b[k], y1 = b[k + 1];
+        b[k] = (cc * y0 - bb * y1) / det;
+        b[k + 1] = (a * y1 - bb * y0) / det;
+        k += 2;
+      }
+    }
+    k = n - 1;
+    while (k >= 0) { /* L^T x = y, then P^T */
+      if (ipiv[k] >= 0) {
+        double s = b[k];
+        for (int64_t i = k + 1; i < n; ++i) s = s - LT(i, k) * b[i];
+        b[k] = s;
+        const int64_t kp = ipiv[k];
+        if (kp != k) swap_d(&b[k], &b[kp]);
+        k -= 1;
+      } else { /* the 2 x 2 block (k-1, k) */
+        double s1 = b[k], s0 = b[k - 1];
+        for (int64_t i = k + 1; i < n; ++i) {
+          s1 = s1 - LT(i, k) * b[i];
+          s0 = s0 - LT(i, k - 1) * b[i];
+        }
+        b[k] = s1;
+        b[k - 1] = s0;
+        const int64_t kp = -ipiv[k] - 1;
+        if (kp != k) swap_d(&b[k], &b[kp]);
+        k -= 2;
+      }
+    }
+  }
+#undef LT
+}
+
+/* ------------------------------------------------------------------------ */
 /* 1-norm estimate of inv(A) (Hager 1984; Higham 1988, the estimator LAPACK's
  * xGECON/xPOCON/xGBCON/xTRCON use).  apply(ctx, x, trans) overwrites x with
  * inv(A) x (trans = 0) or inv(A)^T x (trans = 1). */
@@ -525,6 +664,16 @@ double or_est_inv_norm1_gt(const double* dl, const double* d, const double* du,
                            const double* du2, const int64_t* ipiv, int64_t n) {
   gt_ctx f = {dl, d, du, du2, ipiv, n};
   return est_inv_norm1(n, apply_gt, &f);
+}
+
+static void apply_ldlt(const void* c, double* x, int trans) {
+  (void)trans; /* inv(A) is symmetric */
+  const fac_ctx* f = (const fac_ctx*)c;
+  or_ldlt_solve(f->F, f->ipiv, f->n, x, 1);
+}
+double or_est_inv_norm1_ldlt(const double* F, const int64_t* ipiv, int64_t n) {
+  fac_ctx f = {F, ipiv, n, 0, 0, 0, 0};
+  return est_inv_norm1(n, apply_ldlt, &f);
 }
 
 double or_est_inv_norm1_lu(const double* LU, const int64_t* ipiv, int64_t n) {
@@ -719,6 +868,21 @@ static int solve_lu_route(const double* A, int64_t n, int64_t nrhs, uint32_t fla
   return failed;
 }
 
+/* The symmetric-indefinite route: LDL^T of A's lower triangle. */
+static int solve_ldlt_route(const double* A, int64_t n, int64_t nrhs, uint32_t flags, double anorm,
+                            double* X, or_info_t* info) {
+  double* F = (double*)malloc(sizeof(double) * (size_t)n * n);
+  int64_t* ipiv = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  memcpy(F, A, sizeof(double) * (size_t)n * n);
+  int failed = or_ldlt_factor(F, n, ipiv) != 0;
+  if (!failed) {
+    or_ldlt_solve(F, ipiv, n, X, nrhs);
+    if (!(flags & OR_NO_RCOND)) info->rcond = or_rcond_from(anorm, or_est_inv_norm1_ldlt(F, ipiv, n));
+  }
+  free(F); free(ipiv);
+  return failed;
+}
+
 /* The tridiagonal route: the three diagonals of A taken from dense storage
  * (dense != 0: A(i,j) at M[i + j*n]) or from band storage with leading
  * dimension ld and declared super-diagonal count kud (A(i,j) at
@@ -802,12 +966,22 @@ int or_solve(const double* A, const double* B, int64_t n, int64_t nrhs, uint32_t
       info->route = OR_ROUTE_CHOL;
       or_chol_solve(F, n, X, nrhs);
       if (!(flags & OR_NO_RCOND)) info->rcond = or_rcond_from(sc.norm1, or_est_inv_norm1_chol(F, n));
+    } else if ((flags & OR_SYM_INDEF) && n <= OR_LDLT_NMAX) {
+      /* Cholesky failure, symmetric after all: the symmetric-indefinite solver */
+      info->route = OR_ROUTE_CHOL_FAIL_LDLT;
+      memcpy(X, B, sizeof(double) * (size_t)n * nrhs);
+      failed = solve_ldlt_route(A, n, nrhs, flags, sc.norm1, X, info);
     } else { /* Cholesky failure: not sympd after all, use the general solver */
       info->route = OR_ROUTE_CHOL_FAIL_LU;
       memcpy(X, B, sizeof(double) * (size_t)n * nrhs);
       failed = solve_lu_route(A, n, nrhs, flags, sc.norm1, X, info);
     }
     free(F);
+  } else if ((flags & OR_SYM_INDEF) && !(flags & OR_FORCE_LU) && n <= OR_LDLT_NMAX &&
+             or_is_symmetric(A, n, cfg.sympd_tol)) {
+    /* plain symmetric, not likely_sympd: the symmetric-indefinite solver */
+    info->route = OR_ROUTE_LDLT;
+    failed = solve_ldlt_route(A, n, nrhs, flags, sc.norm1, X, info);
   } else { /* Sec. 2.4 */
     info->route = OR_ROUTE_LU;
     failed = solve_lu_route(A, n, nrhs, flags, sc.norm1, X, info);

@@ -29,7 +29,8 @@ enum { OR_CLS_NONE = 0, OR_CLS_BANDED = 1, OR_CLS_LOWER = 2, OR_CLS_UPPER = 3,
 /* Primary (factorisation) route actually taken. */
 enum { OR_ROUTE_NONE = 0, OR_ROUTE_BAND_LU = 1, OR_ROUTE_TRI_LOWER = 2,
        OR_ROUTE_TRI_UPPER = 3, OR_ROUTE_CHOL = 4, OR_ROUTE_CHOL_FAIL_LU = 5,
-       OR_ROUTE_LU = 6, OR_ROUTE_SVD = 7, OR_ROUTE_TRIDIAG = 8 };
+       OR_ROUTE_LU = 6, OR_ROUTE_SVD = 7, OR_ROUTE_TRIDIAG = 8, OR_ROUTE_LDLT = 9,
+       OR_ROUTE_CHOL_FAIL_LDLT = 10 };
 /* Status codes: negative = error (X not a solution), positive = warning. */
 enum { OR_OK = 0, OR_W_APPROX = 1, OR_W_ILLCOND = 2, OR_E_INVALID = -1,
        OR_E_NONFINITE = -2, OR_E_SINGULAR = -3 };
@@ -38,7 +39,13 @@ enum { OR_NO_APPROX = 1, OR_FORCE_LU = 2, OR_FORCE_SVD = 4, OR_NO_RCOND = 8,
        /* the closing remarks' tridiagonal specialisation: banded systems with
         * kl = ku = 1 take the tridiagonal route (opt-in; off, they take the
         * band LU of Sec. 2.1) */
-       OR_TRIDIAG = 256 };
+       OR_TRIDIAG = 256,
+       /* the closing remarks' plain-symmetric specialisation: a system of
+        * order n <= OR_LDLT_NMAX that is symmetric within the Fig. 4
+        * tolerance but not likely_sympd, or whose Cholesky factorisation
+        * fails, takes the Bunch-Kaufman LDL^T route (opt-in) */
+       OR_SYM_INDEF = 512 };
+enum { OR_LDLT_NMAX = 1024 };
 
 typedef struct {
   int64_t kl, ku;          /* sub/super-diagonal counts (Sec. 2.1)            */
@@ -99,6 +106,18 @@ int     or_gt_factor(double* dl, double* d, double* du, double* du2, int64_t* ip
 void    or_gt_solve(const double* dl, const double* d, const double* du, const double* du2,
                     const int64_t* ipiv, int64_t n, double* B, int64_t nrhs, int trans);
 
+/* The symmetry test of Fig. 4 alone: every pair within tol, absolute or
+ * relative. */
+int     or_is_symmetric(const double* A, int64_t n, double tol);
+/* Symmetric-indefinite LDL^T with Bunch-Kaufman pivoting (xSYTRF semantics,
+ * lower triangle read and overwritten): P A P^T = L D L^T, D with 1 x 1 and
+ * 2 x 2 blocks.  ipiv[k] = kp >= 0: 1 x 1 pivot, rows/columns k and kp
+ * interchanged; ipiv[k] = ipiv[k+1] = -(kp+1): a 2 x 2 pivot at (k, k+1)
+ * with k+1 and kp interchanged.  Returns 0, or k+1 at the first zero 1 x 1
+ * pivot (an exactly zero column). */
+int     or_ldlt_factor(double* A, int64_t n, int64_t* ipiv);
+void    or_ldlt_solve(const double* F, const int64_t* ipiv, int64_t n, double* B, int64_t nrhs);
+
 /* Reciprocal condition estimate (1-norm). */
 double  or_norm1(const double* A, int64_t n);
 double  or_norminf(const double* A, int64_t n);
@@ -109,6 +128,7 @@ double  or_est_inv_norm1_band(const double* AB, int64_t ldab, int64_t n, int64_t
                               int64_t ku, const int64_t* ipiv);
 double  or_est_inv_norm1_gt(const double* dl, const double* d, const double* du,
                             const double* du2, const int64_t* ipiv, int64_t n);
+double  or_est_inv_norm1_ldlt(const double* F, const int64_t* ipiv, int64_t n);
 double  or_rcond_from(double anorm, double ainvnm);
 
 /* One-sided Jacobi SVD: on return G = A V (columns u_i*sigma_i), V orthogonal,
