@@ -992,7 +992,8 @@ int or_solve(const double* A, const double* B, int64_t n, int64_t nrhs, uint32_t
 /* Band-storage input: AB holds A(i,j) at AB[(ku+i-j) + j*ldab] with
  * ldab >= kl+ku+1 (declared bandwidths).  A system given in band storage
  * always takes the banded route, with the true bandwidths found inside
- * the declared band.  The SVD fallback densifies A only for n <= 4096. */
+ * the declared band.  The SVD fallback densifies A only for
+ * n <= OR_SVD_DENSIFY_NMAX (the GPU library's limit for the same step). */
 int or_solve_band(const double* AB, int64_t ldab, int64_t kl, int64_t ku, const double* B,
                   int64_t n, int64_t nrhs, uint32_t flags, const or_config_t* cfg_in,
                   double* X, or_info_t* info) {
@@ -1030,7 +1031,7 @@ int or_solve_band(const double* AB, int64_t ldab, int64_t kl, int64_t ku, const 
     int gfail = solve_gt_route(AB, 0, ldab, ku, n, X, nrhs, flags, norm1, info);
     double* dense = NULL;
     int poor = !gfail && !(flags & OR_NO_RCOND) && !(info->rcond >= cfg.rcond_threshold);
-    if ((gfail || poor) && !(flags & OR_NO_APPROX) && n <= 4096) {
+    if ((gfail || poor) && !(flags & OR_NO_APPROX) && n <= OR_SVD_DENSIFY_NMAX) {
       dense = (double*)calloc((size_t)n * n, sizeof(double));
       for (int64_t j = 0; j < n; ++j)
         for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < n; ++i)
@@ -1056,7 +1057,7 @@ int or_solve_band(const double* AB, int64_t ldab, int64_t kl, int64_t ku, const 
   free(F); free(ipiv);
   double* dense = NULL;
   int poor = !failed && !(flags & OR_NO_RCOND) && !(info->rcond >= cfg.rcond_threshold);
-  if ((failed || poor) && !(flags & OR_NO_APPROX) && n <= 4096) {
+  if ((failed || poor) && !(flags & OR_NO_APPROX) && n <= OR_SVD_DENSIFY_NMAX) {
     dense = (double*)calloc((size_t)n * n, sizeof(double));
     for (int64_t j = 0; j < n; ++j)
       for (int64_t i = (j - ku > 0 ? j - ku : 0); i <= j + kl && i < n; ++i)

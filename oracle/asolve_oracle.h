@@ -46,6 +46,9 @@ enum { OR_NO_APPROX = 1, OR_FORCE_LU = 2, OR_FORCE_SVD = 4, OR_NO_RCOND = 8,
         * fails, takes the Bunch-Kaufman LDL^T route (opt-in) */
        OR_SYM_INDEF = 512 };
 enum { OR_LDLT_NMAX = 1024 };
+/* A system given in band storage reaches the SVD fallback (Sec. 2.5) only up
+ * to this order: the SVD runs on a dense copy. */
+enum { OR_SVD_DENSIFY_NMAX = 8192 };
 
 typedef struct {
   int64_t kl, ku;          /* sub/super-diagonal counts (Sec. 2.1)            */
