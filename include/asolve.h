@@ -24,6 +24,9 @@
  *  - Work is ordered on the context stream.  Calls returning an
  *    asolve_info through a host pointer synchronise that stream before they
  *    return; the *_async / batched calls do not unless ASOLVE_SYNC is set.
+ *    A stream the context creates is non-blocking: it is not ordered after
+ *    work on other streams, so inputs written there must be complete (or
+ *    the context stream made to wait on an event) before the call.
  */
 #ifndef ASOLVE_H
 #define ASOLVE_H
@@ -66,6 +69,14 @@ extern "C" {
 #define ASOLVE_ROUTE_CHOL_FAIL_LU  5   /* Sec. 2.3: Cholesky failed -> general solver */
 #define ASOLVE_ROUTE_LU            6   /* Sec. 2.4, Eq. 4 (xGETRF/xGETRS/xGECON) */
 #define ASOLVE_ROUTE_SVD           7   /* ASOLVE_FORCE_SVD only */
+#define ASOLVE_ROUTE_TRIDIAG       8   /* with ASOLVE_TRIDIAG: a banded system with kl = ku = 1
+                                          (the paper's closing remarks name tridiagonal
+                                          matrices for specialised handling; xGTTRF/xGTTRS/
+                                          xGTCON semantics) */
+#define ASOLVE_ROUTE_LDLT          9   /* with ASOLVE_SYM_INDEF: symmetric (Fig. 4 tolerance), not
+                                          likely_sympd: Bunch-Kaufman LDL^T (xSYTRF/xSYTRS/xSYCON
+                                          semantics; the paper names plain symmetric matrices) */
+#define ASOLVE_ROUTE_CHOL_FAIL_LDLT 10 /* with ASOLVE_SYM_INDEF: Cholesky failed -> LDL^T */
 
 /* ---- precision of the dense factorisations --------------------------- */
 #define ASOLVE_PREC_FP64    0   /* FP64 factorisations (DMMA tensor path) */
@@ -92,6 +103,21 @@ extern "C" {
                                        a later resident request with the same A pointer (A
                                        unchanged) solves with them (systems above n = 1024 or
                                        8 right-hand sides) */
+#define ASOLVE_TRIDIAG       0x100u /* tridiagonal specialisation (opt-in; the paper names it as
+                                       a further improvement): banded systems with kl = ku = 1
+                                       take ASOLVE_ROUTE_TRIDIAG -- elimination with partial
+                                       pivoting on the three diagonals (the pivots and
+                                       operations of xGTTRF), or, for long diagonally dominant
+                                       systems (n >= 4096), the partitioned route */
+#define ASOLVE_SYM_INDEF     0x200u /* symmetric-indefinite specialisation (opt-in; the paper names
+                                       it as a further improvement), n <= 1024 and at most 8
+                                       right-hand sides: a system symmetric within the Fig. 4
+                                       tolerance but not likely_sympd, or whose Cholesky fails,
+                                       takes Bunch-Kaufman LDL^T in FP64 (ASOLVE_ROUTE_LDLT /
+                                       ASOLVE_ROUTE_CHOL_FAIL_LDLT).  With more right-hand sides
+                                       and n <= 1024 the call returns E_UNSUPPORTED; above
+                                       n = 1024 the flag has no effect */
+
 typedef struct asolve_ctx asolve_ctx;
 
 typedef struct {
@@ -125,10 +151,10 @@ typedef struct {           /* 64 bytes, one per system */
   int32_t detail;          /* bit 0: FP32 factor rejected by the rcond gate,
                               bit 1: refinement stalled, bit 2: FP32 Cholesky failed,
                               bit 3: factorisation reused from an earlier resident request,
-                              bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes),
                               bit 4: band system solved by the partitioned route for
                               diagonally dominant bands (the default for n >= 4096;
-                              environment ASOLVE_BAND_SPIKE=0 turns it off) */
+                              environment ASOLVE_BAND_SPIKE=0 turns it off),
+                              bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes) */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */
@@ -246,7 +272,7 @@ int asolve_solve_batched_ptrs(asolve_ctx* ctx, int64_t count, const int64_t* n,
  * flight.  A, B, X: device pointers, or host pointers with
  * ASOLVE_HOST_BUFFERS (the server stages them in device memory it charges
  * to the budget); they must stay valid, and A and B unchanged, until the
- * request completes.  Allowed flags: NO_APPROX, FORCE_LU, FORCE_SVD,
+ * request completes.  Allowed flags: NO_APPROX, FORCE_LU, FORCE_SVD, TRIDIAG, SYM_INDEF,
  * NO_RCOND, BERR, HOST_BUFFERS, RESIDENT (one large request's device block
  * is kept, charged to the budget, until another resident request replaces
  * it or the budget needs it).  Errors: E_INVALID, E_UNSUPPORTED

@@ -1057,6 +1057,14 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
   bool spiked = false;
   double spike_be = NAN;
   int64_t spk_m = 0, spk_P = 0;
+  // the tridiagonal specialisation (ASOLVE_TRIDIAG, kl = ku = 1): the
+  // partitioned route below when it applies, else the elimination, whose
+  // pivots and operations for kl = ku = 1 are xGTTRF's.  (Parallel cyclic
+  // reduction was measured and left out: its O(n log n) FP64 divisions made
+  // it 4x slower than the partitioned route at n = 10^6, and on weakly
+  // dominant, ill-conditioned systems its backward error reached 4e-10.)
+  const bool tridiag = (a.flags & ASOLVE_TRIDIAG) && kl == 1 && ku == 1;
+  if (tridiag) info->route = ASOLVE_ROUTE_TRIDIAG;
   // dominant bands: the partitioned route (band_spike.cuh); blocks twice as
   // long on another attempt when the spikes have not decayed across them
   for (int level = 0; level < 3 && spike_enabled() && n >= kSpkMinN &&

@@ -20,6 +20,7 @@
 // persistent kernel pulling systems from its list; per-CTA scratch slots
 // hold the factors.
 #include "cta_linalg.cuh"
+#include "cta_ldlt.cuh"
 #include "band_warp.cuh"
 
 namespace asv {
@@ -73,7 +74,13 @@ __global__ void __launch_bounds__(1024) k_route(const BatchDesc* __restrict__ dp
       route = ASOLVE_ROUTE_LU;
     } else {
       switch (sr.cls) {
-        case ASOLVE_CLS_BANDED: list = L_BAND; route = ASOLVE_ROUTE_BAND_LU; break;
+        case ASOLVE_CLS_BANDED:
+          list = L_BAND;
+          // the tridiagonal specialisation runs the band kernel with kl = ku = 1,
+          // whose pivots and operations are xGTTRF's
+          route = ((d.flags & ASOLVE_TRIDIAG) && sr.kl == 1 && sr.ku == 1) ? ASOLVE_ROUTE_TRIDIAG
+                                                                            : ASOLVE_ROUTE_BAND_LU;
+          break;
         case ASOLVE_CLS_LOWER: list = L_TRI; route = ASOLVE_ROUTE_TRI_LOWER; break;
         case ASOLVE_CLS_UPPER: list = L_TRI; route = ASOLVE_ROUTE_TRI_UPPER; break;
         case ASOLVE_CLS_SYMPD: list = L_CHOL; route = ASOLVE_ROUTE_CHOL; break;
@@ -106,7 +113,8 @@ __global__ void __launch_bounds__(1024) k_route(const BatchDesc* __restrict__ dp
     if (inf.status != ASOLVE_OK || n <= 0 || n > kBatchNMax || d.nrhs[s] > kBatchRhsMax) continue;
     int list;
     switch (inf.route) {
-      case ASOLVE_ROUTE_BAND_LU: list = L_BAND; break;
+      case ASOLVE_ROUTE_BAND_LU:
+      case ASOLVE_ROUTE_TRIDIAG: list = L_BAND; break;
       case ASOLVE_ROUTE_TRI_LOWER:
       case ASOLVE_ROUTE_TRI_UPPER: list = L_TRI; break;
       case ASOLVE_ROUTE_CHOL: list = L_CHOL; break;
@@ -452,6 +460,50 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   return false;
 }
 
+// The symmetric-indefinite route (ASOLVE_SYM_INDEF): Bunch-Kaufman LDL^T
+// in FP64, solve, FP64 backward error, estimate, then the SVD decision of
+// Sec. 2.5 as for every route.
+__device__ void dense_ldlt(const BatchDesc& d, int64_t s, unsigned char* smem, CtaRed& red, int route) {
+  const int n = (int)d.n[s], nrhs = (int)d.nrhs[s];
+  const double* A = sys_A(d, s);
+  const double* B = sys_B(d, s);
+  double* X = sys_X(d, s);
+  const ScanRes sr = d.scan[s];
+  asolve_info* inf = d.info + s;
+  DenseSlot sl = dense_slot(d, n);
+  const int ldw = round4(n);
+  double* W = reinterpret_cast<double*>(sl.W);
+  copy_to_work<double>(A, n, W, ldw);
+  const int f = cta_ldlt_factor(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), red);
+  if (threadIdx.x == 0) {
+    inf->route = route;
+    inf->precision = ASOLVE_PREC_FP64;
+  }
+  const bool failed = f != 0;
+  double rc = __longlong_as_double(0x7ff8000000000000ll);
+  if (!failed) {
+    double* xd = reinterpret_cast<double*>(smem);
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) xd[e] = B[e];
+    cta_ldlt_solve(W, ldw, n, sl.piv, xd, n, nrhs);
+    for (int e = threadIdx.x; e < n * nrhs; e += blockDim.x) X[e] = xd[e];
+    __syncthreads();
+    if (d.flags & ASOLVE_BERR) {
+      const double be = berr_fp64(A, B, n, nrhs, sr.norminf, xd, sl.R, red);
+      if (threadIdx.x == 0) inf->berr = be;
+    }
+    if (!(d.flags & ASOLVE_NO_RCOND)) {
+      double* v = reinterpret_cast<double*>(smem);
+      double* xi = v + n;
+      auto apply_est = [&](double* x, bool) { cta_ldlt_solve(W, ldw, n, sl.piv, x, n, 1); };
+      const double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
+      rc = rcond_from(sr.norm1, est);
+    }
+  }
+  __syncthreads();
+  finish_primary(d, s, failed, rc, X, (int64_t)n * nrhs);
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_chol_class(const BatchDesc* __restrict__ dp) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ CtaRed red;
@@ -464,7 +516,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_chol_class(const BatchDesc* __r
     int64_t s = d.lists[(int64_t)L_CHOL * d.capacity + it];
     bool to_lu = dense_system<1>(d, s, smem, red);
     if (to_lu && threadIdx.x == 0) {
-      d.info[s].route = ASOLVE_ROUTE_CHOL_FAIL_LU;
+      // not positive definite after all (Sec. 2.3): the general solver, or
+      // with ASOLVE_SYM_INDEF the symmetric-indefinite one
+      d.info[s].route = (d.flags & ASOLVE_SYM_INDEF) ? ASOLVE_ROUTE_CHOL_FAIL_LDLT : ASOLVE_ROUTE_CHOL_FAIL_LU;
       int pos = atomicAdd(&d.list_len[L_LU], 1);
       d.lists[(int64_t)L_LU * d.capacity + pos] = (int32_t)s;
     }
@@ -482,6 +536,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_lu_class(const BatchDesc* __res
     int it = next_item(d, 8 + L_LU, &s_item);
     if (it >= len) break;
     int64_t s = d.lists[(int64_t)L_LU * d.capacity + it];
+    const int rt = d.info[s].route;
+    if (rt == ASOLVE_ROUTE_CHOL_FAIL_LDLT ||
+        (rt == ASOLVE_ROUTE_LU && (d.flags & ASOLVE_SYM_INDEF) && !(d.flags & ASOLVE_FORCE_LU) &&
+         cta_is_symmetric(sys_A(d, s), (int)d.n[s], d.sympd_tol))) {
+      dense_ldlt(d, s, smem, red, rt == ASOLVE_ROUTE_CHOL_FAIL_LDLT ? rt : ASOLVE_ROUTE_LDLT);
+      continue;
+    }
     dense_system<0>(d, s, smem, red);
   }
 }

@@ -1329,8 +1329,12 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   float* dinvL = static_cast<float*>(ar.take(sizeof(float) * inv_elems));
   float* dinvU = static_cast<float*>(ar.take(sizeof(float) * inv_elems));
   if (!Wv || !piv || !perm || !dinvL || !dinvU) return ASOLVE_E_NOMEM;
+  // the symmetric-indefinite route exists on the batched path only
+  // (n <= 1024, nrhs <= 8); here it would silently become LU
+  if ((a.flags & ASOLVE_SYM_INDEF) && n <= kBatchNMax) return info->status = ASOLVE_E_UNSUPPORTED;
   LargeReuse* kept = a.reuse;
-  constexpr uint32_t kRouteFlags = ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_NO_APPROX;
+  constexpr uint32_t kRouteFlags = ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_NO_APPROX |
+                                   ASOLVE_TRIDIAG | ASOLVE_SYM_INDEF;
   const bool reuse_hit = kept && kept->valid && kept->A == a.A && kept->n == a.n &&
                          kept->flags == (a.flags & kRouteFlags) && kept->precision >= 0;
   if (kept && !reuse_hit) kept->valid = 0;

@@ -65,7 +65,7 @@ constexpr int64_t kLargeRhsMax = 256;
 constexpr size_t kMetaBytes = 5 * sizeof(int64_t) + sizeof(asolve_info);  // per small request
 // flags that change how a system is solved (requests in one batch share them)
 constexpr uint32_t kSolverFlags =
-    ASOLVE_NO_APPROX | ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_BERR;
+    ASOLVE_NO_APPROX | ASOLVE_FORCE_LU | ASOLVE_FORCE_SVD | ASOLVE_NO_RCOND | ASOLVE_BERR | ASOLVE_TRIDIAG | ASOLVE_SYM_INDEF;
 
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
