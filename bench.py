@@ -1037,13 +1037,20 @@ def serve_workload(args):
                                 Xs[i].data_ptr(), flags)
             assert rc == 0, rc
             tickets.append(tk)
-        lat, ok, infos = [], 0, []
-        for tk in tickets:
+        lat, ok, infos, missed = [], 0, [], {}
+        for i, tk in enumerate(tickets):
             st, info, l = ctx.poll(tk, -1)
             lat.append(l)
             infos.append(info)
             if st == 0 and info["berr"] <= BERR_BAR:
                 ok += 1
+            else:  # which templates fall short of the bar, and how
+                t, info = tm[pick[i]], info or {}
+                missed.setdefault(int(pick[i]), {"kind": t["kind"], "n": t["n"], "kappa": t["kappa"],
+                                                 "status": st, "route": info.get("route"),
+                                                 "berr": info.get("berr"), "rcond": info.get("rcond"),
+                                                 "count": 0})
+                missed[int(pick[i])]["count"] += 1
         after = ctx.serve_stats()
         wall = time.perf_counter() - tstart
         busy = after["busy_ms"] - before["busy_ms"]
@@ -1055,7 +1062,8 @@ def serve_workload(args):
                 "rounds": after["rounds"] - before["rounds"],
                 "batches": after["batches"] - before["batches"],
                 "large": after["large_solves"] - before["large_solves"],
-                "peak_charged_gb": after["peak_charged_bytes"] / 1e9}
+                "peak_charged_gb": after["peak_charged_bytes"] / 1e9,
+                "unverified": list(missed.values())}
 
     points = []
     with ClockSampler(0) as clk:

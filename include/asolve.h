@@ -27,6 +27,13 @@
  *    A stream the context creates is non-blocking: it is not ordered after
  *    work on other streams, so inputs written there must be complete (or
  *    the context stream made to wait on an event) before the call.
+ *  - Test hooks for the error paths, read from the environment at each
+ *    call (no GPU fault is involved): ASOLVE_FAIL_ALLOC=1 makes the
+ *    context's workspace allocations fail as an out-of-memory would (the
+ *    call returns E_NOMEM, the context stays usable); ASOLVE_WAIT_LIMIT=p
+ *    caps the polls of the tensor-core GEMM's stage waits at p (a wait that
+ *    runs out makes a solve return E_TIMEOUT and sets asolve_gemm_sub's err
+ *    flag; the kernel still drains its tensor-core work before it exits).
  */
 #ifndef ASOLVE_H
 #define ASOLVE_H

@@ -40,11 +40,21 @@ enum KernelId { K_SCAN = 0, K_ROUTE, K_BAND, K_TRI, K_CHOL, K_LU, K_SVD, K_COUNT
 const char* kKernelNames[K_COUNT] = {"k_scan_batched", "k_route", "k_band_class", "k_tri_class",
                                      "k_chol_class", "k_lu_class", "k_svd_class"};
 
+// Allocation-failure injection for tests of the error paths (no GPU fault
+// involved): while the environment variable ASOLVE_FAIL_ALLOC is 1, every
+// workspace allocation below fails as an out-of-memory would; the call
+// returns E_NOMEM and the context stays usable.
+bool alloc_fault_injected() {
+  const char* e = getenv("ASOLVE_FAIL_ALLOC");
+  return e && e[0] == '1' && e[1] == 0;
+}
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
   cudaError_t ensure(size_t need) {
     if (need <= bytes) return cudaSuccess;
+    if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;

@@ -25,6 +25,8 @@
 // from tensor memory with tcgen05.ld (warp w owns rows 32w..32w+31) and
 // writes C - acc with coalesced stores.  Every wait is bounded: on timeout
 // the kernel raises the error flag, frees its tensor memory and returns.
+#include <stdlib.h>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -81,9 +83,22 @@ __device__ __forceinline__ void tc_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// A reduced limit (tests of the timeout path) polls with the non-blocking
+// test_wait: try_wait may itself wait for a while before it returns.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit = kSpinLimit) {
   uint32_t done = 0;
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  if (limit < kSpinLimit) {
+    for (long long it = 0; it < limit; ++it) {
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(done)
+          : "r"(mbar), "r"(parity)
+          : "memory");
+      if (done) return true;
+    }
+    return false;
+  }
+  for (long long it = 0; it < limit; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -139,7 +154,7 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 template <bool TRANS_B, bool LOWER>
 __global__ void __launch_bounds__(kTcThreads, 3)
     k_gemm_tc(float* __restrict__ C, int ldc, const float* __restrict__ A, int lda, const float* __restrict__ B,
-              int ldb, int M, int N, int K, int passes, int* err) {
+              int ldb, int M, int N, int K, int passes, int* err, long long wait_limit) {
   if (LOWER && blockIdx.y > blockIdx.x) return;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar;
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads, 3)
     if (ch + 1 < nchunks) load_chunk((ch + 1) * kTcK);  // in flight during the MMAs
     // the stage may be rewritten only after the MMAs have read it; the
     // verdict is made uniform across the block before anyone acts on it
-    const bool waited = mbar_wait(mbar_a, phase);
+    const bool waited = mbar_wait(mbar_a, phase, wait_limit);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     ok = __syncthreads_and(waited && ok) != 0;
@@ -290,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, 3)
 template <bool TRANS_B, bool LOWER, int OP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc16(float* __restrict__ C, int ldc, const float* __restrict__ A, int lda, const float* __restrict__ B,
-                int ldb, int M, int N, int K, int* err) {
+                int ldb, int M, int N, int K, int* err, long long wait_limit) {
   constexpr int kK = 64;
   constexpr uint32_t kIdesc = OP == kGemmBf16 ? kIdescBf16 : kIdescFp16;
   if (LOWER && blockIdx.y > blockIdx.x) return;
@@ -398,7 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       tc_commit(mbar_a);
     }
-    const bool waited = mbar_wait(mbar_a, phase);
+    const bool waited = mbar_wait(mbar_a, phase, wait_limit);
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     ok = __syncthreads_and(waited && ok) != 0;
@@ -445,6 +460,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// Poll limit of the stage waits: kSpinLimit, or, for tests of the timeout
+// path, the value of the environment variable ASOLVE_WAIT_LIMIT (read at
+// every launch).  A wait that runs out raises the error flag; the kernel
+// then drains its MMAs with the full limit before it frees tensor memory.
+static long long wait_limit() {
+  const char* e = getenv("ASOLVE_WAIT_LIMIT");
+  if (!e || !*e) return kSpinLimit;
+  const long long v = atoll(e);
+  return v > 0 ? v : kSpinLimit;
+}
+
 template <bool TB, bool LO, int OP>
 static cudaError_t launch_gemm_tc16_t(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M,
                                       int N, int K, int* err, cudaStream_t st) {
@@ -452,7 +478,7 @@ static cudaError_t launch_gemm_tc16_t(float* C, int ldc, const float* A, int lda
   cudaError_t e = ASV_SMEM_LIMIT_ONCE((k_gemm_tc16<TB, LO, OP>), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN);
-  k_gemm_tc16<TB, LO, OP><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, err);
+  k_gemm_tc16<TB, LO, OP><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, err, wait_limit());
   return cudaGetLastError();
 }
 
@@ -474,7 +500,7 @@ static cudaError_t launch_gemm_tc_t(float* C, int ldc, const float* A, int lda, 
   cudaError_t e = ASV_SMEM_LIMIT_ONCE((k_gemm_tc<TB, LO>), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((M + kTcM - 1) / kTcM, (N + kTcN - 1) / kTcN);
-  k_gemm_tc<TB, LO><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, passes, err);
+  k_gemm_tc<TB, LO><<<grid, kTcThreads, smem, st>>>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, wait_limit());
   return cudaGetLastError();
 }
 
