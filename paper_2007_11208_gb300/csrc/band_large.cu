@@ -732,13 +732,14 @@ bool spike_enabled() {
   return on == 1;
 }
 
-// Block length and count at attempt `level`: at least 16 (kl+ku) and 64
+// Block length and count at attempt `level`: at least 16 (kl+ku) and 128
 // rows per block (on the band workload's matrices the far tips fell below
-// 2^-60 from about 16 (kl+ku) rows), doubled at each further attempt.
+// 2^-60 from about 16 (kl+ku) rows, but not within 64 rows at kl = ku = 2),
+// doubled at each further attempt.
 bool spike_shape(int64_t n, int kl, int ku, int level, int64_t* m, int64_t* P) {
   int64_t mm = n / kSpkBlocks;
   if (mm < 16 * (int64_t)(kl + ku)) mm = 16 * (int64_t)(kl + ku);
-  if (mm < 64) mm = 64;
+  if (mm < 128) mm = 128;
   mm <<= level;
   *m = mm;
   *P = n / mm;
@@ -755,6 +756,7 @@ size_t spike_bytes(int64_t n, int kl, int ku) {
          2 * round256(sizeof(int) * (size_t)P * qq) +             // their pivots
          round256(sizeof(double) * (size_t)n) +                   // G
          round256(sizeof(double) * (size_t)P * qq) +              // Y
+         round256(sizeof(double) * (size_t)n) +                   // reciprocals of U's diagonal
          256;                                                     // far tips, flags
 }
 
@@ -765,6 +767,7 @@ struct SpikePlan {
   int* piv[2];
   double* G;
   double* Y;
+  double* rd;               // 1 / U_ii (the window solves)
   unsigned long long* far;  // [2]
   int* flags;               // [0] rows, [1] columns dominant, [2] failure
 };
@@ -789,6 +792,8 @@ SpikePlan spike_layout(double* F, int64_t ldf, int64_t n, int kl, int ku, int le
   q += round256(sizeof(double) * (size_t)n);
   pl.Y = reinterpret_cast<double*>(q);
   q += round256(sizeof(double) * (size_t)P * qq);
+  pl.rd = reinterpret_cast<double*>(q);
+  q += round256(sizeof(double) * (size_t)n);
   pl.far = reinterpret_cast<unsigned long long*>(q);
   pl.flags = reinterpret_cast<int*>(q + 64);
   return pl;
@@ -875,10 +880,163 @@ __global__ void __launch_bounds__(kSpkThreads) k_spk_step3_w(spk::Ctx c, bool tr
   spk::wsolve_step3(c, tr, b, Y, x, red + (threadIdx.x & ~31u), run);
 }
 
+// ------------------------------------------------ bands up to 32 wide
+// For kl, ku <= 32 the spike columns run by sliding windows
+// (spike_column_win, one thread each, coalesced).  From kl + ku >= 16 on
+// (spk_warp) the other steps take forms whose chains do not wait on global
+// memory: the block factorisation one phase per column (wlu_step), the
+// boundary systems and their solves one warp each, and the block solves
+// below.  Narrower bands keep the per-thread steps, which use every lane.
+bool spk_win(const spk::Ctx& c) { return c.kl <= spk::kWinMaxBand && c.ku <= spk::kWinMaxBand; }
+bool spk_wide_win(const spk::Ctx& c) { return spk_win(c) && spk::q_of(c) >= kSpkWarpQ; }
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_factor_s(spk::Ctx c, int* flags, double* rd) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;  // the whole warp
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  if (spk::wfactor_block_step(c, b, rd, run) && lane == 0) atomicExch(&flags[2], 1);
+}
+
+// rd[i] = 1 / U_ii after the per-thread or phase factorisations.
+__global__ void k_spk_rdiag(spk::Ctx c, double* rd) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < c.n; i += (int64_t)gridDim.x * blockDim.x)
+    rd[i] = 1.0 / spk::fa(c, i, i);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_spikes_win(spk::Ctx c, bool tr, double* scr, double* M,
+                                                                 unsigned long long* far, const double* rd) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < c.P * spk::q_of(c)) spk::spike_column_win(c, tr, t, scr, M, far, rd);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_boundary_w(spk::Ctx c, double* M, int* piv, int* flags) {
+  __shared__ double rv[kSpkThreads / 32][33];
+  __shared__ int ri[kSpkThreads / 32][33];
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (b + 1 >= c.P) return;  // the whole warp
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  if (spk::wfactor_boundary(c, b, M, piv, rv[w], ri[w], run) && lane == 0) atomicExch(&flags[2], 1);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_step2_w(spk::Ctx c, bool tr, const double* G, const double* M,
+                                                              const int* piv, double* Y) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b + 1 >= c.P) return;
+  auto run = [&](auto&& f) {
+    f(lane);
+    __syncwarp();
+  };
+  spk::wsolve_step2(c, tr, b, G, M, piv, Y, run);
+}
+
+// out[s..e) := A_bb^-1 in[s..e) (tr: A_bb^-T) by one warp, kl, ku <= 32.
+// The lanes hold a window of 32 partial sums in registers, lane l the row
+// l + 1 ahead of the current one (behind it, going backwards); each step
+// finishes the current row in lane 0, broadcasts it, updates the rows
+// within the bandwidth (one coalesced column of the factor for A, a gather
+// of one factor row for A^T), shifts the window by a shuffle and takes the
+// row 32 ahead into lane 31.  Row i receives its terms in the same order as
+// solve_block; the diagonal enters as the reciprocal rd (one multiply in
+// place of a division per row).  The loads of kGroup steps are issued
+// together ahead of their chain.  in and out may alias.  (A variant with
+// rotating row ownership, one shuffle fewer per step, measured slower.)
+constexpr int kGroup = 8;
+
+__device__ __forceinline__ void wsolve_win(const spk::Ctx& c, int64_t b, bool tr, const double* in, double* out,
+                                           const double* __restrict__ rd, int lane) {
+  const int64_t s = spk::blk_s(c, b), e = spk::blk_e(c, b);
+  const int bl = spk::sys_kl(c, tr), bu = spk::sys_ku(c, tr);
+  constexpr unsigned kAll = 0xffffffffu;
+  // forward: the lower factor (A: unit L; A^T: U^T, diagonal U_jj)
+  double acc = s + lane < e ? in[s + lane] : 0.0;
+  for (int64_t j0 = s; j0 < e; j0 += kGroup) {
+    double f[kGroup], nx[kGroup], rj[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t j = j0 + u, i = j + 1 + lane;
+      f[u] = (j < e && lane < bl && i < e) ? spk::blkf(c, tr, i, j) : 0.0;
+      nx[u] = (lane == 31 && j + 32 < e) ? in[j + 32] : 0.0;
+      rj[u] = (tr && j < e) ? rd[j] : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t j = j0 + u;
+      if (j >= e) break;
+      const double yj = __shfl_sync(kAll, (tr && lane == 0) ? acc * rj[u] : acc, 0);
+      if (lane == 0) out[j] = yj;
+      acc = __shfl_down_sync(kAll, acc, 1);
+      if (lane == 31) acc = nx[u];
+      if (lane < bl && j + 1 + lane < e) acc -= f[u] * yj;
+    }
+  }
+  __syncwarp();
+  // backward: the upper factor (A: U, diagonal U_jj; A^T: unit L^T)
+  acc = e - 1 - lane >= s ? out[e - 1 - lane] : 0.0;
+  for (int64_t j0 = e - 1; j0 >= s; j0 -= kGroup) {
+    double f[kGroup], nx[kGroup], rj[kGroup];
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t j = j0 - u, i = j - 1 - lane;
+      f[u] = (j >= s && lane < bu && i >= s) ? spk::blkf(c, tr, i, j) : 0.0;
+      nx[u] = (lane == 31 && j - 32 >= s) ? out[j - 32] : 0.0;
+      rj[u] = (!tr && j >= s) ? rd[j] : 1.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kGroup; ++u) {
+      const int64_t j = j0 - u;
+      if (j < s) break;
+      const double xj = __shfl_sync(kAll, (!tr && lane == 0) ? acc * rj[u] : acc, 0);
+      if (lane == 0) out[j] = xj;
+      acc = __shfl_down_sync(kAll, acc, 1);
+      if (lane == 31) acc = nx[u];
+      if (lane < bu && j - 1 - lane >= s) acc -= f[u] * xj;
+    }
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_step1_r(spk::Ctx c, bool tr, const double* x, double* G,
+                                                              const double* rd) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;
+  wsolve_win(c, b, tr, x, G, rd, lane);
+}
+
+__global__ void __launch_bounds__(kSpkThreads) k_spk_step3_r(spk::Ctx c, bool tr, const double* Y, double* x,
+                                                              const double* rd) {
+  const int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (b >= c.P) return;
+  spk::step3_couplings(c, tr, b, Y, x, lane);
+  __syncwarp();
+  wsolve_win(c, b, tr, x, x, rd, lane);
+}
+
 // x := A^-1 x (tr: A^-T x) in place with the partitioned factors.
 int spike_apply(const SpikePlan& pl, double* x, bool tr, cudaStream_t st) {
   const spk::Ctx& c = pl.c;
   const int k = tr ? 1 : 0;
+  if (spk_wide_win(c)) {
+    k_spk_step1_r<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G, pl.rd);
+    BCK(cudaGetLastError());
+    if (spk::q_of(c) > 0) {
+      k_spk_step2_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, pl.G, pl.M[k], pl.piv[k], pl.Y);
+      BCK(cudaGetLastError());
+    }
+    k_spk_step3_r<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, pl.Y, x, pl.rd);
+    BCK(cudaGetLastError());
+    return ASOLVE_OK;
+  }
   const bool w = spk_warp(c);
   if (w) k_spk_step1_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
   else k_spk_step1<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, tr, x, pl.G);
@@ -945,15 +1103,25 @@ int spike_prepare(const SpikePlan& pl, bool no_rcond, int* out, bool* touched, c
   if (!h[0] && !h[1]) return ASOLVE_OK;
   *touched = true;
   *out = SPK_NUMERIC;
-  if (spk_warp(c)) k_spk_factor_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, pl.flags);
+  const bool win = spk_wide_win(c);
+  if (win) k_spk_factor_s<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, pl.flags, pl.rd);
+  else if (spk_warp(c)) k_spk_factor_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, pl.flags);
   else k_spk_factor<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.flags);
   BCK(cudaGetLastError());
+  if (!win && spk_win(c)) {  // the window spikes take the diagonal's reciprocals
+    k_spk_rdiag<<<4 * 152, 256, 0, st>>>(c, pl.rd);
+    BCK(cudaGetLastError());
+  }
   const int64_t q = spk::q_of(c);
   for (int k = 0; k < (no_rcond ? 1 : 2) && q > 0; ++k) {
     BCK(cudaMemsetAsync(pl.M[k], 0, sizeof(double) * (size_t)(c.P * q * q), st));
-    k_spk_spikes<<<spk_grid(c.P * q), kSpkThreads, 0, st>>>(c, k == 1, pl.scr, pl.M[k], pl.far + k);
+    if (spk_win(c))
+      k_spk_spikes_win<<<spk_grid(c.P * q), kSpkThreads, 0, st>>>(c, k == 1, pl.scr, pl.M[k], pl.far + k, pl.rd);
+    else
+      k_spk_spikes<<<spk_grid(c.P * q), kSpkThreads, 0, st>>>(c, k == 1, pl.scr, pl.M[k], pl.far + k);
     BCK(cudaGetLastError());
-    k_spk_boundary<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.M[k], pl.piv[k], pl.flags);
+    if (win) k_spk_boundary_w<<<spk_grid(32 * c.P), kSpkThreads, 0, st>>>(c, pl.M[k], pl.piv[k], pl.flags);
+    else k_spk_boundary<<<spk_grid(c.P), kSpkThreads, 0, st>>>(c, pl.M[k], pl.piv[k], pl.flags);
     BCK(cudaGetLastError());
   }
   unsigned long long fb[2];

@@ -56,6 +56,20 @@ SPK_HD int64_t imin(int64_t a, int64_t b) { return a < b ? a : b; }
 SPK_HD int64_t imax(int64_t a, int64_t b) { return a > b ? a : b; }
 SPK_HD double dabs(double v) { return v < 0.0 ? -v : v; }
 
+// Tests on a double's bits, for the inner loops: on this GPU an FP64
+// comparison issues on the (narrow) FP64 pipe, an integer test does not.
+SPK_HD uint64_t dbits(double v) {
+#ifdef __CUDA_ARCH__
+  return (uint64_t)__double_as_longlong(v);
+#else
+  uint64_t b;
+  memcpy(&b, &v, sizeof(b));
+  return b;
+#endif
+}
+SPK_HD bool nonzero(double v) { return (dbits(v) << 1) != 0; }                            // v != 0 (NaN: true)
+SPK_HD bool zero_or_nan(double v) { return (dbits(v) << 1) == 0 || (dbits(v) << 1) > (0x7ff0000000000000ull << 1); }
+
 SPK_HD double& fa(const Ctx& c, int64_t i, int64_t j) {
   return c.F[(size_t)(c.kl + c.ku + i - j) + (size_t)j * (size_t)c.ldf];
 }
@@ -370,6 +384,34 @@ SPK_HD void wsolve_block(const Ctx& c, int64_t b, bool tr, double* xl, double* r
   }
 }
 
+// Step 3's couplings with the neighbours' boundary unknowns, rows split
+// over the lanes (only rows within kl' of the block's start or ku' of its
+// end are reached).
+SPK_HD void step3_couplings(const Ctx& c, bool tr, int64_t b, const double* Y, double* x, int lane) {
+  const int64_t q = q_of(c);
+  const int kl = sys_kl(c, tr), ku = sys_ku(c, tr);
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  for (int64_t i = s + lane; i < e; i += 32) {
+    if (i < e - ku && i >= s + kl) {  // skip to the rows the couplings reach
+      const int64_t nxt = e - ku > s + kl ? e - ku : s + kl;
+      i += ((nxt - i + 31) / 32 - 1) * 32;
+      continue;
+    }
+    double t = x[i];
+    if (b + 1 < c.P)
+      for (int r = 0; r < ku; ++r) {
+        const int64_t J = e + r;
+        if (i >= J - ku) t -= sys_at(c, tr, i, J) * Y[(size_t)b * (size_t)q + kl + r];
+      }
+    if (b > 0)
+      for (int r = 0; r < kl; ++r) {
+        const int64_t J = s - kl + r;
+        if (i <= J + kl) t -= sys_at(c, tr, i, J) * Y[(size_t)(b - 1) * (size_t)q + r];
+      }
+    x[i] = t;
+  }
+}
+
 // Solve steps 1 and 3 with one warp per block (steps 2 is per boundary).
 #ifdef __CUDACC__
 #pragma nv_exec_check_disable
@@ -388,28 +430,252 @@ SPK_HD void wsolve_step1(const Ctx& c, bool tr, int64_t b, const double* x, doub
 #endif
 template <class Run>
 SPK_HD void wsolve_step3(const Ctx& c, bool tr, int64_t b, const double* Y, double* x, double* red, Run&& run) {
+  run([&](int lane) { step3_couplings(c, tr, b, Y, x, lane); });
+  wsolve_block(c, b, tr, x + blk_s(c, b), red, run);
+}
+
+// ------------------------------------------------------- sliding windows
+// Spike columns for bandwidths kl', ku' <= 32, in dot-product form over a
+// circular window of the last kWin unknowns computed (a per-thread array:
+// local memory on the GPU, where one index across the 32 lanes is one
+// contiguous line, so every access is coalesced and stays in L1).  Only
+// what the route needs is kept: V's near tip (bottom kl' rows) goes to M and
+// its far tip (top ku' rows) into *far, and V's forward values live in the
+// window alone (the right-hand side starts at most ku' rows above the
+// block's end).  W's forward values are stored once, lane-interleaved in the
+// scratch area (row i of column r at (i - s) q + r), for its backward pass.
+constexpr int kWin = 64;
+constexpr int kWinMaxBand = 32;
+
+// Entry (i, j), i != j, of the system's block factors: for A the unit-lower
+// L and the upper U (fa(i, j)); for A^T = U^T L^T the lower U^T and the
+// unit-upper L^T (fa(j, i)).
+SPK_HD double blkf(const Ctx& c, bool tr, int64_t i, int64_t j) { return tr ? fa(c, j, i) : fa(c, i, j); }
+
+// Forward row i of the lower factor: (rhs - sum over j in [max(lo0, i-bl), i)
+// of L'(i, j) w_j) / d_i, d_i = 1 for A (unit L), U_ii for A^T; the
+// division is a product with rd_i = 1 / U_ii.
+SPK_HD double fwd_row(const Ctx& c, bool tr, int64_t i, int64_t lo0, int bl, double rhs, const double* w,
+                      const double* rd) {
+  double t = rhs;
+  const int64_t j0 = imax(lo0, i - bl);
+  const int cnt = (int)(i - j0);
+  // L'(i, j0 + k): for A fa(i, j) (stride ldf - 1 in j), for A^T fa(j, i) (stride 1)
+  const double* f = tr ? &fa(c, j0, i) : &fa(c, i, j0);
+  const int st = tr ? 1 : (int)c.ldf - 1;
+  int wi = (int)(j0 & (kWin - 1));
+  for (int k = 0, o = 0; k < cnt; ++k, o += st, wi = (wi + 1) & (kWin - 1)) t -= f[o] * w[wi];
+  return tr ? t * rd[i] : t;
+}
+// Backward row i of the upper factor: (y - sum over j in (i, min(hi0, i+bu)]
+// of U'(i, j) w_j) / d_i, d_i = U_ii for A, 1 for A^T (unit L^T).
+SPK_HD double bwd_row(const Ctx& c, bool tr, int64_t i, int64_t hi0, int bu, double y, const double* w,
+                      const double* rd) {
+  double t = y;
+  const int cnt = (int)(imin(hi0, i + bu) - i);
+  // U'(i, i + 1 + k): for A fa(i, j) (stride ldf - 1 in j), for A^T fa(j, i) (stride 1)
+  const double* f = tr ? &fa(c, i + 1, i) : &fa(c, i, i + 1);
+  const int st = tr ? 1 : (int)c.ldf - 1;
+  int wi = (int)((i + 1) & (kWin - 1));
+  for (int k = 0, o = 0; k < cnt; ++k, o += st, wi = (wi + 1) & (kWin - 1)) t -= f[o] * w[wi];
+  return tr ? t : t * rd[i];
+}
+
+// One spike column per thread, t in [0, P q), as spike_column, with the
+// window solves above; rd: the reciprocals of the blocks' U diagonals.
+SPK_HD void spike_column_win(const Ctx& c, bool tr, int64_t t, double* scr, double* M, unsigned long long* far,
+                             const double* rd) {
   const int64_t q = q_of(c);
+  const int64_t b = t / q;
+  const int r = (int)(t % q);
   const int kl = sys_kl(c, tr), ku = sys_ku(c, tr);
   const int64_t s = blk_s(c, b), e = blk_e(c, b);
-  // couplings with the neighbours' boundary unknowns: rows split over lanes
-  run([&](int lane) {
-    for (int64_t i = s + lane; i < e; i += 32) {
-      if (i < e - ku && i >= s + kl) continue;  // rows no coupling reaches
-      double t = x[i];
-      if (b + 1 < c.P)
-        for (int r = 0; r < ku; ++r) {
-          const int64_t J = e + r;
-          if (i >= J - ku) t -= sys_at(c, tr, i, J) * Y[(size_t)b * (size_t)q + kl + r];
-        }
-      if (b > 0)
-        for (int r = 0; r < kl; ++r) {
-          const int64_t J = s - kl + r;
-          if (i <= J + kl) t -= sys_at(c, tr, i, J) * Y[(size_t)(b - 1) * (size_t)q + r];
-        }
-      x[i] = t;
+  double w[kWin];
+  double fm = 0.0;
+  if (r < ku) {  // V_b column r: column J = e + r (block b+1); right-hand side rows [i0, e)
+    if (b + 1 >= c.P) return;
+    const int64_t J = e + r, i0 = imax(s, J - ku);
+    for (int64_t i = i0; i < e; ++i) w[i & (kWin - 1)] = fwd_row(c, tr, i, i0, kl, sys_at(c, tr, i, J), w, rd);
+    double* Mb = M + (size_t)b * (size_t)(q * q);  // boundary b: [x_b^B (kl'); x_{b+1}^T (ku')]
+    for (int64_t i = e - 1; i >= s; --i) {
+      const double v = bwd_row(c, tr, i, e - 1, ku, i >= i0 ? w[i & (kWin - 1)] : 0.0, w, rd);
+      w[i & (kWin - 1)] = v;
+      if (i >= e - kl) Mb[(i - (e - kl)) + (size_t)(kl + r) * q] = v;
+      if (i < s + ku) fm = fm < dabs(v) ? dabs(v) : fm;
     }
+  } else {  // W_b column r - ku': column J = s - kl' + (r - ku') (block b-1); right-hand side rows [s, i1)
+    if (b == 0) return;
+    const int cc = r - ku;
+    const int64_t J = s - kl + cc, i1 = imin(e, J + kl + 1);
+    double* ys = scr + (size_t)s * (size_t)q + (size_t)r;
+    for (int64_t i = s; i < e; ++i) {
+      const double v = fwd_row(c, tr, i, s, kl, i < i1 ? sys_at(c, tr, i, J) : 0.0, w, rd);
+      w[i & (kWin - 1)] = v;
+      ys[(size_t)(i - s) * (size_t)q] = v;
+    }
+    double* Mb = M + (size_t)(b - 1) * (size_t)(q * q);  // boundary b-1
+    for (int64_t i = e - 1; i >= s; --i) {
+      const double v = bwd_row(c, tr, i, e - 1, ku, ys[(size_t)(i - s) * (size_t)q], w, rd);
+      w[i & (kWin - 1)] = v;
+      if (i >= e - kl) fm = fm < dabs(v) ? dabs(v) : fm;
+      if (i < s + ku) Mb[(kl + (i - s)) + (size_t)cc * q] = v;
+    }
+  }
+  max_bits(far, fm);
+}
+
+// Block factorisation by one warp, one phase per column j: lane l takes row
+// i = j + 1 + l (kl <= 32), forms its multiplier with the pivot's
+// reciprocal rd[j] and updates its row from the pivot row j, which no lane
+// writes in that phase; the lane that finishes row j + 1 (lane 0) then
+// forms rd[j + 1].  The loads of a row are issued together before any of
+// its stores.
+SPK_HD void wlu_step(const Ctx& c, int64_t e, int64_t j, int lane, double* rd) {
+  const int64_t i = j + 1 + lane;
+  if (i <= imin(e - 1, j + c.kl)) {
+    const double l = fa(c, i, j) * rd[j];
+    fa(c, i, j) = l;
+    if (nonzero(l)) {
+      const int cnt = (int)(imin(e - 1, j + c.ku) - j);  // columns j+1 .. j+cnt
+      // rows j and i from column j + 1 on: stride ldf - 1 per column
+      const double* pu = &fa(c, j, j + 1);
+      double* pa = &fa(c, i, j + 1);
+      const int st = (int)c.ldf - 1;
+      double u[kWinMaxBand], a[kWinMaxBand];
+      for (int k = 0; k < kWinMaxBand; ++k)
+        if (k < cnt) {
+          u[k] = pu[k * st];
+          a[k] = pa[k * st];
+        }
+      for (int k = 0; k < kWinMaxBand; ++k)
+        if (k < cnt && nonzero(u[k])) pa[k * st] = a[k] - l * u[k];
+    }
+  }
+  if (lane == 0 && i < e) rd[i] = 1.0 / fa(c, i, i);  // row j + 1 is final
+}
+
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD int wfactor_block_step(const Ctx& c, int64_t b, double* rd, Run&& run) {
+  const int64_t s = blk_s(c, b), e = blk_e(c, b);
+  run([&](int lane) {
+    if (lane == 0) rd[s] = 1.0 / fa(c, s, s);
   });
-  wsolve_block(c, b, tr, x + s, red, run);
+  for (int64_t j = s; j < e; ++j) {
+    // final after the previous phase; uniform across the lanes
+    if (zero_or_nan(fa(c, j, j))) return (int)(j - s) + 1;
+    run([&](int lane) { wlu_step(c, e, j, lane, rd); });
+  }
+  return 0;
+}
+
+// Boundary system b by one warp (lanes over rows, then over columns for the
+// interchange): M += I, then LU with partial pivoting, the first largest
+// |a| as in factor_boundary.  rv, ri: 33 entries of per-warp scratch.
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD int wfactor_boundary(const Ctx& c, int64_t b, double* M, int* ipiv, double* rv, int* ri, Run&& run) {
+  const int64_t q = q_of(c);
+  double* A = M + (size_t)b * (size_t)(q * q);
+  int* pv = ipiv + (size_t)b * (size_t)q;
+  run([&](int lane) {
+    for (int64_t i = lane; i < q; i += 32) A[i + i * q] += 1.0;
+  });
+  for (int64_t j = 0; j < q; ++j) {
+    run([&](int lane) {  // the first largest |a| among this lane's rows
+      double best = -1.0;
+      int at = -1;
+      for (int64_t i = j + lane; i < q; i += 32)
+        if (dabs(A[i + j * q]) > best) {
+          best = dabs(A[i + j * q]);
+          at = (int)i;
+        }
+      rv[lane] = best;
+      ri[lane] = at;
+    });
+    run([&](int lane) {  // lane 0: the largest over the lanes, ties to the first row
+      if (lane != 0) return;
+      double best = -1.0;
+      int at = -1;
+      for (int k = 0; k < 32; ++k)
+        if (ri[k] >= 0 && (rv[k] > best || (rv[k] == best && ri[k] < at))) {
+          best = rv[k];
+          at = ri[k];
+        }
+      rv[32] = best;
+      ri[32] = at;
+      pv[j] = at;
+    });
+    const double best = rv[32];
+    const int64_t p = ri[32];
+    if (!(best > 0.0)) return (int)j + 1;
+    if (p != j)
+      run([&](int lane) {
+        for (int64_t k = lane; k < q; k += 32) {
+          const double tmp = A[j + k * q];
+          A[j + k * q] = A[p + k * q];
+          A[p + k * q] = tmp;
+        }
+      });
+    run([&](int lane) {  // rows below the pivot: multiplier and row update
+      const double d = A[j + j * q];
+      for (int64_t i = j + 1 + lane; i < q; i += 32) {
+        const double l = A[i + j * q] / d;
+        A[i + j * q] = l;
+        for (int64_t k = j + 1; k < q; ++k) {
+          const double u = A[j + k * q];
+          if (nonzero(u)) A[i + k * q] -= l * u;
+        }
+      }
+    });
+  }
+  return 0;
+}
+
+// Solve step 2 by one warp per boundary (as solve_step2; u in Y).
+#ifdef __CUDACC__
+#pragma nv_exec_check_disable
+#endif
+template <class Run>
+SPK_HD void wsolve_step2(const Ctx& c, bool tr, int64_t b, const double* G, const double* M, const int* ipiv,
+                         double* Y, Run&& run) {
+  const int64_t q = q_of(c);
+  const int kl = sys_kl(c, tr), ku = sys_ku(c, tr);
+  const double* A = M + (size_t)b * (size_t)(q * q);
+  const int* pv = ipiv + (size_t)b * (size_t)q;
+  double* u = Y + (size_t)b * (size_t)q;
+  const int64_t e = blk_e(c, b), s1 = blk_s(c, b + 1);
+  run([&](int lane) {
+    for (int i = lane; i < kl; i += 32) u[i] = G[e - kl + i];
+    for (int i = lane; i < ku; i += 32) u[kl + i] = G[s1 + i];
+  });
+  for (int64_t j = 0; j < q; ++j) {  // P, then unit L
+    const int64_t p = pv[j];
+    if (p != j)
+      run([&](int lane) {
+        if (lane != 0) return;
+        const double tmp = u[j];
+        u[j] = u[p];
+        u[p] = tmp;
+      });
+    run([&](int lane) {
+      const double uj = u[j];
+      for (int64_t i = j + 1 + lane; i < q; i += 32) u[i] -= A[i + j * q] * uj;
+    });
+  }
+  for (int64_t j = q - 1; j >= 0; --j) {  // U
+    run([&](int lane) {
+      if (lane == 0) u[j] = u[j] / A[j + j * q];
+    });
+    run([&](int lane) {
+      const double uj = u[j];
+      for (int64_t i = lane; i < j; i += 32) u[i] -= A[i + j * q] * uj;
+    });
+  }
 }
 
 // Diagonal dominance of the original matrix in F (before any factoring):

@@ -22,7 +22,7 @@ auto lanes = [](auto&& f) {
 };
 
 void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::vector<int>& piv, double* x,
-               bool warp) {
+               bool warp, bool win) {
   const int64_t q = q_of(c);
   std::vector<double> G((size_t)c.n), Y((size_t)(c.P * (q > 0 ? q : 1)));
   double red[32];
@@ -30,7 +30,9 @@ void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::v
     if (warp) wsolve_step1(c, tr, b, x, G.data(), red, lanes);
     else solve_step1(c, tr, b, x, G.data());
   if (q > 0)
-    for (int64_t b = 0; b + 1 < c.P; ++b) solve_step2(c, tr, b, G.data(), M.data(), piv.data(), Y.data());
+    for (int64_t b = 0; b + 1 < c.P; ++b)
+      if (win) wsolve_step2(c, tr, b, G.data(), M.data(), piv.data(), Y.data(), lanes);
+      else solve_step2(c, tr, b, G.data(), M.data(), piv.data(), Y.data());
   for (int64_t b = 0; b < c.P; ++b)
     if (warp) wsolve_step3(c, tr, b, Y.data(), x, red, lanes);
     else solve_step3(c, tr, b, Y.data(), x);
@@ -43,12 +45,17 @@ void solve_sys(const Ctx& c, bool tr, const std::vector<double>& M, const std::v
 // far-tip entry for A and for A^T; dom[0], dom[1]: dominance by rows / by
 // columns.  warp: the one-warp-per-block factorisation and block solves
 // (lanes run phase by phase; 2: lanes in decreasing order) instead of one
-// thread per block.  Returns 0,
+// thread per block; 3 (4: lanes in decreasing order): the routines of the
+// route for bands up to 32 wide -- window spike columns, the one-phase-per-
+// column block factorisation, the boundary systems and their solves by one
+// warp (the block solves, whose GPU form uses warp shuffles, as in mode 1).
+// Returns 0,
 // -1 - b if block b has a zero pivot, -1000 - b if boundary system b is
 // singular.
 extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, int64_t n, int64_t m,
                                 const double* bvec, double* x, double* xt, double* far, int* dom, int warp) {
-  g_reverse = warp == 2;
+  g_reverse = warp == 2 || warp == 4;
+  const bool win = warp >= 3;
   const int64_t ldf = 2 * (int64_t)kl + ku + 1, kv = (int64_t)kl + ku;
   std::vector<double> F((size_t)(ldf * n), 0.0);
   for (int64_t j = 0; j < n; ++j)
@@ -62,8 +69,12 @@ extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, 
     dom[0] &= r;
     dom[1] &= cc;
   }
+  std::vector<double> rd((size_t)n);
   for (int64_t b = 0; b < c.P; ++b)
-    if (warp ? wfactor_block(c, b, lanes) : factor_block(c, b)) return (int)(-1 - b);
+    if (win ? wfactor_block_step(c, b, rd.data(), lanes) : warp ? wfactor_block(c, b, lanes) : factor_block(c, b))
+      return (int)(-1 - b);
+  if (!win)
+    for (int64_t i = 0; i < n; ++i) rd[(size_t)i] = 1.0 / F[(size_t)(kv + i * ldf)];
   const int64_t q = q_of(c);
   std::vector<double> scr((size_t)(n * (q > 0 ? q : 1)));
   std::vector<double> M[2];
@@ -72,14 +83,20 @@ extern "C" int spike_host_solve(const double* AB, int64_t ldab, int kl, int ku, 
     M[tr].assign((size_t)(c.P * q * q + 1), 0.0);
     piv[tr].assign((size_t)(c.P * q + 1), 0);
     unsigned long long fb = 0;
-    for (int64_t t = 0; t < c.P * q; ++t) spike_column(c, tr != 0, t, scr.data(), M[tr].data(), &fb);
+    for (int64_t t = 0; t < c.P * q; ++t)
+      if (win) spike_column_win(c, tr != 0, t, scr.data(), M[tr].data(), &fb, rd.data());
+      else spike_column(c, tr != 0, t, scr.data(), M[tr].data(), &fb);
     memcpy(&far[tr], &fb, sizeof(double));
+    double rv[33];
+    int ri[33];
     for (int64_t b = 0; b + 1 < c.P; ++b)
-      if (q > 0 && factor_boundary(c, b, M[tr].data(), piv[tr].data())) return (int)(-1000 - b);
+      if (q > 0 && (win ? wfactor_boundary(c, b, M[tr].data(), piv[tr].data(), rv, ri, lanes)
+                        : factor_boundary(c, b, M[tr].data(), piv[tr].data())))
+        return (int)(-1000 - b);
   }
   memcpy(x, bvec, sizeof(double) * (size_t)n);
   memcpy(xt, bvec, sizeof(double) * (size_t)n);
-  solve_sys(c, false, M[0], piv[0], x, warp != 0);
-  solve_sys(c, true, M[1], piv[1], xt, warp != 0);
+  solve_sys(c, false, M[0], piv[0], x, warp != 0, win);
+  solve_sys(c, true, M[1], piv[1], xt, warp != 0, win);
   return 0;
 }

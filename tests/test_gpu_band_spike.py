@@ -29,6 +29,7 @@ def ctx():
 
 @pytest.mark.parametrize("n,kl,ku,nrhs", [(20011, 3, 4, 5), (100000, 2, 2, 1), (100000, 8, 8, 3),
                                           (100000, 32, 32, 1), (65537, 0, 6, 2), (65537, 5, 0, 2),
+                                          (77777, 31, 17, 2), (40000, 1, 1, 1), (50001, 33, 3, 1),
                                           (1000000, 8, 8, 2)])
 def test_dominant_bands_take_the_partitioned_route(ctx, orc, n, kl, ku, nrhs):
     from paper_2007_11208_gb300 import asolve

@@ -78,7 +78,7 @@ def check(orc, AB, kl, ku, x, xt, b):
 @pytest.mark.parametrize("n,kl,ku,m", [(3000, 2, 2, 300), (3000, 8, 8, 375), (3000, 32, 32, 750),
                                        (2500, 3, 0, 250), (2500, 0, 5, 250), (2000, 7, 2, 333),
                                        (1999, 1, 9, 401)])
-@pytest.mark.parametrize("warp", [False, True])
+@pytest.mark.parametrize("warp", [0, 1, 3])
 def test_row_dominant_bands_against_oracle(orc, shim, n, kl, ku, m, warp):
     AB = row_dominant(n, kl, ku, n + kl)
     b = np.random.default_rng(kl + 10 * ku).standard_normal(n)
@@ -109,10 +109,11 @@ def test_column_dominant_band(orc, shim):
         j = np.arange(max(0, -d), min(n, n - d))
         AB[r, j] = A[j + d, j]
     b = rng.standard_normal(n)
-    rc, x, xt, far, dom = run(shim, AB, kl, ku, 300, b, warp=True)
-    assert rc == 0 and dom[1] == 1
-    assert far.max() < 1e-20, far
-    check(orc, AB, kl, ku, x, xt, b)
+    for warp in (1, 3):
+        rc, x, xt, far, dom = run(shim, AB, kl, ku, 300, b, warp=warp)
+        assert rc == 0 and dom[1] == 1
+        assert far.max() < 1e-20, far
+        check(orc, AB, kl, ku, x, xt, b)
 
 
 def test_far_tips_flag_short_blocks(shim):
@@ -121,10 +122,11 @@ def test_far_tips_flag_short_blocks(shim):
     n, k = 2000, 8
     AB = row_dominant(n, k, k, 3)
     b = np.ones(n)
-    rc, x, xt, far, dom = run(shim, AB, k, k, 40, b)
-    assert rc == 0 and far.max() > 1e-12, far
-    rc, x, xt, far, dom = run(shim, AB, k, k, 500, b)
-    assert rc == 0 and far.max() < 1e-20, far
+    for warp in (0, 3):
+        rc, x, xt, far, dom = run(shim, AB, k, k, 40, b, warp)
+        assert rc == 0 and far.max() > 1e-12, far
+        rc, x, xt, far, dom = run(shim, AB, k, k, 500, b, warp)
+        assert rc == 0 and far.max() < 1e-20, far
 
 
 def test_zero_pivot_reports_the_block(shim):
@@ -132,8 +134,9 @@ def test_zero_pivot_reports_the_block(shim):
     AB = row_dominant(n, k, k, 4)
     AB[k, 450] = 0.0  # column 450: block 3 (0-based) of 4, m = 150
     AB[:, 450] = 0.0
-    rc, *_ = run(shim, AB, k, k, 150, np.ones(n))
-    assert rc == -1 - 3
+    for warp in (0, 3):
+        rc, *_ = run(shim, AB, k, k, 150, np.ones(n), warp)
+        assert rc == -1 - 3
 
 
 def test_warp_and_thread_routines_agree(shim):
@@ -149,16 +152,17 @@ def test_warp_and_thread_routines_agree(shim):
     assert np.abs(r1[2] - r2[2]).max() <= 1e-14 * np.abs(r1[2]).max()
 
 
-@pytest.mark.parametrize("kl,ku", [(20, 20), (40, 5), (3, 37), (70, 70)])
-def test_warp_phases_do_not_depend_on_lane_order(shim, kl, ku):
+@pytest.mark.parametrize("kl,ku,mode", [(20, 20, 1), (40, 5, 1), (3, 37, 1), (70, 70, 1),
+                                        (20, 20, 3), (32, 32, 3), (31, 2, 3), (1, 30, 3)])
+def test_warp_phases_do_not_depend_on_lane_order(shim, kl, ku, mode):
     """Within a phase no lane reads what another lane writes: running the
     lanes of every phase in the opposite order gives the same bits."""
     n = 4000
     AB = row_dominant(n, kl, ku, kl + ku)
     b = np.random.default_rng(kl).standard_normal(n)
     m = max(16 * (kl + ku), 256)
-    fwd = run(shim, AB, kl, ku, m, b, warp=1)
-    rev = run(shim, AB, kl, ku, m, b, warp=2)
+    fwd = run(shim, AB, kl, ku, m, b, warp=mode)
+    rev = run(shim, AB, kl, ku, m, b, warp=mode + 1)
     assert fwd[0] == rev[0] == 0
     assert np.array_equal(fwd[1], rev[1]) and np.array_equal(fwd[2], rev[2])
 
@@ -175,3 +179,18 @@ def test_dominance_flags_refuse_a_plain_random_band(shim):
     AB[k, 1234] *= 0.5  # one row loses its dominance
     rc, x, xt, far, dom = run(shim, AB, k, k, 300, np.ones(n))
     assert dom[0] == 0
+
+
+@pytest.mark.parametrize("n,kl,ku,m", [(4000, 32, 32, 1024), (3001, 17, 9, 433), (2600, 1, 1, 130)])
+def test_window_routines_against_oracle_and_the_per_thread_ones(orc, shim, n, kl, ku, m):
+    """The bands-up-to-32 routines (window spikes, per-column block
+    factorisation, one warp per boundary system) against the oracle, and
+    their boundary systems' far tips against the per-thread routines'."""
+    AB = row_dominant(n, kl, ku, n + kl + 3)
+    b = np.random.default_rng(n).standard_normal(n)
+    r0 = run(shim, AB, kl, ku, m, b, 0)
+    r3 = run(shim, AB, kl, ku, m, b, 3)
+    assert r0[0] == r3[0] == 0
+    check(orc, AB, kl, ku, r3[1], r3[2], b)
+    assert np.abs(r0[1] - r3[1]).max() <= 1e-13 * np.abs(r0[1]).max()
+    assert np.abs(r0[3] - r3[3]).max() <= 1e-6 * np.abs(r0[3]).max() + 1e-300, (r0[3], r3[3])
