@@ -257,12 +257,17 @@ def large_case_roofline(kind, prec, n, nrhs, ms, peaks):
     the triangular route at the FP64 pipe rate measured on this GPU (the
     larger of the DFMA and mma.sync f64 probes); the mixed path's trailing updates at the 3xTF32 rate
     (three TF32 products, TF32 = half the measured bf16 burst rate); the
-    BF16 / FP16 updates at the measured bf16 burst rate."""
+    BF16 / FP16 updates at the measured bf16 burst rate; the Ozaki-split
+    FP64 updates (FP64_OZ mode, and the triangular route's blocked updates
+    from 32 right-hand sides in every mode but FP64) at the bf16 burst rate
+    / 28, the slice products per FP64 product."""
     flops = {"general": 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs,
              "spd": 1.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs,
              "lower": float(n) * n * nrhs}[kind]
     bf16 = peaks["bf16_tflops"] * 1e12
-    if kind == "lower" or prec == "fp64":
+    if prec == "fp64_oz" or (kind == "lower" and prec != "fp64" and nrhs >= 32):
+        peak, unit_src = bf16 / 28.0, f"Ozaki split: bf16 {peaks['src']} / 28"
+    elif kind == "lower" or prec == "fp64":
         p32, pdfma, pdmma, src = pipe_peaks()
         peak, unit_src = max(pdfma, pdmma), "FP64 pipe, " + src
     elif prec == "mixed":
@@ -596,7 +601,7 @@ def large_workload(args):
     kinds = args.kinds.split(",")
     nrhs_list = [int(x) for x in args.nrhs_list.split(",")]
     precs = [(asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64"), (asolve.PREC_BF16, "bf16"),
-             (asolve.PREC_FP16, "fp16")]
+             (asolve.PREC_FP16, "fp16"), (asolve.PREC_FP64_OZ, "fp64_oz")]
     precs = [p for p in precs if p[1] in args.precs.split(",")]
     ctxs = {p: asolve.Context(precision=p) for p, _ in precs}
     peaks = load_peaks()
@@ -1119,7 +1124,7 @@ def main():
     ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds (general, spd, lower)")
     ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
     ap.add_argument("--nrhs-list", default="1,64", help="large: right-hand-side counts")
-    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions (mixed, fp64, bf16, fp16)")
+    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions (mixed, fp64, bf16, fp16, fp64_oz)")
     ap.add_argument("--templates", type=int, default=40, help="serve: distinct request matrices")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests per load point")
     ap.add_argument("--load", default="0.25,0.5,0.8", help="serve: arrival rates as fractions of capacity")

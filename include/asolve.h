@@ -97,6 +97,13 @@ extern "C" {
                                    n <= 1024 factor in FP32 as with MIXED */
 #define ASOLVE_PREC_FP16    3   /* as BF16 with FP16 operands (per-tile power-of-two
                                    scaling); gate ir_kappa_limit capped at 1e4 */
+#define ASOLVE_PREC_FP64_OZ 4   /* FP64 factorisations as ASOLVE_PREC_FP64, but on large dense
+                                   systems (n > 1024) the trailing updates and the blocked
+                                   triangular-solve updates are FP64-accurate Ozaki-split
+                                   products on the BF16 tensor cores (asolve_gemm_oz); the
+                                   FP64 re-factorisations of the mixed modes' large systems
+                                   use the same products.  asolve_info.precision reports
+                                   ASOLVE_PREC_FP64 and detail bit 6 (64) */
 
 /* ---- flags ----------------------------------------------------------- */
 #define ASOLVE_NO_APPROX     0x01u  /* disable the SVD fallback (Sec. 2.5 option) */
@@ -161,7 +168,10 @@ typedef struct {           /* 64 bytes, one per system */
                               bit 4: band system solved by the partitioned route for
                               diagonally dominant bands (the default for n >= 4096;
                               environment ASOLVE_BAND_SPIKE=0 turns it off),
-                              bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes) */
+                              bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes),
+                              bit 6: large path, FP64 updates as Ozaki-split tensor-core
+                              products (ASOLVE_PREC_FP64_OZ, or a mixed mode's FP64
+                              re-factorisation) */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */
@@ -337,6 +347,28 @@ int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, voi
 #define ASOLVE_GEMM_FP16    17
 int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
                     int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream);
+
+/* The FP64 product of the large path's FP64 trailing updates, blocked
+ * triangular-solve updates and many-right-hand-side residuals (Sec. 2.2-2.4
+ * in FP64), exposed so it can be verified on its own:
+ *   C (M x N) -= A (M x K) * op(B), FP64, column-major, device pointers,
+ * op(B) = B (K x N, ldb >= K) or, with transb != 0, B^T for B stored N x K
+ * (ldb >= N).  Computed by the Ozaki splitting (Ozaki, Ogita, Oishi, Rump
+ * 2012; the paper has no counterpart): each operand becomes seven exact
+ * BF16 slices (per-row / per-column power-of-two scales over each K chunk
+ * of 128), the 28 significant slice products accumulate exactly in FP32 on
+ * the tcgen05 tensor cores, and each chunk is added to C in FP64; the error
+ * is about 2^-48 (max_k |A(i,k)|) (max_k |op(B)(k,j)|) per chunk of 128,
+ * that of an FP64 GEMM.  A or B non-finite in a chunk: C(i,j) becomes NaN.
+ * ws: device workspace of asolve_gemm_oz_ws_bytes(M, N, K) bytes, 256-byte
+ * aligned, owned by the caller (its content is scratch).  err: optional
+ * device int set to 1 if a device-side wait gave up.  Asynchronous on
+ * `stream`.  Errors: E_INVALID (null pointer, leading dimension, workspace
+ * too small or unaligned), E_UNSUPPORTED (a size above 2^31 - 1), E_CUDA. */
+size_t asolve_gemm_oz_ws_bytes(int64_t M, int64_t N, int64_t K);
+int asolve_gemm_oz(double* C, int64_t ldc, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   int64_t M, int64_t N, int64_t K, int transb, void* ws, size_t ws_bytes, int* err,
+                   void* stream);
 
 /* Panel widths of the batched dense factorisations, one per size bucket
  * (bucket i holds n in [32 i + 1, 32 i + 32]), as chosen by the autotuner

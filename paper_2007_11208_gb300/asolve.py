@@ -22,7 +22,7 @@ E_INVALID, E_NONFINITE, E_SINGULAR, E_NOMEM, E_CUDA, E_TIMEOUT, E_IR_STALL, E_UN
 CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
 (ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
  ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD, ROUTE_TRIDIAG, ROUTE_LDLT, ROUTE_CHOL_FAIL_LDLT) = range(11)
-PREC_FP64, PREC_MIXED, PREC_BF16, PREC_FP16 = 0, 1, 2, 3
+PREC_FP64, PREC_MIXED, PREC_BF16, PREC_FP16, PREC_FP64_OZ = 0, 1, 2, 3, 4
 GEMM_TF32, GEMM_TF32X3, GEMM_BF16, GEMM_FP16 = 1, 3, 16, 17
 NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND, SYNC, HOST_BUFFERS, BERR, RESIDENT, TRIDIAG, SYM_INDEF = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80, 0x100, 0x200)
@@ -78,7 +78,8 @@ EXPORTS = ("asolve_version", "asolve_strerror", "asolve_default_config", "asolve
            "asolve_solve_band", "asolve_solve_batched", "asolve_set_profiling",
            "asolve_get_profile", "asolve_reset_profile", "asolve_scan_noalloc",
            "asolve_gemm_sub", "asolve_solve_batched_ptrs", "asolve_submit", "asolve_poll",
-           "asolve_get_serve_stats", "asolve_set_panel_widths", "asolve_pipe_peak")
+           "asolve_get_serve_stats", "asolve_set_panel_widths", "asolve_pipe_peak",
+           "asolve_gemm_oz_ws_bytes", "asolve_gemm_oz")
 PIPE_FFMA, PIPE_DFMA, PIPE_DMMA = 1, 2, 3
 
 
@@ -115,8 +116,10 @@ def lib():
     L.asolve_get_serve_stats.argtypes = [vp, P(ServeStats)]
     L.asolve_set_panel_widths.argtypes = [vp, i32, vp, i32]
     L.asolve_pipe_peak.argtypes = [i32, i32, P(C.c_double), P(C.c_double)]
+    L.asolve_gemm_oz_ws_bytes.argtypes = [i64, i64, i64]
+    L.asolve_gemm_oz_ws_bytes.restype = C.c_size_t
     for f in EXPORTS:
-        if f not in ("asolve_version", "asolve_strerror", "asolve_stream"):
+        if f not in ("asolve_version", "asolve_strerror", "asolve_stream", "asolve_gemm_oz_ws_bytes"):
             getattr(L, f).restype = i32
     _lib = L
     return L

@@ -170,7 +170,7 @@ extern "C" int asolve_create(asolve_ctx** out, const asolve_config* cfg) {
   if (!c) return ASOLVE_E_NOMEM;
   if (cfg) c->cfg = *cfg;
   else asolve_default_config(&c->cfg);
-  if (c->cfg.precision < ASOLVE_PREC_FP64 || c->cfg.precision > ASOLVE_PREC_FP16) {
+  if (c->cfg.precision < ASOLVE_PREC_FP64 || c->cfg.precision > ASOLVE_PREC_FP64_OZ) {
     delete c;
     return ASOLVE_E_INVALID;
   }
@@ -627,6 +627,26 @@ extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t ld
   if (M == 0 || N == 0 || K == 0) return ASOLVE_OK;
   cudaError_t e = launch_gemm_tc(C, (int)ldc, A, (int)lda, B, (int)ldb, (int)M, (int)N, (int)K, passes, err,
                                  (cudaStream_t)stream, false, false);
+  return e == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
+}
+
+extern "C" size_t asolve_gemm_oz_ws_bytes(int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return 0;
+  return gemm_oz_ws_bytes((int)M, (int)N, (int)K);
+}
+
+extern "C" int asolve_gemm_oz(double* C, int64_t ldc, const double* A, int64_t lda, const double* B, int64_t ldb,
+                              int64_t M, int64_t N, int64_t K, int transb, void* ws, size_t ws_bytes, int* err,
+                              void* stream) {
+  if (!C || !A || !B || M < 0 || N < 0 || K < 0) return ASOLVE_E_INVALID;
+  if (ldc < (M > 0 ? M : 1) || lda < (M > 0 ? M : 1) || ldb < (transb ? (N > 0 ? N : 1) : (K > 0 ? K : 1)))
+    return ASOLVE_E_INVALID;
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || ldc > INT32_MAX || lda > INT32_MAX || ldb > INT32_MAX)
+    return ASOLVE_E_UNSUPPORTED;
+  if (M == 0 || N == 0 || K == 0) return ASOLVE_OK;
+  if (!ws || ((uintptr_t)ws & 255) || ws_bytes < gemm_oz_ws_bytes((int)M, (int)N, (int)K)) return ASOLVE_E_INVALID;
+  cudaError_t e = gemm_oz(C, (int)ldc, A, (int)lda, B, (int)ldb, (int)M, (int)N, (int)K, transb != 0, false, ws, err,
+                          (cudaStream_t)stream);
   return e == cudaSuccess ? ASOLVE_OK : ASOLVE_E_CUDA;
 }
 

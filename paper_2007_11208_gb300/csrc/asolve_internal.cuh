@@ -163,6 +163,11 @@ int large_svd(const double* A, int64_t n, const double* B, double* X, int64_t nr
               double* G, void* ws, int64_t* rank, int* sweeps, cudaStream_t st);
 size_t large_ws_bytes(int64_t n, int64_t nrhs);
 int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info);
+// FP64 C (M x N) -= A (M x K) op(B) by the Ozaki splitting on the BF16
+// tensor cores (gemm_oz.cu); ws: gemm_oz_ws_bytes(M, N, K) bytes.
+size_t gemm_oz_ws_bytes(int M, int N, int K);
+cudaError_t gemm_oz(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N, int K,
+                    bool tb, bool lower, void* ws, int* err, cudaStream_t st);
 
 // One system for the banded route (band_large.cu): band storage input
 // (AB, ldab, declared kld/kud) or a dense matrix A with its scan results.

@@ -353,7 +353,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   // ---- mixed precision attempt (not when magnitudes leave the FP32 range)
   // (the 16-bit modes differ only in the large path's tensor-core updates:
   // here they factor in FP32 as MIXED does)
-  if (d.precision != ASOLVE_PREC_FP64 && !(sr.flags & SF_NORM_FP64)) {
+  if (d.precision != ASOLVE_PREC_FP64 && d.precision != ASOLVE_PREC_FP64_OZ && !(sr.flags & SF_NORM_FP64)) {
     float* W = reinterpret_cast<float*>(sl.W);
     copy_to_work<float>(A, n, W, ldw);
     const int nb = pick_nb<float>(n, d, KIND);

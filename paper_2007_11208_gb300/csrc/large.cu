@@ -1105,6 +1105,7 @@ struct Fac {  // a factorisation of the large path and its scratch
   PanelBuf pb;
   WaveBuf wb;
   int gemm_mode = 3;  // FP32 factors: operand mode of the trailing updates (launch_gemm_tc)
+  void* ozws = nullptr;  // FP64 factors: Ozaki-split trailing updates (gemm_oz) in this workspace
   const T* dinvL = nullptr;  // FP32 factors: inverses of the 128 x 128 diagonal blocks (k_diag_inv)
   const T* dinvU = nullptr;
 };
@@ -1163,15 +1164,18 @@ int apply_large(const Fac<T>& f, bool lu, int n, V* x, int nrhs, bool trans, V* 
 
 template <typename T>
 cudaError_t gemm_update(T* C, int ldc, const T* A, int lda, const T* B, int ldb, int M, int N, int K, bool tb,
-                        bool lower, int* err, int mode, cudaStream_t st);
+                        bool lower, int* err, int mode, cudaStream_t st, void* ozws = nullptr);
 template <>
 cudaError_t gemm_update<float>(float* C, int ldc, const float* A, int lda, const float* B, int ldb, int M, int N,
-                               int K, bool tb, bool lower, int* err, int mode, cudaStream_t st) {
+                               int K, bool tb, bool lower, int* err, int mode, cudaStream_t st, void*) {
   return launch_gemm_tc(C, ldc, A, lda, B, ldb, M, N, K, mode, err, st, tb, lower);
 }
+// FP64: the Ozaki-split product on the BF16 tensor cores when a workspace
+// is given, else the mma.sync f64 GEMM
 template <>
 cudaError_t gemm_update<double>(double* C, int ldc, const double* A, int lda, const double* B, int ldb, int M, int N,
-                                int K, bool tb, bool lower, int* err, int, cudaStream_t st) {
+                                int K, bool tb, bool lower, int* err, int, cudaStream_t st, void* ozws) {
+  if (ozws) return gemm_oz(C, ldc, A, lda, B, ldb, M, N, K, tb, lower, ozws, err, st);
   dim3 g((M + kDmM - 1) / kDmM, (N + kDmN - 1) / kDmN);
   if (tb && lower) k_gemm_dmma<true, true><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
   else if (tb) k_gemm_dmma<true, false><<<g, kThreads, kDmSmem, st>>>(C, ldc, A, lda, B, ldb, M, N, K);
@@ -1231,7 +1235,7 @@ int chol_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
       k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 1, 0);
       T* L21 = f.W + (size_t)k0 * f.ldw + k0 + kb;
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, L21, f.ldw, L21, f.ldw, rest, rest, kb,
-                         true, true, f.fail + 1, f.gemm_mode, st));
+                         true, true, f.fail + 1, f.gemm_mode, st, f.ozws));
     }
   }
   LCK(cudaGetLastError());
@@ -1270,7 +1274,7 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
       k_trsm_sub<T><<<(rest + 63) / 64, kThreads, trsm_smem<T>(), st>>>(f.W, f.ldw, k0, kb, k0 + kb, n, 0, 1);
       LCK(gemm_update<T>(f.W + (size_t)(k0 + kb) * f.ldw + k0 + kb, f.ldw, f.W + (size_t)k0 * f.ldw + k0 + kb,
                          f.ldw, f.W + (size_t)(k0 + kb) * f.ldw + k0, f.ldw, rest, rest, kb, false, false,
-                         f.fail + 1, f.gemm_mode, st));
+                         f.fail + 1, f.gemm_mode, st, f.ozws));
     }
   }
   LCK(cudaGetLastError());
@@ -1306,6 +1310,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += sizeof(int) * (size_t)(((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR)) + 1024;  // wave flags
   if (n <= kSvdLargeMax) b += large_svd_ws_bytes(n, nrhs) + 4096;  // SVD fallback (V, sigma, coefficients)
   b += sizeof(double) * (size_t)n * (kGmresM + 4) + sizeof(double) * (kGmresM + 2) + 2048;  // GMRES-IR
+  b += gemm_oz_ws_bytes((int)n, (int)(n > nrhs ? n : nrhs), kLB) + 256;  // Ozaki-split FP64 updates
   return b + (1 << 20);
 }
 
@@ -1411,6 +1416,9 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   void* exi = ar.take(sizeof(double) * (size_t)n);
   unsigned long long* colmax = static_cast<unsigned long long*>(ar.take(sizeof(unsigned long long) * 3 * nrhs));
   if (!R || !Pres || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
+  // FP64 updates as Ozaki-split tensor products in every mode but the plain
+  // FP64 one (which keeps the mma.sync f64 GEMM)
+  void* ozws = a.precision != ASOLVE_PREC_FP64 ? ar.take(gemm_oz_ws_bytes(n, n > nrhs ? n : nrhs, kLB)) : nullptr;
   // FP64 normwise backward error of X, the maximum over the columns
   auto backward_error = [&](double& be) -> int {
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
@@ -1489,7 +1497,9 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     int rc;
     if (nrhs >= kTrsmBlockedRhs) {
       // many right-hand sides: blocked TRSM, diagonal blocks by substitution,
-      // the rest of the right-hand sides updated on mma.sync f64
+      // the rest of the right-hand sides updated by the Ozaki-split product
+      // (the mma.sync f64 GEMM in the plain FP64 mode)
+      if (ozws) info->detail |= 64;
       const unsigned gr = (unsigned)((nrhs + 63) / 64);
       for (int q = 0; q < n; q += kLB) {
         const int k0 = lower ? q : ((n - 1 - q) / kLB) * kLB;
@@ -1497,10 +1507,10 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
         k_trsm_rhs<<<gr, kThreads, trsm_smem<double>(), st>>>(a.A, n, k0, kb, a.X, n, nrhs, lower ? 0 : 1);
         if (lower && k0 + kb < n)
           LCK(gemm_update<double>(a.X + k0 + kb, n, a.A + (size_t)k0 * n + k0 + kb, n, a.X + k0, n, n - k0 - kb, nrhs,
-                                  kb, false, false, nullptr, 0, st));
+                                  kb, false, false, werr, 0, st, ozws));
         if (!lower && k0 > 0)
-          LCK(gemm_update<double>(a.X, n, a.A + (size_t)k0 * n, n, a.X + k0, n, k0, nrhs, kb, false, false, nullptr, 0,
-                                  st));
+          LCK(gemm_update<double>(a.X, n, a.A + (size_t)k0 * n, n, a.X + k0, n, k0, nrhs, kb, false, false, werr, 0,
+                                  st, ozws));
       }
       LCK(cudaGetLastError());
     } else if ((rc = tri_solve_large<double>(a.A, n, n, lower, false, false, a.X, nrhs, false, wb, st))) {
@@ -1846,7 +1856,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   }
   // ---- mixed precision: FP32 factors (trailing updates as 3xTF32, BF16 or
   // FP16 tensor products), FP64 refinement
-  if (a.precision != ASOLVE_PREC_FP64 && !(sr.flags & SF_NORM_FP64)) {
+  if (a.precision != ASOLVE_PREC_FP64 && a.precision != ASOLVE_PREC_FP64_OZ && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
     Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, wb};
     f.gemm_mode = a.precision == ASOLVE_PREC_BF16 ? kGemmBf16 : (a.precision == ASOLVE_PREC_FP16 ? kGemmFp16 : 3);
@@ -1923,6 +1933,8 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   // ---- FP64 path
   if ((rc = set_large_attrs<double>())) return rc;
   Fac<double> f{static_cast<double*>(Wv), ldw, piv, perm, static_cast<double*>(Dtmp), fail, pb, wb};
+  f.ozws = ozws;
+  if (ozws) detail |= 64;
   info->precision = ASOLVE_PREC_FP64;
   info->detail = detail;
   bool lu = !chol;

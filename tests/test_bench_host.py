@@ -35,11 +35,20 @@ def test_precision_selects_the_peak():
     assert mixed["floor_ms"] == pytest.approx(6 * bf16["floor_ms"])
 
 
-def test_triangular_route_is_fp64_whatever_the_precision():
-    for prec in ("mixed", "fp64", "bf16"):
+def test_triangular_route_peak_follows_its_update_product():
+    """The triangular route is FP64 in every mode; its blocked updates (from
+    32 right-hand sides) are Ozaki-split tensor products in every mode but
+    plain FP64, whose peak is the bf16 rate over the 28 slice products."""
+    for prec in ("mixed", "fp64", "bf16", "fp64_oz"):
         r = bench.large_case_roofline("lower", prec, 16384, 256, 285.8, PEAKS)
-        assert r["peak_tflops"] == pytest.approx(fp64_peak() / 1e12)
+        want = fp64_peak() / 1e12 if prec == "fp64" else 1917.9 / 28
+        assert r["peak_tflops"] == pytest.approx(want)
         assert r["flops"] == pytest.approx(16384.0 ** 2 * 256)
+    for prec in ("mixed", "fp64"):  # few right-hand sides: the FP64 wavefront solve
+        r = bench.large_case_roofline("lower", prec, 16384, 16, 30.0, PEAKS)
+        assert r["peak_tflops"] == pytest.approx(fp64_peak() / 1e12)
+    oz = bench.large_case_roofline("general", "fp64_oz", 16384, 1, 1000.0, PEAKS)
+    assert oz["peak_tflops"] == pytest.approx(1917.9 / 28)
 
 
 def test_one_rhs_triangular_solve_is_hbm_bound():

@@ -1,6 +1,7 @@
 """Large single systems (n > 1024): blocked Cholesky / LU on the whole GPU
 (tcgen05 3xTF32 trailing updates in the mixed mode, mma.sync f64 in the
-FP64 mode), blocked triangular solves, FP64 refinement.
+FP64 mode, Ozaki-split BF16 tensor products in the FP64_OZ mode), blocked
+triangular solves, FP64 refinement.
 
 Element-wise parity with the oracle at sizes it solves in seconds; at
 larger n the backward error (oracle Dot2 residual) and the forward error
@@ -14,11 +15,11 @@ pytestmark = pytest.mark.gpu
 EPS = np.finfo(np.float64).eps
 
 
-@pytest.fixture(scope="module", params=["fp64", "mixed"])
+@pytest.fixture(scope="module", params=["fp64", "mixed", "fp64_oz"])
 def ctx(request):
     from paper_2007_11208_gb300 import asolve, build
     build.build()
-    prec = asolve.PREC_FP64 if request.param == "fp64" else asolve.PREC_MIXED
+    prec = {"fp64": asolve.PREC_FP64, "mixed": asolve.PREC_MIXED, "fp64_oz": asolve.PREC_FP64_OZ}[request.param]
     c = asolve.Context(precision=prec)
     c.prec = request.param
     yield c
@@ -158,3 +159,25 @@ def test_large_16bit_updates(orc, prec_name, kind, n, kappa):
             (info["precision"] == asolve.PREC_FP64 and info["detail"] & 3), info
     elif kappa is None:
         assert info["precision"] == prec and info["ir_iters"] >= 1, info
+
+
+def test_mixed_fallback_refactors_with_ozaki_updates(orc):
+    """A system beyond the FP32 factors' kappa gate: the mixed mode
+    re-factors it in FP64 with Ozaki-split trailing updates (detail bit 6),
+    and the answer meets the FP64 bar against the oracle."""
+    from paper_2007_11208_gb300 import asolve, build
+    build.build()
+    rng = np.random.default_rng(77)
+    n = 2048
+    A = spectrum(n, 1e12, rng)
+    B = rng.standard_normal((n, 2))
+    ctx = asolve.Context(precision=asolve.PREC_MIXED)
+    rc, info, X = solve_gpu(ctx, A, B, asolve.BERR)
+    ctx.close()
+    Xo, io = orc.solve(A, B)
+    assert (info["route"], rc) == (io["route"], io["status"]), (info, io)
+    assert info["precision"] == asolve.PREC_FP64 and info["detail"] & 64 and info["detail"] & 1, info
+    _, berr = orc.residual_dot2(A, X, B)
+    assert berr.max() <= 1e-13, berr
+    assert fwd_err(X, Xo) <= 2.0 ** -52 * n * n * 1e12
+    assert abs(info["rcond"] - io["rcond"]) <= 1e-2 * io["rcond"], (info["rcond"], io["rcond"])
