@@ -654,7 +654,7 @@ def large_workload(args):
     head = [c for c in cases if c["n"] == sizes[-1] and c["kind"] == "general" and c["kappa"] == 1e4
             and c["nrhs"] == 1]
     head = head[0] if head else cases[-1]
-    hp = "mixed" if "mixed" in head else "fp64"
+    hp = next(p for p in ("mixed", "fp64", "fp64_oz", "bf16", "fp16") if p in head)
     ok = head[hp]["rc"] == 0 and head[hp]["berr"] <= BERR_BAR
     cpu = None
     if args.cpu_baseline:

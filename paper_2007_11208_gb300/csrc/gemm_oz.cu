@@ -329,11 +329,22 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       mma_pending = false;
     }
     if (!ok) break;
-    // drain: warp w owns rows 32w..32w+31, 16 columns at a time
+    // drain: warp w owns rows 32w..32w+31, 16 columns at a time; the
+    // group's loads of C and of the column scales go out together, before
+    // the accumulator reads, and its stores after all of them
     const int r = m0 + 32 * w + lane;
     const int E = r < M ? __ldg(eA + (size_t)kc * Mp + r) : 0;
 #pragma unroll 1
     for (int c0 = 0; c0 < kOzN; c0 += 16) {
+      double cv[16];
+      int F[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = n0 + c0 + j;
+        const bool in = r < M && c < N;
+        F[j] = c < N ? __ldg(eB + (size_t)kc * Np + c) : 0;
+        cv[j] = in ? C[(size_t)c * ldc + r] : 0.0;
+      }
       uint32_t v[kOzS][16];
 #pragma unroll
       for (int g = 0; g < kOzS; ++g) {
@@ -351,23 +362,20 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int c = n0 + c0 + j;
-          if (c >= N) continue;
-          const int F = __ldg(eB + (size_t)kc * Np + c);
-          if (E == 0 || F == 0) continue;  // a zero row or column of this chunk
-          double* pc = C + (size_t)c * ldc + r;
-          if (E == kOzNonFinite || F == kOzNonFinite) {
-            *pc = __longlong_as_double(0x7ff8000000000000ll);
-            continue;
+          if (c >= N || E == 0 || F[j] == 0) continue;  // a zero row or column of this chunk
+          if (E == kOzNonFinite || F[j] == kOzNonFinite) {
+            cv[j] = __longlong_as_double(0x7ff8000000000000ll);
+          } else {
+            const int64_t V = (oz_int(v[0][j]) << 36) + (oz_int(v[1][j]) << 28) + (oz_int(v[2][j]) << 20) +
+                              (oz_int(v[3][j]) << 12) + (oz_int(v[4][j]) << 4) + ((oz_int(v[5][j]) + 8) >> 4) +
+                              ((oz_int(v[6][j]) + 2048) >> 12);
+            // C -= V 2^(E + F - 2094): the power of two built from its
+            // bits when it is a normal double, else scalbn
+            const int x = E + F[j] - 2094;
+            if (x >= -1022 && x <= 1023) cv[j] = fma(-(double)V, __longlong_as_double((long long)(x + 1023) << 52), cv[j]);
+            else cv[j] = cv[j] - scalbn((double)V, x);
           }
-          const int64_t V = (oz_int(v[0][j]) << 36) + (oz_int(v[1][j]) << 28) + (oz_int(v[2][j]) << 20) +
-                            (oz_int(v[3][j]) << 12) + (oz_int(v[4][j]) << 4) + ((oz_int(v[5][j]) + 8) >> 4) +
-                            ((oz_int(v[6][j]) + 2048) >> 12);
-          if (V == 0) continue;
-          // C -= V 2^(E + F - 2094): the power of two built from its bits
-          // when it is a normal double, else scalbn
-          const int x = E + F - 2094;
-          if (x >= -1022 && x <= 1023) *pc = fma(-(double)V, __longlong_as_double((long long)(x + 1023) << 52), *pc);
-          else *pc = *pc - scalbn((double)V, x);
+          C[(size_t)c * ldc + r] = cv[j];
         }
       }
     }

@@ -210,15 +210,16 @@ __global__ void __launch_bounds__(kThreads) k_trsm_rhs(const double* __restrict_
 // row, and the whole panel row) and the owner of the diagonal row publishes
 // that row; after one grid barrier every CTA picks the same pivot (largest
 // |value|, first row on ties), swaps locally and updates its own rows.
-// Buffers are double-buffered by column parity.  This is the FP64 panel;
-// the FP32 panel (k_lu_panel32, below) elects the pivot with an atomic.
+// Buffers are double-buffered by column parity.  This is the FP64 panel of
+// more than 2^16 rows; the others (k_lu_panel_at, below) elect the pivot
+// with an atomic.
 struct PanelBuf {
   void* cand;      // [2][G][4] of T: |v|, row, v, valid
   void* rows;      // [2][G][kLB] of T
   void* diag;      // [2][kLB] of T
   unsigned* bar;   // grid barrier (zeroed before the launch)
   int* err;
-  unsigned long long* key;  // [3] k_lu_panel32: (|v| bits << 32) | ~row, by atomicMax
+  unsigned long long* key;  // [3] k_lu_panel_at: election keys (PivKey), by atomicMax
 };
 
 template <typename T>
@@ -353,9 +354,33 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
     for (int i = lane; i < nr; i += 32) W[(size_t)(k0 + c) * ldw + k0 + rlo + i] = S[i * (kLB + 1) + c];
 }
 
-// FP32 panel with the pivot elected by one 64-bit atomicMax per CTA and
-// column: key = (|v| bits << 32) | ~row, so the largest key is the largest
-// |v| and, among equal magnitudes, the first row.  Per column:
+// Pivot election key of the atomic panel: the largest key is the largest
+// |v| and, among equal magnitudes, the first row.  FP32: (|v| bits << 32) |
+// ~row.  FP64: |v|'s sign-free bits with the low 16 cleared, | ~row in the
+// low 16 bits (rows below 2^16): the winner is within 2^-36 of the
+// column's largest |v| (first row among those that agree in the top 47
+// bits), as stable a choice as the exact maximum.
+template <typename T>
+struct PivKey;
+template <>
+struct PivKey<float> {
+  static constexpr int kMaxRows = 0x7fffffff;
+  __device__ static unsigned long long make(float a, int row) {
+    return ((unsigned long long)__float_as_uint(a) << 32) | (0xffffffffull - (unsigned)row);
+  }
+  __device__ static int row(unsigned long long key) { return (int)(0xffffffffull - (key & 0xffffffffull)); }
+};
+template <>
+struct PivKey<double> {
+  static constexpr int kMaxRows = 0xffff;
+  __device__ static unsigned long long make(double a, int row) {
+    return ((unsigned long long)__double_as_longlong(a) & ~0xffffull) | (0xffffull - (unsigned)row);
+  }
+  __device__ static int row(unsigned long long key) { return (int)(0xffffull - (key & 0xffffull)); }
+};
+
+// The panel with the pivot elected by one 64-bit atomicMax per CTA and
+// column (PivKey).  Per column:
 //   1. each warp finds its best row among the CTA's rows >= c; warp 0
 //      reduces the eight, posts the key and publishes that row; the owner
 //      of row c publishes it (the row a swap moves down);
@@ -367,14 +392,16 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel(T* __restrict__ W, int ld
 //      copy of row c and the pivot row is written over row c, so the swap
 //      needs no barrier of its own.
 // Keys are triple-buffered (the buffer for column c + 1 is cleared while
-// column c is elected), rows double-buffered by column parity.
-__global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, int ldw, int n, int k0, int kb,
-                                                        int R, int* __restrict__ piv, PanelBuf pb, int* fail) {
+// column c is elected), rows double-buffered by column parity.  FP64 panels
+// of more than PivKey<double>::kMaxRows rows take k_lu_panel.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_lu_panel_at(T* __restrict__ W, int ldw, int n, int k0, int kb, int R,
+                                                         int* __restrict__ piv, PanelBuf pb, int* fail) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* S = reinterpret_cast<float*>(smem);  // R x (kLB + 1)
-  float* prow = S + (size_t)R * (kLB + 1);     // the pivot row
-  float* drow = prow + kLB;                    // the old row c
-  __shared__ float s_best[kWarps];
+  T* S = reinterpret_cast<T*>(smem);  // R x (kLB + 1)
+  T* prow = S + (size_t)R * (kLB + 1);  // the pivot row
+  T* drow = prow + kLB;                 // the old row c
+  __shared__ T s_best[kWarps];
   __shared__ int s_idx[kWarps];
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int m = n - k0;
@@ -383,19 +410,19 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, 
   for (int c = w; c < kb; c += kWarps)
     for (int i = lane; i < nr; i += 32) S[i * (kLB + 1) + c] = W[(size_t)(k0 + c) * ldw + k0 + rlo + i];
   __syncthreads();
-  float* rowsT = reinterpret_cast<float*>(pb.rows);
-  float* diagT = reinterpret_cast<float*>(pb.diag);
+  T* rowsT = reinterpret_cast<T*>(pb.rows);
+  T* diagT = reinterpret_cast<T*>(pb.diag);
   for (int c = 0; c < kb; ++c) {
     const int buf = c & 1;
-    float best = -1.f;
+    T best = T(-1);
     int bi = 0x7fffffff;
     for (int i = max(0, c - rlo) + tid; i < nr; i += kThreads) {
-      const float a = fabsf(S[i * (kLB + 1) + c]);
+      const T a = fabs(S[i * (kLB + 1) + c]);
       if (a > best) { best = a; bi = rlo + i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
@@ -404,11 +431,11 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, 
       for (int k = lane; k < kb; k += 32) diagT[(size_t)buf * kLB + k] = S[(c - rlo) * (kLB + 1) + k];
     __syncthreads();
     if (w == 0) {
-      best = lane < kWarps ? s_best[lane] : -1.f;
+      best = lane < kWarps ? s_best[lane] : T(-1);
       bi = lane < kWarps ? s_idx[lane] : 0x7fffffff;
 #pragma unroll
       for (int o = 4; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
       }
@@ -416,8 +443,7 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, 
       bi = __shfl_sync(0xffffffffu, bi, 0);
       if (bi != 0x7fffffff) {
         for (int k = lane; k < kb; k += 32) rowsT[((size_t)buf * G + b) * kLB + k] = S[(bi - rlo) * (kLB + 1) + k];
-        if (lane == 0 && best >= 0.f)
-          atomicMax(pb.key + c % 3, ((unsigned long long)__float_as_uint(best) << 32) | (0xffffffffull - (unsigned)bi));
+        if (lane == 0 && best >= T(0)) atomicMax(pb.key + c % 3, PivKey<T>::make(best, bi));
       }
       // the next column's key was last read after barrier c - 2: clear it now
       if (b == 0 && lane == 0) pb.key[(c + 1) % 3] = 0ull;
@@ -425,27 +451,27 @@ __global__ void __launch_bounds__(kThreads) k_lu_panel32(float* __restrict__ W, 
     __threadfence();
     if (!grid_barrier_count(pb.bar, (unsigned)(c + 1) * (unsigned)G, pb.err)) return;
     const unsigned long long key = *(volatile unsigned long long*)(pb.key + c % 3);
-    const int p = key ? (int)(0xffffffffull - (key & 0xffffffffull)) : 0x7fffffff;
+    const int p = key ? PivKey<T>::row(key) : 0x7fffffff;
     const int wb = (p != 0x7fffffff) ? p / R : -1;
     const bool okw = wb >= 0 && wb < G;
     if (tid < kb) {
-      prow[tid] = okw ? ((volatile float*)rowsT)[((size_t)buf * G + wb) * kLB + tid] : 0.f;
-      drow[tid] = ((volatile float*)diagT)[(size_t)buf * kLB + tid];
+      prow[tid] = okw ? ((volatile T*)rowsT)[((size_t)buf * G + wb) * kLB + tid] : T(0);
+      drow[tid] = ((volatile T*)diagT)[(size_t)buf * kLB + tid];
     }
     __syncthreads();
-    const float pv = prow[c];
-    const bool stop = !okw || p < c || p >= m || pv == 0.f || pv != pv;  // uniform: the same key everywhere
+    const T pv = prow[c];
+    const bool stop = !okw || p < c || p >= m || pv == T(0) || pv != pv;  // uniform: the same key everywhere
     if (tid == 0 && b == 0) {
       if (stop) *fail = k0 + c + 1;
       else piv[k0 + c] = k0 + p;
     }
     if (stop) return;
-    const float inv = 1.f / pv;
+    const T inv = T(1) / pv;
     const int pl = (p != c && p >= rlo && p < rhi) ? p - rlo : -1;  // the swapped-in row, if here
     for (int i = max(0, c + 1 - rlo) + w; i < nr; i += kWarps) {
-      float* row = S + i * (kLB + 1);
-      const float* src = (i == pl) ? drow : row;
-      const float l = src[c] * inv;
+      T* row = S + i * (kLB + 1);
+      const T* src = (i == pl) ? drow : row;
+      const T l = src[c] * inv;
       if (i == pl)
         for (int k = lane; k < c; k += 32) row[k] = drow[k];
       for (int k = c + 1 + lane; k < kb; k += 32) row[k] = src[k] - l * prow[k];
@@ -1200,11 +1226,12 @@ cudaError_t set_large_attrs_dev() {
   SA(cudaFuncSetAttribute(k_gemm_dmma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDmSmem));
   // the panel kernel also has a little static shared memory
   if constexpr (sizeof(T) == 4) {
-    SA(cudaFuncSetAttribute(k_lu_panel32, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+    SA(cudaFuncSetAttribute(k_lu_panel_at<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
     SA(cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagInvSmem));
   }
   else
     SA(cudaFuncSetAttribute(k_lu_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
+    SA(cudaFuncSetAttribute(k_lu_panel_at<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 226 * 1024));
   SA(cudaFuncSetAttribute(k_trsv_wave<T, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)wave_smem<T, float>()));
   SA(cudaFuncSetAttribute(k_trsv_wave<T, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1265,7 +1292,7 @@ int lu_large(Fac<T>& f, int n, int num_sms, int* fail_out, cudaStream_t st) {
     int* fail = f.fail;
     void* args[] = {&W, &ldw, &n, &k0, (void*)&kb, (void*)&R, &piv, &pb, &fail};
     const void* kern;
-    if constexpr (sizeof(T) == 4) kern = (const void*)k_lu_panel32;
+    if (sizeof(T) == 4 || m <= PivKey<double>::kMaxRows + 1) kern = (const void*)k_lu_panel_at<T>;
     else kern = (const void*)k_lu_panel<T>;
     LCK(cudaLaunchCooperativeKernel(kern, dim3(G), dim3(kThreads), args, psmem, st));
     k_swap_rows<T><<<(n + 255) / 256, 256, 0, st>>>(f.W, f.ldw, n, k0, kb, f.piv);
