@@ -307,18 +307,22 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (!ok) break;
       ph_ld ^= 1u;
       ld_pending = false;
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        for (int s = 0; s < kOzS; ++s)
-          for (int t = 0; s + t < kOzS; ++t) {
-            const uint32_t acc_col = tmem + (uint32_t)((s + t) * kOzN);
+      if (w == 0) {  // lane 0 issues; the other lanes wait at the warp barrier, not on the mbarrier
+        if (lane == 0) {
+          asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+          const uint64_t da = oz_desc(oz_smem(sA)), db = oz_desc(oz_smem(sB));
+          for (int s = 0; s < kOzS; ++s)
+            for (int t = 0; s + t < kOzS; ++t) {
+              const uint32_t acc_col = tmem + (uint32_t)((s + t) * kOzN);
 #pragma unroll
-            for (int j = 0; j < kOzKs / 16; ++j)  // K = 16 per MMA: two core matrices
-              oz_mma(acc_col, oz_desc(oz_smem(sA + s * kOzABytes) + j * 256),
-                     oz_desc(oz_smem(sB + t * kOzBBytes) + j * 256), (sub > 0 || s > 0 || j > 0) ? 1u : 0u);
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb_mma)
-                     : "memory");
+              for (int j = 0; j < kOzKs / 16; ++j)  // K = 16 per MMA: two core matrices (16-byte units)
+                oz_mma(acc_col, da + (uint64_t)((s * kOzABytes + j * 256) >> 4),
+                       db + (uint64_t)((t * kOzBBytes + j * 256) >> 4), (sub > 0 || s > 0 || j > 0) ? 1u : 0u);
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mb_mma)
+                       : "memory");
+        }
+        __syncwarp();
       }
       mma_pending = true;
       const bool done = oz_wait(mb_mma, ph_mma, wait_limit);
