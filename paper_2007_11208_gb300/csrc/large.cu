@@ -1033,12 +1033,23 @@ struct Arena {
 
 // R = B - A X in FP64 with rmax[c] |= max |R(:, c)| (rmax zeroed by the
 // caller); P: kResMaxSeg x 8 x n doubles of scratch.
+// K columns of A per Ozaki-split residual product (bounds its workspace
+// to gemm_oz_ws_bytes(n, nrhs, kOzResK))
+constexpr int kOzResK = 1024;
+
 int residual_large(const double* A, int n, const double* B, const double* X, int nrhs, double* R,
-                   unsigned long long* rmax, double* P, int num_sms, cudaStream_t st) {
-  if (nrhs > 8) {  // R = B, then R -= A X on the mma.sync f64 GEMM, then max |R|
+                   unsigned long long* rmax, double* P, int num_sms, cudaStream_t st, void* ozws = nullptr,
+                   int* err = nullptr) {
+  if (nrhs > 8) {  // R = B, then R -= A X, then max |R|
     LCK(cudaMemcpyAsync(R, B, sizeof(double) * (size_t)n * nrhs, cudaMemcpyDeviceToDevice, st));
-    k_gemm_dmma<false, false><<<dim3((n + kDmM - 1) / kDmM, (nrhs + kDmN - 1) / kDmN), kThreads, kDmSmem, st>>>(
-        R, n, A, n, X, n, n, nrhs, n);
+    if (ozws) {  // Ozaki-split products on the tensor cores, kOzResK columns of A at a time
+      for (int k0 = 0; k0 < n; k0 += kOzResK)
+        LCK(gemm_oz(R, n, A + (size_t)k0 * n, n, X + k0, n, n, nrhs, std::min(kOzResK, n - k0), false, false, ozws,
+                    err, st));
+    } else {  // the mma.sync f64 GEMM
+      k_gemm_dmma<false, false><<<dim3((n + kDmM - 1) / kDmM, (nrhs + kDmN - 1) / kDmN), kThreads, kDmSmem, st>>>(
+          R, n, A, n, X, n, n, nrhs, n);
+    }
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(R, n, nrhs, rmax);
     LCK(cudaGetLastError());
     return ASOLVE_OK;
@@ -1322,6 +1333,14 @@ double rcond_of(double anorm, double est) {
 
 }  // namespace
 
+// Workspace of the Ozaki-split products: trailing and TRSM updates (K = kLB)
+// and the residuals with more than 8 right-hand sides (K = kOzResK).
+size_t oz_ws_bytes(int64_t n, int64_t nrhs) {
+  const size_t upd = gemm_oz_ws_bytes((int)n, (int)(n > nrhs ? n : nrhs), kLB);
+  const size_t res = nrhs > 8 ? gemm_oz_ws_bytes((int)n, (int)nrhs, (int)std::min<int64_t>(n, kOzResK)) : 0;
+  return upd > res ? upd : res;
+}
+
 size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   const size_t ldw = (size_t)((n + 3) & ~3);
   size_t b = 0;
@@ -1337,7 +1356,7 @@ size_t large_ws_bytes(int64_t n, int64_t nrhs) {
   b += sizeof(int) * (size_t)(((n + 63) / 64) * ((nrhs + kWaveNR - 1) / kWaveNR)) + 1024;  // wave flags
   if (n <= kSvdLargeMax) b += large_svd_ws_bytes(n, nrhs) + 4096;  // SVD fallback (V, sigma, coefficients)
   b += sizeof(double) * (size_t)n * (kGmresM + 4) + sizeof(double) * (kGmresM + 2) + 2048;  // GMRES-IR
-  b += gemm_oz_ws_bytes((int)n, (int)(n > nrhs ? n : nrhs), kLB) + 256;  // Ozaki-split FP64 updates
+  b += oz_ws_bytes(n, nrhs) + 256;  // Ozaki-split FP64 updates and residuals
   return b + (1 << 20);
 }
 
@@ -1445,12 +1464,12 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (!R || !Pres || !xs || !tmp || !ev || !exi || !colmax) return ASOLVE_E_NOMEM;
   // FP64 updates as Ozaki-split tensor products in every mode but the plain
   // FP64 one (which keeps the mma.sync f64 GEMM)
-  void* ozws = a.precision != ASOLVE_PREC_FP64 ? ar.take(gemm_oz_ws_bytes(n, n > nrhs ? n : nrhs, kLB)) : nullptr;
+  void* ozws = a.precision != ASOLVE_PREC_FP64 ? ar.take(oz_ws_bytes(n, nrhs)) : nullptr;
   // FP64 normwise backward error of X, the maximum over the columns
   auto backward_error = [&](double& be) -> int {
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
     {
-      const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+      const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
       if (rr_) return rr_;
     }
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
@@ -1555,7 +1574,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if (a.flags & ASOLVE_BERR) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
       {
-        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
         if (rr_) return rr_;
       }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
@@ -1625,7 +1644,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     for (int it = 0;; ++it) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
       {
-        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
         if (rr_) return rr_;
       }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
@@ -1773,7 +1792,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     for (int it = 0;; ++it) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
       {
-        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
         if (rr_) return rr_;
       }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
@@ -1857,7 +1876,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
     if (a.flags & ASOLVE_BERR) {
       LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 2 * nrhs, st));
       {
-        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
         if (rr_) return rr_;
       }
       k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
@@ -1999,7 +2018,7 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (a.flags & ASOLVE_BERR) {
     LCK(cudaMemsetAsync(colmax, 0, sizeof(unsigned long long) * 3 * nrhs, st));
     {
-        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st);
+        const int rr_ = residual_large(a.A, n, a.B, a.X, nrhs, R, colmax, Pres, a.num_sms, st, ozws, werr);
         if (rr_) return rr_;
       }
     k_colmax_abs<double><<<dim3(64, nrhs), 256, 0, st>>>(a.X, n, nrhs, colmax + nrhs);
