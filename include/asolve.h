@@ -171,7 +171,10 @@ typedef struct {           /* 64 bytes, one per system */
                               bit 5: refined by GMRES-IR (large path, BF16 / FP16 modes),
                               bit 6: large path, FP64 updates as Ozaki-split tensor-core
                               products (ASOLVE_PREC_FP64_OZ, or a mixed mode's FP64
-                              re-factorisation) */
+                              re-factorisation),
+                              bit 7: band system of n >= 2048 re-solved by the sequential
+                              kernels after the partitioned sweeps' answer missed a
+                              backward error of 2^-46 */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */

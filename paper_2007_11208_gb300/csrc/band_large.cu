@@ -1289,7 +1289,7 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
     }
     BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
     // long systems with windows of up to kSwMaxWs: partitioned sweeps
-    const bool par = n >= kSwMinN && kv + 1 <= kSwMaxWs;
+    bool par = n >= kSwMinN && kv + 1 <= kSwMaxWs;
     SweepPlan pl{};
     if (par) {
       char* q = region;
@@ -1315,8 +1315,18 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
         return info->status = src;
       for (int64_t c = 0; c < nrhs; ++c)
         if ((src = sw_apply(pl, a.X + (size_t)c * n, false, st))) return info->status = src;
-    } else
-    switch (R) {
+      // the sweeps chain transfer matrices, which can amplify rounding on a
+      // band that is not dominant: their answer stands only with a backward
+      // error below 2^-46, else the sequential kernels solve again
+      double pbe = 0.0;
+      if ((src = band_berr(a, kl, ku, norminf, colmax, &pbe, st))) return info->status = src;
+      if (!(pbe <= kSpkBerrMax)) {
+        BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
+        par = false;
+        info->detail |= 128;  // re-solved sequentially
+      }
+    }
+    if (!par) switch (R) {
       case 1: k_band_solve<1><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
       case 2: k_band_solve<2><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
       case 4: k_band_solve<4><<<(unsigned)nrhs, 32, 0, st>>>(F, ldf, (int)n, kl, ku, piv, a.X); break;
