@@ -274,6 +274,8 @@ def large_case_roofline(kind, prec, n, nrhs, ms, peaks):
         peak, unit_src = max(pdfma, pdmma), "FP64 pipe, " + src
     elif prec == "mixed":
         peak, unit_src = bf16 / 6.0, f"3xTF32 = bf16 {peaks['src']} / 6"
+    elif prec == "fp8":
+        peak, unit_src = 2.0 * bf16, f"FP8 = bf16 {peaks['src']} x 2 (nominal dense ratio 4.5 / 2.25)"
     else:
         peak, unit_src = bf16, f"bf16 {peaks['src']} (burst)"
     t_alu = flops / peak
@@ -603,7 +605,7 @@ def large_workload(args):
     kinds = args.kinds.split(",")
     nrhs_list = [int(x) for x in args.nrhs_list.split(",")]
     precs = [(asolve.PREC_MIXED, "mixed"), (asolve.PREC_FP64, "fp64"), (asolve.PREC_BF16, "bf16"),
-             (asolve.PREC_FP16, "fp16"), (asolve.PREC_FP64_OZ, "fp64_oz")]
+             (asolve.PREC_FP16, "fp16"), (asolve.PREC_FP64_OZ, "fp64_oz"), (asolve.PREC_FP8, "fp8")]
     precs = [p for p in precs if p[1] in args.precs.split(",")]
     ctxs = {p: asolve.Context(precision=p) for p, _ in precs}
     peaks = load_peaks()
@@ -656,7 +658,7 @@ def large_workload(args):
     head = [c for c in cases if c["n"] == sizes[-1] and c["kind"] == "general" and c["kappa"] == 1e4
             and c["nrhs"] == 1]
     head = head[0] if head else cases[-1]
-    hp = next(p for p in ("mixed", "fp64", "fp64_oz", "bf16", "fp16") if p in head)
+    hp = next(p for p in ("mixed", "fp64", "fp64_oz", "bf16", "fp16", "fp8") if p in head)
     ok = head[hp]["rc"] == 0 and head[hp]["berr"] <= BERR_BAR
     cpu = None
     if args.cpu_baseline:
@@ -1126,7 +1128,7 @@ def main():
     ap.add_argument("--kinds", default="general,spd", help="large: matrix kinds (general, spd, lower)")
     ap.add_argument("--kappas", default="1e2,1e4,1e6", help="large: condition numbers")
     ap.add_argument("--nrhs-list", default="1,64", help="large: right-hand-side counts")
-    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions (mixed, fp64, bf16, fp16, fp64_oz)")
+    ap.add_argument("--precs", default="mixed,fp64", help="large: precisions (mixed, fp64, bf16, fp16, fp64_oz, fp8)")
     ap.add_argument("--templates", type=int, default=40, help="serve: distinct request matrices")
     ap.add_argument("--requests", type=int, default=160, help="serve: requests per load point")
     ap.add_argument("--load", default="0.25,0.5,0.8", help="serve: arrival rates as fractions of capacity")

@@ -104,6 +104,11 @@ extern "C" {
                                    FP64 re-factorisations of the mixed modes' large systems
                                    use the same products.  asolve_info.precision reports
                                    ASOLVE_PREC_FP64 and detail bit 6 (64) */
+#define ASOLVE_PREC_FP8     5   /* the FP8 experiment: as FP16 with FP8 E4M3 operands
+                                   (kind::f8f6f4, per-tile power-of-two scaling) in the
+                                   large path's trailing updates; classical refinement
+                                   gate 1e1 (unit roundoff 2^-4), GMRES-IR to kappa 1e3,
+                                   else the FP64 re-factorisation */
 
 /* ---- flags ----------------------------------------------------------- */
 #define ASOLVE_NO_APPROX     0x01u  /* disable the SVD fallback (Sec. 2.5 option) */
@@ -341,13 +346,15 @@ int asolve_scan_noalloc(const double* A, int64_t n, asolve_scan_result* out, voi
  * remainder (three products, FP32-level accuracy), ASOLVE_GEMM_TF32 (1) is
  * plain TF32, ASOLVE_GEMM_BF16 / ASOLVE_GEMM_FP16 round every operand once
  * to the 16-bit type (FP16 tiles scaled by powers of two from each tile's
- * largest magnitude).  err: optional device int set to 1 if a device-side
+ * largest magnitude), ASOLVE_GEMM_FP8 to FP8 E4M3 (kind::f8f6f4, per-tile
+ * power-of-two scales as FP16; the configuration's FP8 experiment).  err: optional device int set to 1 if a device-side
  * wait gave up.  Asynchronous on `stream`.  Errors: E_INVALID for another
  * `passes` value. */
 #define ASOLVE_GEMM_TF32    1
 #define ASOLVE_GEMM_TF32X3  3
 #define ASOLVE_GEMM_BF16    16
 #define ASOLVE_GEMM_FP16    17
+#define ASOLVE_GEMM_FP8     18
 int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t lda, const float* B, int64_t ldb,
                     int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream);
 

@@ -22,8 +22,8 @@ E_INVALID, E_NONFINITE, E_SINGULAR, E_NOMEM, E_CUDA, E_TIMEOUT, E_IR_STALL, E_UN
 CLS_NONE, CLS_BANDED, CLS_LOWER, CLS_UPPER, CLS_SYMPD, CLS_GENERAL = range(6)
 (ROUTE_NONE, ROUTE_BAND_LU, ROUTE_TRI_LOWER, ROUTE_TRI_UPPER, ROUTE_CHOL,
  ROUTE_CHOL_FAIL_LU, ROUTE_LU, ROUTE_SVD, ROUTE_TRIDIAG, ROUTE_LDLT, ROUTE_CHOL_FAIL_LDLT) = range(11)
-PREC_FP64, PREC_MIXED, PREC_BF16, PREC_FP16, PREC_FP64_OZ = 0, 1, 2, 3, 4
-GEMM_TF32, GEMM_TF32X3, GEMM_BF16, GEMM_FP16 = 1, 3, 16, 17
+PREC_FP64, PREC_MIXED, PREC_BF16, PREC_FP16, PREC_FP64_OZ, PREC_FP8 = 0, 1, 2, 3, 4, 5
+GEMM_TF32, GEMM_TF32X3, GEMM_BF16, GEMM_FP16, GEMM_FP8 = 1, 3, 16, 17, 18
 NO_APPROX, FORCE_LU, FORCE_SVD, NO_RCOND, SYNC, HOST_BUFFERS, BERR, RESIDENT, TRIDIAG, SYM_INDEF = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80, 0x100, 0x200)
 

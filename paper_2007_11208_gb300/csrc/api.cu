@@ -170,7 +170,7 @@ extern "C" int asolve_create(asolve_ctx** out, const asolve_config* cfg) {
   if (!c) return ASOLVE_E_NOMEM;
   if (cfg) c->cfg = *cfg;
   else asolve_default_config(&c->cfg);
-  if (c->cfg.precision < ASOLVE_PREC_FP64 || c->cfg.precision > ASOLVE_PREC_FP64_OZ) {
+  if (c->cfg.precision < ASOLVE_PREC_FP64 || c->cfg.precision > ASOLVE_PREC_FP8) {
     delete c;
     return ASOLVE_E_INVALID;
   }
@@ -619,7 +619,7 @@ extern "C" int asolve_gemm_sub(float* C, int64_t ldc, const float* A, int64_t ld
                                int64_t M, int64_t N, int64_t K, int passes, int* err, void* stream) {
   if (!C || !A || !B || M < 0 || N < 0 || K < 0 ||
       (passes != ASOLVE_GEMM_TF32 && passes != ASOLVE_GEMM_TF32X3 && passes != ASOLVE_GEMM_BF16 &&
-       passes != ASOLVE_GEMM_FP16))
+       passes != ASOLVE_GEMM_FP16 && passes != ASOLVE_GEMM_FP8))
     return ASOLVE_E_INVALID;
   if (ldc < (M > 0 ? M : 1) || lda < (M > 0 ? M : 1) || ldb < (K > 0 ? K : 1)) return ASOLVE_E_INVALID;
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX || ldc > INT32_MAX || lda > INT32_MAX || ldb > INT32_MAX)

@@ -55,6 +55,7 @@ constexpr int kCtaThreads = 256;   // threads of the per-system (class) kernels
 constexpr double kEps = 2.220446049250313080847e-16;  // 2^-52, machine epsilon
 constexpr int kGemmBf16 = ASOLVE_GEMM_BF16;  // operand modes of launch_gemm_tc
 constexpr int kGemmFp16 = ASOLVE_GEMM_FP16;
+constexpr int kGemmFp8 = ASOLVE_GEMM_FP8;
 // kappa limits of refinement with 16-bit trailing updates (unit roundoff
 // 2^-8 for BF16, 2^-11 for FP16, times a margin for the growth of |L||U|)
 constexpr double kKappaLimitBf16 = 1e3;
@@ -64,6 +65,10 @@ constexpr double kKappaLimitFp16 = 1e4;
 // far beyond the classical refinement's limit
 constexpr double kKappaLimitGmresBf16 = 1e7;
 constexpr double kKappaLimitGmresFp16 = 1e8;
+// FP8 E4M3 trailing updates (unit roundoff 2^-4): classical refinement only
+// for the best-conditioned systems; GMRES-IR to kappa 1e3
+constexpr double kKappaLimitFp8 = 1e1;
+constexpr double kKappaLimitGmresFp8 = 1e3;
 
 // Scan flags (Sec. 2.1, 2.2, Fig. 4).
 enum : int32_t {

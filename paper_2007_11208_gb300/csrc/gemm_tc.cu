@@ -29,6 +29,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 
 #include "asolve_internal.cuh"
 
@@ -69,6 +70,17 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t tmem_d, uint64_t ad, uint64_
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
       "l"(ad), "l"(bd), "r"(IDESC), "r"(accum));
+}
+
+// Instruction descriptor of kind::f8f6f4: D = F32, A = B = E4M3 (type 0),
+// both K-major, N = 128, M = 128.
+constexpr uint32_t kIdescE4m3 = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma_f8(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accum) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(kIdescE4m3), "r"(accum));
 }
 
 __device__ __forceinline__ void tc_mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accum) {
@@ -134,12 +146,27 @@ __device__ __forceinline__ uint32_t pack16(float lo, float hi, float s) {
 }
 
 // exponent of the power-of-two scale that brings a tile's largest magnitude
-// m into [2^14, 2^15) (FP16 range), clamped to +-60 so that both scales and
-// the product that undoes them stay normal FP32 numbers; 0 for a zero or
-// non-finite tile
+// m into [2^14, 2^15) (FP16 range; FP8 E4M3, whose largest value is 448:
+// [2^7, 2^8)), clamped to +-60 so that both scales and the product that
+// undoes them stay normal FP32 numbers; 0 for a zero or non-finite tile
+template <int OP = kGemmFp16>
 __device__ __forceinline__ int tile_shift(float m) {
   if (!(m > 0.f) || !(m <= 3.0e38f)) return 0;
-  return max(-60, min(60, 14 - ilogbf(m)));
+  return max(-60, min(60, (OP == kGemmFp8 ? 7 : 14) - ilogbf(m)));
+}
+
+// four consecutive-K elements, scaled, rounded to E4M3 (saturating) and
+// packed, element k in the lowest byte
+__device__ __forceinline__ uint32_t pack8(float v0, float v1, float v2, float v3, float s) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v0 * s, v1 * s), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v2 * s, v3 * s), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xffffu) | (hi << 16);
+}
+
+// byte offset of element (row r, k) of a 128 x 128 K-major tile of 8-bit
+// elements: the core-matrix geometry of the 16-bit tiles (8 rows x 16 bytes)
+__device__ __forceinline__ uint32_t tc_off8(int r, int k) {
+  return (uint32_t)((((r >> 3) * 8 + (k >> 4)) * 128) + ((r & 7) * 16) + (k & 15));
 }
 
 // TF32 head of x (low 13 mantissa bits cleared) and the remainder.
@@ -301,12 +328,15 @@ __global__ void __launch_bounds__(kTcThreads, 3)
 }
 
 // 16-bit operands (OP = kGemmBf16 or kGemmFp16): K chunks of 64, four
-// K = 16 MMAs per chunk; otherwise the structure of k_gemm_tc.
+// K = 16 MMAs per chunk; FP8 E4M3 (OP = kGemmFp8): K chunks of 128, four
+// K = 32 MMAs of kind::f8f6f4 (the same bytes per chunk and core-matrix
+// geometry); otherwise the structure of k_gemm_tc.
 template <bool TRANS_B, bool LOWER, int OP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gemm_tc16(float* __restrict__ C, int ldc, const float* __restrict__ A, int lda, const float* __restrict__ B,
                 int ldb, int M, int N, int K, int* err, long long wait_limit) {
-  constexpr int kK = 64;
+  constexpr bool kF8 = OP == kGemmFp8;
+  constexpr int kK = kF8 ? 128 : 64;
   constexpr uint32_t kIdesc = OP == kGemmBf16 ? kIdescBf16 : kIdescFp16;
   if (LOWER && blockIdx.y > blockIdx.x) return;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -330,7 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // FP16: scales from the largest magnitudes of this tile's A rows and B
   // columns over all of K
   int sha = 0, shb = 0;
-  if (OP == kGemmFp16) {
+  if (OP == kGemmFp16 || kF8) {
     float am = 0.f, bm = 0.f;
     for (int k = w; k < K; k += kTcThreads / 32)
       for (int r = lane; r < kTcM; r += 32)
@@ -357,15 +387,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  if (OP == kGemmFp16) {
+  if (OP == kGemmFp16 || kF8) {
     float am = 0.f, bm = 0.f;
 #pragma unroll
     for (int q = 0; q < kTcThreads / 32; ++q) {
       am = fmaxf(am, s_max[0][q]);
       bm = fmaxf(bm, s_max[1][q]);
     }
-    sha = tile_shift(am);
-    shb = tile_shift(bm);
+    sha = tile_shift<OP>(am);
+    shb = tile_shift<OP>(bm);
   }
   const float sa = ldexpf(1.f, sha), sb = ldexpf(1.f, shb);
   const uint32_t tmem = tmem_base;
@@ -374,6 +404,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nchunks = (K + kK - 1) / kK;
   for (int ch = 0; ch < nchunks && ok; ++ch) {
     const int k0 = ch * kK;
+    if constexpr (kF8) {
+      // FP8: quadruples (r, k..k+3), lanes over r; (n, k..k+3), lanes over k
+      // (over n when B is given transposed)
+      for (int e = tid; e < kTcM * kK / 4; e += kTcThreads) {
+        const int r = e & (kTcM - 1), k = 4 * (e >> 7);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (m0 + r < M)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (k0 + k + q < K) v[q] = __ldg(A + (size_t)(k0 + k + q) * lda + m0 + r);
+        *reinterpret_cast<uint32_t*>(sA + tc_off8(r, k)) = pack8(v[0], v[1], v[2], v[3], sa);
+      }
+      for (int e = tid; e < kTcN * kK / 4; e += kTcThreads) {
+        const int n = TRANS_B ? (e & (kTcN - 1)) : (e >> 5);
+        const int k = TRANS_B ? 4 * (e >> 7) : 4 * (e & 31);
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (n0 + n < N)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (k0 + k + q < K)
+              v[q] = TRANS_B ? __ldg(B + (size_t)(k0 + k + q) * ldb + n0 + n)
+                             : __ldg(B + (size_t)(n0 + n) * ldb + k0 + k + q);
+        *reinterpret_cast<uint32_t*>(sB + tc_off8(n, k)) = pack8(v[0], v[1], v[2], v[3], sb);
+      }
+    } else {
     // A: element pairs (r, k), (r, k + 1); lanes over r
     for (int e = tid; e < kTcM * kK / 2; e += kTcThreads) {
       const int r = e & (kTcM - 1), k = 2 * (e >> 7);
@@ -401,15 +456,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       *reinterpret_cast<uint32_t*>(sB + tc_off16(n, k)) = pack16<OP>(v0, v1, sb);
     }
+    }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < kK / 16; ++j) {  // K = 16 per MMA: two core matrices
+      for (int j = 0; j < 4; ++j) {  // K = 16 (FP8: 32) per MMA: two core matrices
         const uint32_t off = (uint32_t)j * 256;
-        tc_mma_f16<kIdesc>(tmem, tc_desc(smem_u32(sA) + off, 128, 1024), tc_desc(smem_u32(sB) + off, 128, 1024),
-                           (ch > 0 || j > 0) ? 1u : 0u);
+        if constexpr (kF8)
+          tc_mma_f8(tmem, tc_desc(smem_u32(sA) + off, 128, 1024), tc_desc(smem_u32(sB) + off, 128, 1024),
+                    (ch > 0 || j > 0) ? 1u : 0u);
+        else
+          tc_mma_f16<kIdesc>(tmem, tc_desc(smem_u32(sA) + off, 128, 1024), tc_desc(smem_u32(sB) + off, 128, 1024),
+                             (ch > 0 || j > 0) ? 1u : 0u);
       }
       tc_commit(mbar_a);
     }
@@ -511,6 +571,8 @@ cudaError_t launch_gemm_tc(float* C, int ldc, const float* A, int lda, const flo
     return launch_gemm_tc16<kGemmBf16>(C, ldc, A, lda, B, ldb, M, N, K, err, st, trans_b, lower);
   if (passes == kGemmFp16)
     return launch_gemm_tc16<kGemmFp16>(C, ldc, A, lda, B, ldb, M, N, K, err, st, trans_b, lower);
+  if (passes == kGemmFp8)
+    return launch_gemm_tc16<kGemmFp8>(C, ldc, A, lda, B, ldb, M, N, K, err, st, trans_b, lower);
   if (trans_b && lower) return launch_gemm_tc_t<true, true>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
   if (trans_b) return launch_gemm_tc_t<true, false>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);
   if (lower) return launch_gemm_tc_t<false, true>(C, ldc, A, lda, B, ldb, M, N, K, passes, err, st);

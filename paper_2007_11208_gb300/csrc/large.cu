@@ -1905,11 +1905,15 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
   if (a.precision != ASOLVE_PREC_FP64 && a.precision != ASOLVE_PREC_FP64_OZ && !(sr.flags & SF_NORM_FP64)) {
     if ((rc = set_large_attrs<float>())) return rc;
     Fac<float> f{static_cast<float*>(Wv), ldw, piv, perm, static_cast<float*>(Dtmp), fail, pb, wb};
-    f.gemm_mode = a.precision == ASOLVE_PREC_BF16 ? kGemmBf16 : (a.precision == ASOLVE_PREC_FP16 ? kGemmFp16 : 3);
+    f.gemm_mode = a.precision == ASOLVE_PREC_BF16   ? kGemmBf16
+                  : a.precision == ASOLVE_PREC_FP16 ? kGemmFp16
+                  : a.precision == ASOLVE_PREC_FP8  ? kGemmFp8
+                                                    : 3;
     // the refinement converges while kappa times the factors' relative
     // error stays below one: the 16-bit updates lower the kappa limit
     const double klim = a.precision == ASOLVE_PREC_BF16   ? fmin(a.ir_kappa_limit, kKappaLimitBf16)
                         : a.precision == ASOLVE_PREC_FP16 ? fmin(a.ir_kappa_limit, kKappaLimitFp16)
+                        : a.precision == ASOLVE_PREC_FP8  ? fmin(a.ir_kappa_limit, kKappaLimitFp8)
                                                           : a.ir_kappa_limit;
     for (int attempt = 0; attempt < 2; ++attempt) {
       const bool try_chol = chol && attempt == 0;
@@ -1932,8 +1936,11 @@ int large_solve(const LargeArgs& a, void* ws, size_t ws_bytes, asolve_info* info
       double rcv = NAN;
       bool gate_ok = true;
       // the 16-bit modes also have GMRES-IR, which reaches much larger kappa
-      const bool sixteen = a.precision == ASOLVE_PREC_BF16 || a.precision == ASOLVE_PREC_FP16;
-      const double klim_gm = a.precision == ASOLVE_PREC_BF16 ? kKappaLimitGmresBf16 : kKappaLimitGmresFp16;
+      const bool sixteen =
+          a.precision == ASOLVE_PREC_BF16 || a.precision == ASOLVE_PREC_FP16 || a.precision == ASOLVE_PREC_FP8;
+      const double klim_gm = a.precision == ASOLVE_PREC_BF16   ? kKappaLimitGmresBf16
+                             : a.precision == ASOLVE_PREC_FP16 ? kKappaLimitGmresFp16
+                                                               : kKappaLimitGmresFp8;
       bool gm_ok = sixteen;
       if (!no_rcond) {
         double est;

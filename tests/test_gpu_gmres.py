@@ -67,3 +67,35 @@ def test_gmres_ir_large(orc, prec_name, n, kappa):
         Xo, io = orc.solve(A, b)
         assert io["route"] == orc.ROUTE_LU and io["status"] == 0
         assert np.abs(x - Xo).max() / np.abs(Xo).max() <= EPS * n * kinf_bound
+
+
+@pytest.mark.parametrize("n,kappa", [(2048, 1e1), (2048, 1e2), (4096, 1e2)])
+def test_fp8_experiment(orc, n, kappa):
+    """FP8 E4M3 trailing updates (the configuration's experiment): the
+    answer meets the same bars whichever way it comes -- GMRES-IR on the FP8
+    factors (precision FP8, detail bit 5) or the FP64 re-factorisation
+    after the gate or a stall (detail bits 0 / 1)."""
+    from paper_2007_11208_gb300 import asolve, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    g = synth.gen(int(n + 7 * kappa) % 100003, dev)
+    M = synth.spectrum_fast(n, g, kappa, spd=False, device=dev)
+    xt = synth.rhs(n, 1, g, dev)
+    B = (M.t() @ xt.t()).t().contiguous()
+    X = torch.zeros_like(B)
+    ctx = asolve.Context(precision=asolve.PREC_FP8)
+    rc, info = ctx.solve(M, B, n, 1, X, asolve.BERR)
+    torch.cuda.synchronize()
+    ctx.close()
+    A = M.cpu().numpy().T
+    b = B.cpu().numpy().reshape(n, 1)
+    x = X.cpu().numpy().reshape(n, 1)
+    sr = orc.scan(A)
+    assert rc == 0 and (info["cls"], info["kl"], info["ku"], info["route"]) == \
+        (sr["cls"], sr["kl"], sr["ku"], orc.ROUTE_LU), info
+    assert (info["precision"] == asolve.PREC_FP8 and info["detail"] & 32) or \
+        (info["precision"] == asolve.PREC_FP64 and info["detail"] & 3), info
+    _, berr = orc.residual_dot2(A, x, b)
+    assert berr.max() <= BERR, berr
+    xtrue = xt.cpu().numpy().reshape(n, 1)
+    assert np.abs(x - xtrue).max() / np.abs(xtrue).max() <= 2.0 ** -52 * n * n * kappa, info
