@@ -177,9 +177,11 @@ typedef struct {           /* 64 bytes, one per system */
                               bit 6: large path, FP64 updates as Ozaki-split tensor-core
                               products (ASOLVE_PREC_FP64_OZ, or a mixed mode's FP64
                               re-factorisation),
-                              bit 7: band system of n >= 2048 re-solved by the sequential
-                              kernels after the partitioned sweeps' answer missed a
-                              backward error of 2^-46 */
+                              bit 7: band system of n >= 2048 whose partitioned sweeps'
+                              answer missed a backward error of 2^-46 and was refined
+                              in FP64 with the same sweeps,
+                              bit 8: ... and re-solved by the sequential kernels when
+                              that refinement did not reach 2^-46 either */
 } asolve_info;
 
 typedef struct {           /* result of the property scan alone (Sec. 2.1, 2.2, Fig. 4) */

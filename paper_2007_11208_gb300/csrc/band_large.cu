@@ -378,6 +378,26 @@ __global__ void __launch_bounds__(32) k_band_est(double* F, int ldf, int n, int 
 
 // ------------------------------------------------------------ berr
 // Per column: max |b - A x|, max |x|, max |b| (FP64; A read in its input form).
+// r = b - A x for one right-hand side (A in band storage or dense), and
+// x += d, the refinement steps of the partitioned sweeps.
+__global__ void k_band_resid(const double* __restrict__ AB, int64_t ldab, int kud, const double* __restrict__ A,
+                             int64_t n, int kl, int ku, const double* __restrict__ b, const double* __restrict__ x,
+                             double* __restrict__ r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = i - kl > 0 ? i - kl : 0, hi = i + ku < n - 1 ? i + ku : n - 1;
+    double acc = 0.0;
+    for (int64_t j = lo; j <= hi; ++j) {
+      const double a = A ? A[(size_t)j * n + i] : AB[(size_t)(kud + i - j) + (size_t)j * ldab];
+      acc = fma(a, x[j], acc);
+    }
+    r[i] = b[i] - acc;
+  }
+}
+__global__ void k_band_xadd(double* __restrict__ x, const double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += d[i];
+}
+
 __global__ void k_band_berr(const double* __restrict__ AB, int64_t ldab, int kud, const double* __restrict__ A,
                             int64_t n, int kl, int ku, const double* __restrict__ B, const double* __restrict__ X,
                             int nrhs, unsigned long long* colmax) {
@@ -630,6 +650,7 @@ __global__ void __launch_bounds__(128) k_sw_out(SweepCtx c, int ws, const double
 
 constexpr int kSwMaxWs = 72;     // widest window of the partitioned sweeps
 constexpr int64_t kSwMinN = 2048;  // shorter systems keep the one-warp sweeps
+constexpr int kSwRefineSteps = 3;  // refinement steps after the sweeps before the sequential solve
 
 struct SweepPlan {
   SweepCtx c;
@@ -1317,13 +1338,29 @@ int band_solve(const BandArgs& a, void* ws, size_t ws_bytes, asolve_info* info) 
         if ((src = sw_apply(pl, a.X + (size_t)c * n, false, st))) return info->status = src;
       // the sweeps chain transfer matrices, which can amplify rounding on a
       // band that is not dominant: their answer stands only with a backward
-      // error below 2^-46, else the sequential kernels solve again
+      // error below 2^-46.  Short of it, FP64 refinement with the same
+      // sweeps (r = b - A x, x += A^-1 r; a few steps at O(n (kl + ku))
+      // each), and if that does not get there either the sequential kernels
+      // solve again (and estimate).
       double pbe = 0.0;
       if ((src = band_berr(a, kl, ku, norminf, colmax, &pbe, st))) return info->status = src;
+      for (int it = 0; it < kSwRefineSteps && !(pbe <= kSpkBerrMax); ++it) {
+        info->detail |= 128;
+        const unsigned g = (unsigned)((n + 255) / 256 < 4 * 152 ? (n + 255) / 256 : 4 * 152);
+        for (int64_t c = 0; c < nrhs; ++c) {
+          k_band_resid<<<g, 256, 0, st>>>(a.AB, a.ldab, (int)a.kud, a.A, n, kl, ku, a.B + (size_t)c * n,
+                                           a.X + (size_t)c * n, ev);
+          BCK(cudaGetLastError());
+          if ((src = sw_apply(pl, ev, false, st))) return info->status = src;
+          k_band_xadd<<<g, 256, 0, st>>>(a.X + (size_t)c * n, ev, n);
+          BCK(cudaGetLastError());
+        }
+        if ((src = band_berr(a, kl, ku, norminf, colmax, &pbe, st))) return info->status = src;
+      }
       if (!(pbe <= kSpkBerrMax)) {
         BCK(cudaMemcpyAsync(a.X, a.B, sizeof(double) * (size_t)(n * nrhs), cudaMemcpyDeviceToDevice, st));
         par = false;
-        info->detail |= 128;  // re-solved sequentially
+        info->detail |= 256;  // re-solved sequentially
       }
     }
     if (!par) switch (R) {

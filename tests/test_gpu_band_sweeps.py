@@ -3,9 +3,11 @@ several decades (the serving workload's banded requests, kappa up to
 1e12): they take the band route's partitioned sweeps, whose chained
 transfer matrices can amplify rounding when the band is not dominant.  The
 route keeps their answer only below a backward error of 2^-46 and else
-solves again with the sequential kernels (asolve_info.detail bit 7).  Bar:
+solves again (see below).  Bar:
 class, route and bandwidths as the oracle's, backward error <= 1e-13 by the
-oracle's compensated residual, X within the forward-error bound."""
+oracle's compensated residual, X within the forward-error bound.  (Short of
+2^-46 the route first refines the sweeps' answer in FP64 with the same
+sweeps, detail bit 7, and only then solves sequentially, bit 8.)"""
 import numpy as np
 import pytest
 import torch
