@@ -270,7 +270,7 @@ __device__ bool refine(const BatchDesc& d, const double* __restrict__ A, const d
   iters = 0;
   bool ok = false;
   for (int it = 0;; ++it) {
-    cta_residual(A, n, n, B, xd, nrhs, R, s_rmax, red);
+    cta_residual(A, n, n, B, xd, nrhs, R, s_rmax);
     double berr = 0.0;
     for (int c = 0; c < nrhs; ++c) {
       double xm = 0.0, bm = 0.0;
@@ -318,7 +318,7 @@ __device__ bool refine(const BatchDesc& d, const double* __restrict__ A, const d
 __device__ double berr_fp64(const double* __restrict__ A, const double* __restrict__ B, int n, int nrhs,
                             double norminf, const double* xd, double* R, CtaRed& red) {
   __shared__ double s_rmax[8];
-  cta_residual(A, n, n, B, xd, nrhs, R, s_rmax, red);
+  cta_residual(A, n, n, B, xd, nrhs, R, s_rmax);
   double berr = 0.0;
   for (int c = 0; c < nrhs; ++c) {
     double xm = 0.0, bm = 0.0;
@@ -581,12 +581,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
         if (threadIdx.x == 0) d.info[s].berr = be;
       }
       if (!(d.flags & ASOLVE_NO_RCOND)) {
-        // (the transposed solves use warp-per-row sums here: A itself is
-        // the factor, mostly outside L2, and staging tiles measured slower)
         double* v = reinterpret_cast<double*>(smem);
         double* xi = v + n;
+        double* stage = reinterpret_cast<double*>(smem + kEstStageOff);
         auto apply_est = [&](double* x, bool tr) {
-          cta_tri_solve<double, double>(A, n, n, lower, tr, false, x, n, 1);
+          cta_tri_solve<double, double>(A, n, n, lower, tr, false, x, n, 1, nullptr, stage);
         };
         double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
         rc = rcond_from(sr.norm1, est);

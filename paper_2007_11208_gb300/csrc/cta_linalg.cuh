@@ -530,6 +530,84 @@ __device__ __noinline__ void cta_block_inverses(const T* __restrict__ M, int ldm
   __syncthreads();
 }
 
+// Compile-time right-hand-side count: with_nr(nrhs, f) calls f with an
+// IntC<nrhs> (1 <= nrhs <= 8), so that per-column loops unroll to exactly
+// nrhs operations.  A loop over 8 columns predicated on c < nrhs still
+// issues all 8 instructions per warp, and on GB300's FP64 pipe (2 lanes
+// per clock per SM) every issued FP64 warp instruction costs 16 SM cycles
+// whether its lanes are on or off.
+template <int N>
+struct IntC {
+  static constexpr int value = N;
+};
+template <typename F>
+__device__ __forceinline__ void with_nr(int nrhs, F&& f) {
+  switch (nrhs) {
+    case 0: break;
+    case 1: f(IntC<1>{}); break;
+    case 2: f(IntC<2>{}); break;
+    case 3: f(IntC<3>{}); break;
+    case 4: f(IntC<4>{}); break;
+    case 5: f(IntC<5>{}); break;
+    case 6: f(IntC<6>{}); break;
+    case 7: f(IntC<7>{}); break;
+    default: f(IntC<8>{}); break;
+  }
+}
+
+// Row update of a blocked triangular solve, E = M:  x(r, :) -= M(r, b0 +
+// j) x(b0 + j, :) for rows r_lo <= r < r_hi, j < bs; thread per row,
+// coalesced over r, the block's loads of M unrolled so that they are in
+// flight together.
+template <int NR, typename T, typename V>
+__device__ __forceinline__ void tri_update_direct(const T* __restrict__ M, int ldm, V* x, int ldx, int b0, int bs,
+                                                  int r_lo, int r_hi) {
+  for (int r = r_lo + (int)threadIdx.x; r < r_hi; r += kThreads) {
+    V acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = V(0);
+#pragma unroll 16
+    for (int j = 0; j < bs; ++j) {
+      const V m = (V)M[(size_t)(b0 + j) * ldm + r];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] += m * x[(size_t)c * ldx + b0 + j];
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) x[(size_t)c * ldx + r] -= acc[c];
+  }
+}
+
+// The same with E = M^T:  x(r, :) -= M(b0 + j, r) x(b0 + j, :).  Each warp
+// stages the 32 x 32 tile M(b0.., r0..) in `tile` (32 x 33) with coalesced
+// column loads, then lane i finishes row r0 + i.
+template <int NR, typename T, typename V>
+__device__ __forceinline__ void tri_update_staged(const T* __restrict__ M, int ldm, V* x, int ldx, int b0, int bs,
+                                                  int r_lo, int r_hi, T* tile) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int r0 = r_lo + 32 * w; r0 < r_hi; r0 += 32 * kWarps) {
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+      const int r = r0 + i;
+      tile[i * 33 + lane] = (r < r_hi && lane < bs) ? M[(size_t)r * ldm + b0 + lane] : T(0);
+    }
+    __syncwarp();
+    const int r = r0 + lane;
+    if (r < r_hi) {
+      V acc[NR];
+#pragma unroll
+      for (int c = 0; c < NR; ++c) acc[c] = V(0);
+      for (int j = 0; j < bs; ++j) {
+        const V m = (V)tile[lane * 33 + j];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] += m * x[(size_t)c * ldx + b0 + j];
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) x[(size_t)c * ldx + r] -= acc[c];
+    }
+    __syncwarp();
+  }
+}
+
 // x (smem, n x nrhs, ld ldx) <- inv(E) x with E = trans ? M^T : M, M lower
 // or upper (ld ldm), unit diagonal if `unit`.  Blocked by 32 rows.  With
 // Dinv (the diagonal-block inverses of M) the block step is a product with
@@ -596,51 +674,11 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
     __syncthreads();
     const int r_lo = ELOWER ? b0 + bs : 0, r_hi = ELOWER ? n : b0;
     if (!trans) {
-      // E(r, j) = M(r, j): thread per row, coalesced over r
-      for (int r = r_lo + threadIdx.x; r < r_hi; r += kThreads) {
-        V acc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = V(0);
-        // unrolled so that the loads of M (global memory) are in flight together
-#pragma unroll 16
-        for (int j = 0; j < bs; ++j) {
-          const V m = (V)M[(size_t)(b0 + j) * ldm + r];
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < nrhs) acc[c] += m * x[(size_t)c * ldx + b0 + j];
-        }
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (c < nrhs) x[(size_t)c * ldx + r] -= acc[c];
-      }
+      with_nr(nrhs, [&](auto nr) { tri_update_direct<decltype(nr)::value, T, V>(M, ldm, x, ldx, b0, bs, r_lo, r_hi); });
     } else if (stage) {
-      // E(r, j) = M(j, r): each warp stages the 32 x 32 tile M(b0.., r0..)
-      // with coalesced column loads, then lane i finishes row r0 + i
-      T* tile = stage + (size_t)w * 32 * 33;
-      for (int r0 = r_lo + 32 * w; r0 < r_hi; r0 += 32 * kWarps) {
-#pragma unroll 8
-        for (int i = 0; i < 32; ++i) {
-          const int r = r0 + i;
-          tile[i * 33 + lane] = (r < r_hi && lane < bs) ? M[(size_t)r * ldm + b0 + lane] : T(0);
-        }
-        __syncwarp();
-        const int r = r0 + lane;
-        if (r < r_hi) {
-          V acc[8];
-#pragma unroll
-          for (int c = 0; c < 8; ++c) acc[c] = V(0);
-          for (int j = 0; j < bs; ++j) {
-            const V m = (V)tile[lane * 33 + j];
-#pragma unroll
-            for (int c = 0; c < 8; ++c)
-              if (c < nrhs) acc[c] += m * x[(size_t)c * ldx + b0 + j];
-          }
-#pragma unroll
-          for (int c = 0; c < 8; ++c)
-            if (c < nrhs) x[(size_t)c * ldx + r] -= acc[c];
-        }
-        __syncwarp();
-      }
+      with_nr(nrhs, [&](auto nr) {
+        tri_update_staged<decltype(nr)::value, T, V>(M, ldm, x, ldx, b0, bs, r_lo, r_hi, stage + (size_t)w * 32 * 33);
+      });
     } else {
       // E(r, j) = M(j, r): warp per row, lanes over j (coalesced), shuffle sums
       for (int r = r_lo + w; r < r_hi; r += kWarps) {
@@ -725,91 +763,63 @@ __device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nr
 
 // -------------------------------------------------------------- residual
 // R = B - A X in FP64 (A: n x n ld lda; X: n x nrhs ld n), writes R (ld n)
-// and the per-column max |r| to rmax_s[c].  For nrhs >= 3 the products run
-// on the FP64 tensor instruction (8 rows x 8 right-hand sides x 4 columns
-// per mma.sync, a warp per 32 rows); otherwise on DFMA, one thread per row.
-__device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
-                                          const double* Xs, int nrhs, double* R, double* rmax_s, CtaRed& red) {
+// and the per-column max |r| to rmax_s[c] (NaN when a column has one).
+// DFMA, one thread per row (coalesced over the rows of column-major A) and
+// exactly nrhs accumulators: the work is n^2 nrhs FP64 FMAs, which bound
+// it on GB300's narrow FP64 pipe (the 8-column mma.sync f64 form would
+// spend n^2 8 whatever nrhs is, at a lower rate than DFMA).
+template <int NR>
+__device__ __forceinline__ void residual_rows(const double* __restrict__ A, int lda, int n,
+                                              const double* __restrict__ B, const double* Xs, double* R,
+                                              unsigned long long* s_mx) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double mx[8];
+  constexpr int U = NR == 1 ? 16 : (NR == 2 ? 8 : (NR <= 4 ? 4 : 2));
+  unsigned long long mx[NR];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) mx[c] = 0.0;
-  if (nrhs >= 3) {
-    // a warp pass covers 4 row groups (32 rows): four independent
-    // accumulator chains and four loads of A per lane per K step
-    constexpr int G = 4;
-    const int g = lane >> 2, t = lane & 3;
-    const bool xok = g < nrhs;
-    for (int r0 = 8 * G * w; r0 < n; r0 += 8 * G * kWarps) {
-      double c0[G], c1[G];
+  for (int c = 0; c < NR; ++c) mx[c] = 0ull;
+  for (int i0 = 32 * w; i0 < n; i0 += kThreads) {  // warp-uniform: idle warps skip
+    const int i = i0 + lane;
+    const bool ok = i < n;
+    double acc[NR];
 #pragma unroll
-      for (int q = 0; q < G; ++q) c0[q] = c1[q] = 0.0;
-#pragma unroll 4
-      for (int k = 0; k < n; k += 4) {
-        const int ka = k + t;
-        const double b = (xok && ka < n) ? Xs[(size_t)g * n + ka] : 0.0;
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const int ra = r0 + 8 * q + g;  // A fragment row
-          const double a = (ra < n && ka < n) ? __ldg(A + (size_t)ka * lda + ra) : 0.0;
-          dmma_8x8x4(c0[q], c1[q], a, b);
-        }
-      }
-      // c0[q], c1[q] = (A X)(r0 + 8q + g, 2t), (A X)(r0 + 8q + g, 2t + 1)
-#pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const int r = r0 + 8 * q + g;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = 2 * t + h;
-          double v = 0.0;
-          if (r < n && c < nrhs) {
-            v = B[(size_t)c * n + r] - (h ? c1[q] : c0[q]);
-            R[(size_t)c * n + r] = v;
-          }
-          // lane holds column c = 2t + h: fold into mx via a per-lane max
-          const double av = fabs(v);
-#pragma unroll
-          for (int cc = 0; cc < 8; ++cc)
-            if (cc == c) mx[cc] = fmax(mx[cc], av);
-        }
-      }
-    }
-  } else {
-    constexpr int kRows = 4;
-    double acc[kRows][2];
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < kRows; ++q) acc[q][0] = acc[q][1] = 0.0;
-#pragma unroll 8
+    for (int c = 0; c < NR; ++c) acc[c] = 0.0;
+#pragma unroll U
     for (int j = 0; j < n; ++j) {
-      const double x0 = Xs[j], x1 = (nrhs > 1) ? Xs[(size_t)n + j] : 0.0;
+      const double a = ok ? __ldg(A + (size_t)j * lda + i) : 0.0;
 #pragma unroll
-      for (int q = 0; q < kRows; ++q) {
-        const int i = tid + q * kThreads;
-        if (i < n) {
-          const double a = __ldg(A + (size_t)j * lda + i);
-          acc[q][0] = fma(a, x0, acc[q][0]);
-          if (nrhs > 1) acc[q][1] = fma(a, x1, acc[q][1]);
-        }
-      }
+      for (int c = 0; c < NR; ++c) acc[c] = fma(a, Xs[(size_t)c * n + j], acc[c]);
     }
+    if (ok) {
 #pragma unroll
-    for (int q = 0; q < kRows; ++q) {
-      const int i = tid + q * kThreads;
-      if (i < n) {
-        for (int c = 0; c < nrhs; ++c) {
-          const double r = B[(size_t)c * n + i] - acc[q][c];
-          R[(size_t)c * n + i] = r;
-          mx[c] = fmax(mx[c], fabs(r));
-        }
+      for (int c = 0; c < NR; ++c) {
+        const double r = B[(size_t)c * n + i] - acc[c];
+        R[(size_t)c * n + i] = r;
+        // |r| as bits: ordered like the values, NaN above every number
+        const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(r));
+        mx[c] = b > mx[c] ? b : mx[c];
       }
     }
   }
-  for (int c = 0; c < nrhs; ++c) {
-    double m = cta_max(mx[c], red);
-    if (threadIdx.x == 0) rmax_s[c] = m;
+#pragma unroll
+  for (int c = 0; c < NR; ++c) {
+    unsigned long long v = mx[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u > v ? u : v;
+    }
+    if (lane == 0) atomicMax(s_mx + c, v);
   }
+}
+
+__device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda, int n, const double* __restrict__ B,
+                                          const double* Xs, int nrhs, double* R, double* rmax_s) {
+  __shared__ unsigned long long s_mx[8];
+  if (threadIdx.x < 8) s_mx[threadIdx.x] = 0ull;
+  __syncthreads();
+  with_nr(nrhs, [&](auto nr) { residual_rows<decltype(nr)::value>(A, lda, n, B, Xs, R, s_mx); });
+  __syncthreads();
+  if (threadIdx.x < nrhs) rmax_s[threadIdx.x] = __longlong_as_double((long long)s_mx[threadIdx.x]);
   __syncthreads();
 }
 
