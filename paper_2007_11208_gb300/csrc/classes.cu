@@ -186,9 +186,9 @@ __device__ __forceinline__ int next_item(const BatchDesc& d, int ctr, int* s_ite
 
 // Dense-class dynamic shared memory: 110 KB (two blocks per SM).
 constexpr int kDenseSmem = 110 * 1024;
-// FP64 estimates: v and xi (2 x 1024 doubles) first, then the 8 warps'
+// FP64 estimates: v (two columns) and xi (3 x 1024 doubles) first, then the 8 warps'
 // 32 x 33 tiles of the transposed triangular updates.
-constexpr int kEstStageOff = 2 * 1024 * 8 + 64;
+constexpr int kEstStageOff = 3 * 1024 * 8 + 64;
 static_assert(kEstStageOff + kWarps * 32 * 33 * 8 <= kDenseSmem, "estimate stage");
 
 // Panel width: the n x nb panel plus the 32 x 33 inverse and two 32 x 64
@@ -367,11 +367,16 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
       cta_block_inverses<float>(W, ldw, n, true, KIND == 0, Li);
       if (KIND == 0) cta_block_inverses<float>(W, ldw, n, false, false, Ui);
       float* v = reinterpret_cast<float*>(smem);
-      float* xi = v + n;
+      float* xi = v + 2 * n;
       float* stage = reinterpret_cast<float*>(smem + 8192 * 2 + 64);  // after v, xi (n <= 1024)
-      auto apply_est = [&](float* x, bool tr) {
-        if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.perm, x, n, 1, tr, tmp, Li, Ui, stage);
-        else cta_chol_apply<float, float>(W, ldw, n, x, n, 1, Li, stage);
+      // the factor's transpose, in the second half of the slot's working
+      // area (sized for an FP64 factor): the transposed solves of the
+      // estimate and of the Cholesky applications read it coalesced
+      float* WT = W + (size_t)ldw * n;
+      if (KIND == 1 || !no_rcond) cta_transpose<float>(W, ldw, n, WT, stage);
+      auto apply_est = [&](float* x, bool tr, int k) {
+        if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.perm, x, n, k, tr, tmp, Li, Ui, stage, WT);
+        else cta_chol_apply<float, float>(W, ldw, n, x, n, k, Li, stage, WT);
       };
       double rc = __longlong_as_double(0x7ff8000000000000ll);
       bool gate_ok = true;
@@ -387,7 +392,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
         float* stage = reinterpret_cast<float*>(smem + (size_t)4 * 1024 * 8 + 64);
         auto apply32 = [&](float* x) {
           if (KIND == 0) cta_lu_apply<float, float>(W, ldw, n, sl.perm, x, n, nrhs, false, tmp, Li, Ui, stage);
-          else cta_chol_apply<float, float>(W, ldw, n, x, n, nrhs, Li, stage);
+          else cta_chol_apply<float, float>(W, ldw, n, x, n, nrhs, Li, stage, WT);
         };
         double berr;
         int iters;
@@ -444,11 +449,11 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
       // FP64 estimate by substitution: on an ill-conditioned factor a
       // product with explicit block inverses would corrupt the estimate
       double* v = reinterpret_cast<double*>(smem);
-      double* xi = v + n;
+      double* xi = v + 2 * n;
       double* stage = reinterpret_cast<double*>(smem + kEstStageOff);
-      auto apply_est = [&](double* x, bool tr) {
-        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, x, n, 1, tr, sl.tmp, nullptr, nullptr, stage);
-        else cta_chol_apply<double, double>(W, ldw, n, x, n, 1, nullptr, stage);
+      auto apply_est = [&](double* x, bool tr, int k) {
+        if (KIND == 0) cta_lu_apply<double, double>(W, ldw, n, sl.perm, x, n, k, tr, sl.tmp, nullptr, nullptr, stage);
+        else cta_chol_apply<double, double>(W, ldw, n, x, n, k, nullptr, stage);
       };
       double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
       rc = rcond_from(sr.norm1, est);
@@ -493,8 +498,8 @@ __device__ void dense_ldlt(const BatchDesc& d, int64_t s, unsigned char* smem, C
     }
     if (!(d.flags & ASOLVE_NO_RCOND)) {
       double* v = reinterpret_cast<double*>(smem);
-      double* xi = v + n;
-      auto apply_est = [&](double* x, bool) { cta_ldlt_solve(W, ldw, n, sl.piv, x, n, 1); };
+      double* xi = v + 2 * n;
+      auto apply_est = [&](double* x, bool, int k) { cta_ldlt_solve(W, ldw, n, sl.piv, x, n, k); };
       const double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
       rc = rcond_from(sr.norm1, est);
     }
@@ -582,10 +587,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
       }
       if (!(d.flags & ASOLVE_NO_RCOND)) {
         double* v = reinterpret_cast<double*>(smem);
-        double* xi = v + n;
+        double* xi = v + 2 * n;
         double* stage = reinterpret_cast<double*>(smem + kEstStageOff);
-        auto apply_est = [&](double* x, bool tr) {
-          cta_tri_solve<double, double>(A, n, n, lower, tr, false, x, n, 1, nullptr, stage);
+        auto apply_est = [&](double* x, bool tr, int k) {
+          cta_tri_solve<double, double>(A, n, n, lower, tr, false, x, n, k, nullptr, stage);
         };
         double est = cta_est_inv_norm1<double>(n, v, xi, apply_est, red);
         rc = rcond_from(sr.norm1, est);

@@ -613,11 +613,13 @@ __device__ __forceinline__ void tri_update_staged(const T* __restrict__ M, int l
 // Dinv (the diagonal-block inverses of M) the block step is a product with
 // the inverse; without it the block is loaded into registers (lane i holds
 // row i) and solved by substitution, one warp per right-hand side.  The
-// rows after the block are then updated by all threads.
+// rows after the block are then updated by all threads.  MT (optional,
+// with E = M^T): M's transpose, ld ldm; the updates then read E's rows
+// as coalesced columns of MT instead of strided rows of M.
 template <typename T, typename V, bool ELOWER>
 __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm, int n, bool trans, bool unit,
                                                V* x, int ldx, int nrhs, const T* __restrict__ Dinv,
-                                               T* stage) {
+                                               T* stage, const T* __restrict__ MT) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nblk = (n + 31) / 32;
   for (int bi = 0; bi < nblk; ++bi) {
@@ -673,8 +675,9 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
     }
     __syncthreads();
     const int r_lo = ELOWER ? b0 + bs : 0, r_hi = ELOWER ? n : b0;
-    if (!trans) {
-      with_nr(nrhs, [&](auto nr) { tri_update_direct<decltype(nr)::value, T, V>(M, ldm, x, ldx, b0, bs, r_lo, r_hi); });
+    if (!trans || MT) {
+      const T* E = trans ? MT : M;
+      with_nr(nrhs, [&](auto nr) { tri_update_direct<decltype(nr)::value, T, V>(E, ldm, x, ldx, b0, bs, r_lo, r_hi); });
     } else if (stage) {
       with_nr(nrhs, [&](auto nr) {
         tri_update_staged<decltype(nr)::value, T, V>(M, ldm, x, ldx, b0, bs, r_lo, r_hi, stage + (size_t)w * 32 * 33);
@@ -694,12 +697,13 @@ __device__ __noinline__ void cta_tri_solve_dir(const T* __restrict__ M, int ldm,
 }
 
 // stage: optional shared-memory scratch of 8 x 32 x 33 elements of T for
-// the transposed update (without it, warp-per-row shuffle sums are used).
+// the transposed update (without it, warp-per-row shuffle sums are used);
+// MT: optional transpose of M, which the transposed update reads instead.
 template <typename T, typename V>
 __device__ void cta_tri_solve(const T* M, int ldm, int n, bool lower, bool trans, bool unit, V* x, int ldx,
-                              int nrhs, const T* Dinv = nullptr, T* stage = nullptr) {
-  if (lower != trans) cta_tri_solve_dir<T, V, true>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage);
-  else cta_tri_solve_dir<T, V, false>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage);
+                              int nrhs, const T* Dinv = nullptr, T* stage = nullptr, const T* MT = nullptr) {
+  if (lower != trans) cta_tri_solve_dir<T, V, true>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage, MT);
+  else cta_tri_solve_dir<T, V, false>(M, ldm, n, trans, unit, x, ldx, nrhs, Dinv, stage, MT);
 }
 
 // Row permutation of LU with partial pivoting as one gather: after the
@@ -738,27 +742,57 @@ __device__ __noinline__ void cta_permute(V* x, int ldx, int n, int nrhs, const i
 
 // LU application: x <- inv(A) x (trans: inv(A)^T x) with A = P L U, where
 // perm is the gather form of the pivots (cta_build_perm).  Linv/Uinv: the
-// diagonal-block inverses of L and U, or null for substitution.
+// diagonal-block inverses of L and U, or null for substitution.  WT: the
+// factor's transpose (cta_transpose), or null.
 template <typename T, typename V>
 __device__ void cta_lu_apply(const T* W, int ldw, int n, const int* perm, V* x, int ldx, int nrhs,
                              bool trans, V* tmp, const T* Linv = nullptr, const T* Uinv = nullptr,
-                             T* stage = nullptr) {
+                             T* stage = nullptr, const T* WT = nullptr) {
   if (!trans) {
     cta_permute<V>(x, ldx, n, nrhs, perm, false, tmp);
     cta_tri_solve<T, V>(W, ldw, n, true, false, true, x, ldx, nrhs, Linv, stage);
     cta_tri_solve<T, V>(W, ldw, n, false, false, false, x, ldx, nrhs, Uinv, stage);
   } else {
-    cta_tri_solve<T, V>(W, ldw, n, false, true, false, x, ldx, nrhs, Uinv, stage);
-    cta_tri_solve<T, V>(W, ldw, n, true, true, true, x, ldx, nrhs, Linv, stage);
+    cta_tri_solve<T, V>(W, ldw, n, false, true, false, x, ldx, nrhs, Uinv, stage, WT);
+    cta_tri_solve<T, V>(W, ldw, n, true, true, true, x, ldx, nrhs, Linv, stage, WT);
     cta_permute<V>(x, ldx, n, nrhs, perm, true, tmp);
   }
 }
 
 template <typename T, typename V>
 __device__ void cta_chol_apply(const T* W, int ldw, int n, V* x, int ldx, int nrhs,
-                               const T* Linv = nullptr, T* stage = nullptr) {
+                               const T* Linv = nullptr, T* stage = nullptr, const T* WT = nullptr) {
   cta_tri_solve<T, V>(W, ldw, n, true, false, false, x, ldx, nrhs, Linv, stage);
-  cta_tri_solve<T, V>(W, ldw, n, true, true, false, x, ldx, nrhs, Linv, stage);
+  cta_tri_solve<T, V>(W, ldw, n, true, true, false, x, ldx, nrhs, Linv, stage, WT);
+}
+
+// WT = W^T (n x n, both ld ldw; W and WT do not overlap), through one
+// 32 x 33 shared-memory tile per warp (stage: 8 x 32 x 33 elements of T):
+// coalesced column loads of W and column stores of WT.
+template <typename T>
+__device__ __noinline__ void cta_transpose(const T* __restrict__ W, int ldw, int n, T* __restrict__ WT, T* stage) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* tile = stage + (size_t)w * 32 * 33;
+  const int nt = (n + 31) / 32;
+  __syncthreads();
+  for (int t = w; t < nt * nt; t += kWarps) {
+    const int i0 = (t % nt) * 32, j0 = (t / nt) * 32;
+    const int i = i0 + lane;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {  // tile[c][lane] = W(i0 + lane, j0 + c)
+      const int j = j0 + c;
+      tile[c * 33 + lane] = (i < n && j < n) ? W[(size_t)j * ldw + i] : T(0);
+    }
+    __syncwarp();
+    const int j = j0 + lane;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) {  // WT(j0 + lane, i0 + c) = W(i0 + c, j0 + lane)
+      const int ic = i0 + c;
+      if (ic < n && j < n) WT[(size_t)ic * ldw + j] = tile[lane * 33 + c];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
 }
 
 // -------------------------------------------------------------- residual
@@ -824,32 +858,43 @@ __device__ __noinline__ void cta_residual(const double* __restrict__ A, int lda,
 }
 
 // ------------------------------------------------------------ estimator
-// 1-norm estimate of inv(A) (Hager 1984; Higham 1988): apply(v, trans)
-// overwrites the smem vector v (length n) with inv(A) v or inv(A)^T v.
-// xi: smem scratch of length n.
+// 1-norm estimate of inv(A) (Hager 1984; Higham 1988): apply(v, trans, k)
+// overwrites the k <= 2 smem columns v, v + n with inv(A) v or inv(A)^T v.
+// v: room for 2n values; xi: smem scratch of length n after them.  The
+// closing test vector of alternating signs (Higham 1988) does not depend on
+// the iteration, so it is the second column of the first product: the same
+// values as a product of its own, one dependent solve fewer.
 template <typename V, typename Apply>
 __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red) {
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kThreads) v[i] = V(1) / V(n);
-  apply(v, false);
   if (n == 1) {
+    if (threadIdx.x == 0) v[0] = V(1);
+    apply(v, false, 1);
     __syncthreads();
     double e = fabs((double)v[0]);
     __syncthreads();
     return e;
   }
-  auto sum_abs = [&]() {
+  for (int i = threadIdx.x; i < n; i += kThreads) {
+    v[i] = V(1) / V(n);
+    const V sgn = (i & 1) ? V(-1) : V(1);
+    v[n + i] = sgn * (V(1) + V(i) / V(n - 1));
+  }
+  apply(v, false, 2);
+  auto sum_abs_of = [&](const V* p) {
     double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += kThreads) s += fabs((double)v[i]);
+    for (int i = threadIdx.x; i < n; i += kThreads) s += fabs((double)p[i]);
     return cta_sum(s, red);
   };
+  auto sum_abs = [&]() { return sum_abs_of(v); };
+  const double temp = 2.0 * sum_abs_of(v + n) / (double)(3 * n);
   double est = sum_abs();
   for (int i = threadIdx.x; i < n; i += kThreads) {
     V sg = v[i] >= V(0) ? V(1) : V(-1);
     xi[i] = sg;
     v[i] = sg;
   }
-  apply(v, true);
+  apply(v, true, 1);
   int k = 2;
   for (;;) {
     double best = -1.0;
@@ -865,7 +910,7 @@ __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red
       break;
     }
     for (int i = threadIdx.x; i < n; i += kThreads) v[i] = (i == j) ? V(1) : V(0);
-    apply(v, false);
+    apply(v, false, 1);
     const double estold = est;
     est = sum_abs();
     bool same = true;
@@ -880,7 +925,7 @@ __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red
       xi[i] = sg;
       v[i] = sg;
     }
-    apply(v, true);
+    apply(v, true, 1);
     double best2 = -1.0;
     int bi2 = 0x7fffffff;
     for (int i = threadIdx.x; i < n; i += kThreads) {
@@ -897,13 +942,6 @@ __device__ double cta_est_inv_norm1(int n, V* v, V* xi, Apply apply, CtaRed& red
     __syncthreads();
     if (vj == vjn || k > 5) break;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += kThreads) {
-    V sgn = (i & 1) ? V(-1) : V(1);
-    v[i] = sgn * (V(1) + V(i) / V(n - 1));
-  }
-  apply(v, false);
-  const double temp = 2.0 * sum_abs() / (double)(3 * n);
   if (temp > est) est = temp;
   __syncthreads();
   return est;
