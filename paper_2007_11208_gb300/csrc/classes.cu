@@ -359,7 +359,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
     const int nb = pick_nb<float>(n, d, KIND);
     int f = KIND == 0 ? cta_lu_factor<float>(W, ldw, n, sl.piv, reinterpret_cast<float*>(smem), nb)
                       : cta_chol_factor<float>(W, ldw, n, reinterpret_cast<float*>(smem), nb);
-    if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);
+    if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm, reinterpret_cast<int*>(smem));
     if (f == 0) {
       float* Li = reinterpret_cast<float*>(sl.Linv);
       float* Ui = reinterpret_cast<float*>(sl.Uinv);
@@ -423,7 +423,7 @@ __device__ bool dense_system(const BatchDesc& d, int64_t s, unsigned char* smem,
   const int nb = pick_nb<double>(n, d, KIND);
   int f = KIND == 0 ? cta_lu_factor<double>(W, ldw, n, sl.piv, reinterpret_cast<double*>(smem), nb)
                     : cta_chol_factor<double>(W, ldw, n, reinterpret_cast<double*>(smem), nb);
-  if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm);
+  if (KIND == 0 && f == 0) cta_build_perm(sl.piv, n, sl.perm, reinterpret_cast<int*>(smem));
   if (threadIdx.x == 0) {
     inf->detail |= detail;
     inf->precision = ASOLVE_PREC_FP64;

@@ -350,6 +350,7 @@ template <typename T>
 __device__ __noinline__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* smem, int nb) {
   __shared__ PivRed<T> pr;
   __shared__ T prow[32];
+  __shared__ int spiv[32];  // this panel's pivot rows, for the swaps outside it
   T* Pn = smem;
   // after the panel: L11 inverse (32 x 33) and two 32 x 64 tiles
   T* Li = smem + (size_t)n * nb;
@@ -381,11 +382,19 @@ __device__ __noinline__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* sme
       }
       if (lane == 0) { pr.mag[w] = best; pr.idx[w] = bi; pr.val[w] = bval; }
       __syncthreads();  // S1
-      T bm = pr.mag[0], pv = pr.val[0];
-      int p = pr.idx[0];
+      // the 8 warps' candidates: lane l reads candidate l & 7, then a
+      // butterfly over groups of 8 lanes (the same order: largest |v|,
+      // then the smallest row)
+      static_assert(kWarps == 8, "pivot candidates: one per warp, 8 warps");
+      T bm = pr.mag[lane & 7], pv = pr.val[lane & 7];
+      int p = pr.idx[lane & 7];
 #pragma unroll
-      for (int k = 1; k < kWarps; ++k)
-        if (pr.mag[k] > bm || (pr.mag[k] == bm && pr.idx[k] < p)) { bm = pr.mag[k]; p = pr.idx[k]; pv = pr.val[k]; }
+      for (int o = 4; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, bm, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, p, o);
+        const T ov = __shfl_xor_sync(0xffffffffu, pv, o);
+        if (ob > bm || (ob == bm && oi < p)) { bm = ob; p = oi; pv = ov; }
+      }
       if (p < c || p >= m || pv == T(0) || pv != pv) {
         __syncthreads();
         return k0 + c + 1;
@@ -399,12 +408,16 @@ __device__ __noinline__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* sme
         Pn[(size_t)cc * m + p] = a;
         prow[cc] = b;
       }
-      if (threadIdx.x == 0) piv[k0 + c] = k0 + p;
+      if (threadIdx.x == 0) {
+        piv[k0 + c] = k0 + p;
+        spiv[c] = k0 + p;
+      }
       __syncthreads();  // S2
       const T inv = T(1) / pv;
       for (int r = c + 1 + threadIdx.x; r < m; r += kThreads) {
         const T l = Pn[(size_t)c * m + r] * inv;
         Pn[(size_t)c * m + r] = l;
+#pragma unroll 4
         for (int cc = c + 1; cc < kb; ++cc) Pn[(size_t)cc * m + r] -= l * prow[cc];
       }
     }
@@ -415,7 +428,7 @@ __device__ __noinline__ int cta_lu_factor(T* W, int ldw, int n, int* piv, T* sme
       if (col >= k0 && col < k0 + kb) continue;
       T* cp = W + (size_t)col * ldw;
       for (int c = 0; c < kb; ++c) {
-        const int p = piv[k0 + c];
+        const int p = spiv[c];
         if (p != k0 + c) {
           const T a = cp[k0 + c];
           cp[k0 + c] = cp[p];
@@ -708,17 +721,28 @@ __device__ void cta_tri_solve(const T* M, int ldm, int n, bool lower, bool trans
 
 // Row permutation of LU with partial pivoting as one gather: after the
 // swaps k <-> piv[k] (k = 0..n-1), position k holds original row perm[k].
-__device__ void cta_build_perm(const int* piv, int n, int* perm) {
+// The swaps form one sequential chain, so they run in shared memory
+// (s_tmp: 2n ints); a chain of dependent global-memory round trips cost
+// ~0.4 ms at n = 512.
+__device__ void cta_build_perm(const int* piv, int n, int* perm, int* s_tmp) {
+  int* sp = s_tmp;
+  int* sq = s_tmp + n;
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += kThreads) {
+    sp[k] = piv[k];
+    sq[k] = k;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 0; k < n; ++k) perm[k] = k;
     for (int k = 0; k < n; ++k) {
-      const int p = piv[k];
-      const int t = perm[k];
-      perm[k] = perm[p];
-      perm[p] = t;
+      const int p = sp[k];
+      const int t = sq[k];
+      sq[k] = sq[p];
+      sq[p] = t;
     }
   }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += kThreads) perm[k] = sq[k];
   __syncthreads();
 }
 
