@@ -13,6 +13,7 @@ namespace {
 struct WarpBand {
   double* F;
   int* piv;
+  double* rd = nullptr;  // optional: 1 / U(j,j), written by warp_band_lu
   int n, kl, ku, kv, ldf;
   __device__ double& at(int i, int j) const { return F[(size_t)(kv + i - j) + (size_t)j * ldf]; }
 };
@@ -46,6 +47,7 @@ __device__ int warp_band_lu(WarpBand& b) {
       }
     __syncwarp();
     const double inv = 1.0 / b.at(j, j);
+    if (b.rd && lane == 0) b.rd[j] = inv;
     for (int t = 1 + lane; t <= km; t += 32) b.at(j + t, j) *= inv;
     __syncwarp();
     // rank-1 update of rows j+1..j+km, columns j+1..ju
@@ -194,56 +196,65 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// x <- inv(A) x with the band factors (Sec. 2.1 solve), one warp, one vector.
-// ring: kD * (kv + 2) doubles + kD ints of shared memory.
-template <int R>
+// x <- inv(A) x with the band factors (Sec. 2.1 solve), one warp; NC
+// vectors at once (x column-major, ld ldx): the columns share the chain of
+// steps, each step's column work is independent, so NC columns cost far
+// less than NC sweeps.  With RD, rd[i] = 1 / U(i,i) (from the
+// factorisation) turns each step's FP64 division into a multiplication:
+// GB300's FP64 pipe, shared by every warp of the SM, bounds the batched
+// sweeps, and a division is several of its instructions.  ring: kD * (kv + 1
+// + NC + RD) doubles + kD ints of shared memory.
+template <int R, int NC = 1, bool RD = false>
 __device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl, int ku, const int* __restrict__ piv,
-                           double* x, double* ring, int* pring) {
+                           double* x, double* ring, int* pring, int ldx = 0, const double* __restrict__ rd = nullptr) {
   const int lane = threadIdx.x & 31;
-  const int kv = kl + ku, SL = kv + 2;
-  Win<R> W;
+  const int kv = kl + ku, SL = kv + 1 + NC + (RD ? 1 : 0);
+  Win<R> W[NC];
   // ---- forward: apply P_j then L_j, j = 0..n-1; element t = x[j+t], t <= kl
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int t = r * 32 + lane;
-    W.w[r] = (t <= kl && t < n) ? x[t] : 0.0;
-  }
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int t = r * 32 + lane;
+      W[c].w[r] = (t <= kl && t < n) ? x[(size_t)c * ldx + t] : 0.0;
+    }
   __syncwarp();
-  auto pre_f = [&](int c) {
-    if (c < n) {
-      double* sl = ring + (size_t)(c % kD) * SL;
-      const int kmc = min(kl, n - 1 - c);
-      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)c * ldf);
-      if (lane == 0) {
-        if (c + kl + 1 < n) cp_async8(sl + kl, x + c + kl + 1);
-        cp_async4(pring + c % kD, piv + c);
-      }
+  auto pre_f = [&](int cs) {
+    if (cs < n) {
+      double* sl = ring + (size_t)(cs % kD) * SL;
+      const int kmc = min(kl, n - 1 - cs);
+      for (int t = 1 + lane; t <= kmc; t += 32) cp_async8(sl + t - 1, F + (size_t)kv + t + (size_t)cs * ldf);
+      if (lane < NC && cs + kl + 1 < n) cp_async8(sl + kl + lane, x + (size_t)lane * ldx + cs + kl + 1);
+      if (lane == 0) cp_async4(pring + cs % kD, piv + cs);
     }
     cp_commit();
   };
-  for (int c = 0; c < kD; ++c) pre_f(c);
+  for (int cs = 0; cs < kD; ++cs) pre_f(cs);
   for (int j = 0; j < n; ++j) {
     cp_wait<kD - 1>();
     __syncwarp();
     const double* sl = ring + (size_t)(j % kD) * SL;
     const int km = min(kl, n - 1 - j);
     const int d = pring[j % kD] - j;
-    const double e0 = W.get(0);
-    const double ed = W.get(d);
-    if (d) {
-      W.set(0, ed);
-      W.set(d, e0);
-    }
-    const double xj = d ? ed : e0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int t = r * 32 + lane;
-      if (t >= 1 && t <= km) W.w[r] = fma(-sl[t - 1], xj, W.w[r]);
+    for (int c = 0; c < NC; ++c) {
+      const double e0 = W[c].get(0);
+      const double ed = W[c].get(d);
+      if (d) {
+        W[c].set(0, ed);
+        W[c].set(d, e0);
+      }
+      const double xj = d ? ed : e0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int t = r * 32 + lane;
+        if (t >= 1 && t <= km) W[c].w[r] = fma(-sl[t - 1], xj, W[c].w[r]);
+      }
+      if (lane == 0) x[(size_t)c * ldx + j] = xj;
+      const double inc = (j + kl + 1 < n) ? sl[kl + c] : 0.0;
+      W[c].shift_down();
+      W[c].set(kl, inc);
     }
-    if (lane == 0) x[j] = xj;
-    const double inc = (j + kl + 1 < n) ? sl[kl] : 0.0;
-    W.shift_down();
-    W.set(kl, inc);
     __syncwarp();
     pre_f(j + kD);
   }
@@ -252,17 +263,20 @@ __device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl,
   __threadfence();
   // ---- backward: U x = y, i = n-1..0; element s = y[i-s], s <= kv
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int s = r * 32 + lane;
-    W.w[r] = (s <= kv && n - 1 - s >= 0) ? x[n - 1 - s] : 0.0;
-  }
+  for (int c = 0; c < NC; ++c)
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int s = r * 32 + lane;
+      W[c].w[r] = (s <= kv && n - 1 - s >= 0) ? x[(size_t)c * ldx + n - 1 - s] : 0.0;
+    }
   __syncwarp();
   auto pre_b = [&](int q) {
     const int i = n - 1 - q;
     if (i >= 0) {
       double* sl = ring + (size_t)(q % kD) * SL;
       for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)i * ldf);
-      if (lane == 0 && i - kv - 1 >= 0) cp_async8(sl + kv + 1, x + i - kv - 1);
+      if (lane < NC && i - kv - 1 >= 0) cp_async8(sl + kv + 1 + lane, x + (size_t)lane * ldx + i - kv - 1);
+      if (RD && lane == 31) cp_async8(sl + kv + 1 + NC, rd + i);
     }
     cp_commit();
   };
@@ -272,17 +286,20 @@ __device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl,
     cp_wait<kD - 1>();
     __syncwarp();
     const double* sl = ring + (size_t)(q % kD) * SL;
-    const double xi = W.get(0) / sl[kv];
-    if (lane == 0) x[i] = xi;
     const int lim = min(kv, i);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int s = r * 32 + lane;
-      if (s >= 1 && s <= lim) W.w[r] = fma(-sl[kv - s], xi, W.w[r]);
+    for (int c = 0; c < NC; ++c) {
+      const double xi = RD ? W[c].get(0) * sl[kv + 1 + NC] : W[c].get(0) / sl[kv];
+      if (lane == 0) x[(size_t)c * ldx + i] = xi;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int s = r * 32 + lane;
+        if (s >= 1 && s <= lim) W[c].w[r] = fma(-sl[kv - s], xi, W[c].w[r]);
+      }
+      const double inc = (i - kv - 1 >= 0) ? sl[kv + 1 + c] : 0.0;
+      W[c].shift_down();
+      W[c].set(kv, inc);
     }
-    const double inc = (i - kv - 1 >= 0) ? sl[kv + 1] : 0.0;
-    W.shift_down();
-    W.set(kv, inc);
     __syncwarp();
     pre_b(q + kD);
   }
@@ -292,11 +309,12 @@ __device__ void band_apply(const double* __restrict__ F, int ldf, int n, int kl,
 }
 
 // x <- inv(A)^T x: U^T z = x forward, then L_j^T and P_j backward.
-template <int R>
+template <int R, bool RD = false>
 __device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int kl, int ku,
-                             const int* __restrict__ piv, double* x, double* ring, int* pring) {
+                             const int* __restrict__ piv, double* x, double* ring, int* pring,
+                             const double* __restrict__ rd = nullptr) {
   const int lane = threadIdx.x & 31;
-  const int kv = kl + ku, SL = kv + 2;
+  const int kv = kl + ku, SL = kv + 2 + (RD ? 1 : 0);
   Win<R> W;
   // ---- U^T z = b, i = 0..n-1: element 0 = b_i, element s = z_{i-s}
 #pragma unroll
@@ -307,6 +325,7 @@ __device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int k
       double* sl = ring + (size_t)(c % kD) * SL;
       for (int t = lane; t <= kv; t += 32) cp_async8(sl + t, F + (size_t)t + (size_t)c * ldf);
       if (lane == 0 && c + 1 < n) cp_async8(sl + kv + 1, x + c + 1);
+      if (RD && lane == 31) cp_async8(sl + kv + 2, rd + c);
     }
     cp_commit();
   };
@@ -323,7 +342,7 @@ __device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int k
       if (s >= 1 && s <= lim) acc = fma(sl[kv - s], W.w[r], acc);
     }
     acc = warp_sum_d(acc);
-    const double zi = (W.get(0) - acc) / sl[kv];
+    const double zi = RD ? (W.get(0) - acc) * sl[kv + 2] : (W.get(0) - acc) / sl[kv];
     if (lane == 0) x[i] = zi;
     W.set(0, zi);
     const double inc = (i + 1 < n) ? sl[kv + 1] : 0.0;
@@ -396,8 +415,9 @@ __device__ void band_apply_t(const double* __restrict__ F, int ldf, int n, int k
 }
 
 
-// Ring storage of the sweeps for a window of R registers.
-__host__ __device__ constexpr int band_ring_doubles(int R) { return kD * (32 * R + 2); }
+// Ring storage of the sweeps for a window of R registers and up to NC
+// vectors at once.
+__host__ __device__ constexpr int band_ring_doubles(int R, int NC = 1) { return kD * (32 * R + 2 + NC); }
 
 // x <- inv(A) x (trans: inv(A)^T x) for one vector, choosing the register
 // window from the bandwidth; beyond 32 * rmax elements the global-memory
@@ -410,11 +430,19 @@ __device__ __forceinline__ void band_sweep_any(const WarpBand& b, double* x, boo
   __threadfence();
   const int need = (b.kv + 1 + 31) / 32;
   if (need <= 1 && rmax >= 1) {
-    trans ? band_apply_t<1>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring)
-          : band_apply<1>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring);
+    if (b.rd)
+      trans ? band_apply_t<1, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.rd)
+            : band_apply<1, 1, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, 0, b.rd);
+    else
+      trans ? band_apply_t<1>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring)
+            : band_apply<1>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring);
   } else if (need <= 2 && rmax >= 2) {
-    trans ? band_apply_t<2>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring)
-          : band_apply<2>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring);
+    if (b.rd)
+      trans ? band_apply_t<2, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.rd)
+            : band_apply<2, 1, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, 0, b.rd);
+    else
+      trans ? band_apply_t<2>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring)
+            : band_apply<2>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring);
   } else {
     warp_band_apply(b, x, trans);
   }

@@ -608,16 +608,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
 // to kBandR registers (kl + ku < 32 kBandR); wider bands use the
 // global-memory sweep.
 constexpr int kBandR = 2;
-constexpr int kBandRingBytes = band_ring_doubles(kBandR) * 8 + 64;  // ring + pivot ring, per warp
+constexpr int kBandCols = 8;  // right-hand sides per sweep
+constexpr int kBandRingBytes = band_ring_doubles(kBandR, kBandCols) * 8 + 64;  // ring + pivot ring, per warp
 
-// Warp-scope estimator (same iteration as cta_est_inv_norm1).
+// x (n x k, ld n) <- inv(A) x: all k <= kBandCols columns in one pair of
+// sweeps when the register window fits, else column by column on the
+// global-memory routine.
+__device__ void band_solve_cols(const WarpBand& b, double* x, int k, double* ring, int* pring) {
+  // the factor and x were written with ordinary stores; the sweeps read
+  // them through cp.async
+  __syncwarp();
+  __threadfence();
+  const int need = (b.kv + 1 + 31) / 32;
+  if (need <= kBandR) {
+    with_nr(k, [&](auto nc) {
+      constexpr int NC = decltype(nc)::value;
+      if (need <= 1) band_apply<1, NC, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+      else band_apply<2, NC, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+    });
+  } else {
+    for (int c = 0; c < k; ++c) warp_band_apply(b, x + (size_t)c * b.n, false);
+  }
+}
+
+// Warp-scope estimator (same iteration as cta_est_inv_norm1, whose closing
+// vector of alternating signs likewise rides along the first product, as
+// the second column: xi = v + n).
 __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi, double* ring, int* pring) {
   const int lane = threadIdx.x & 31;
   const int n = b.n;
-  for (int i = lane; i < n; i += 32) v[i] = 1.0 / (double)n;
-  __syncwarp();
-  band_sweep_any(b, v, false, ring, pring, kBandR);
-  if (n == 1) return fabs(v[0]);
+  if (n == 1) {
+    if (lane == 0) v[0] = 1.0;
+    band_solve_cols(b, v, 1, ring, pring);
+    return fabs(v[0]);
+  }
+  for (int i = lane; i < n; i += 32) {
+    v[i] = 1.0 / (double)n;
+    xi[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
+  }
+  band_solve_cols(b, v, 2, ring, pring);
+  double temp = 0.0;
+  for (int i = lane; i < n; i += 32) temp += fabs(xi[i]);
+  temp = 2.0 * warp_sum(temp) / (double)(3 * n);
   auto sum_abs = [&]() {
     double s = 0.0;
     for (int i = lane; i < n; i += 32) s += fabs(v[i]);
@@ -671,10 +703,6 @@ __device__ double warp_est_inv_norm1(const WarpBand& b, double* v, double* xi, d
     if (vj == vjn || k > 5) break;
   }
   __syncwarp();
-  for (int i = lane; i < n; i += 32) v[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (double)i / (double)(n - 1));
-  __syncwarp();
-  band_sweep_any(b, v, false, ring, pring, kBandR);
-  double temp = 2.0 * sum_abs() / (double)(3 * n);
   return temp > est ? temp : est;
 }
 
@@ -686,7 +714,7 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
   const BatchDesc& d = *dp;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double* ring = reinterpret_cast<double*>(band_smem + (size_t)w * kBandRingBytes);
-  int* pring = reinterpret_cast<int*>(band_smem + (size_t)w * kBandRingBytes + band_ring_doubles(kBandR) * 8);
+  int* pring = reinterpret_cast<int*>(band_smem + (size_t)w * kBandRingBytes + band_ring_doubles(kBandR, kBandCols) * 8);
   const int len = d.list_len[L_BAND];
   const size_t sub = (size_t)d.slot_bytes / kWarps;
   for (int phase = 0; phase < 2; ++phase) {
@@ -719,7 +747,7 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
       b.piv = reinterpret_cast<int*>(base + fbytes);
       double* v = reinterpret_cast<double*>(base + fbytes + (((size_t)n * 4 + 255) & ~(size_t)255));
       double* xi = v + n;
-      double* xv = xi + n;
+      b.rd = xi + n;  // 1 / U(j,j) of the factorisation, for the sweeps
       const double* A = sys_A(d, s);
       const double* B = sys_B(d, s);
       double* X = sys_X(d, s);
@@ -735,13 +763,9 @@ __global__ void __launch_bounds__(kThreads) k_band_class(const BatchDesc* __rest
       const bool failed = f != 0;
       double rc = __longlong_as_double(0x7ff8000000000000ll);
       if (!failed) {
-        for (int c = 0; c < nrhs; ++c) {
-          for (int i = lane; i < n; i += 32) xv[i] = B[(size_t)c * n + i];
-          __syncwarp();
-          band_sweep_any(b, xv, false, ring, pring, kBandR);
-          for (int i = lane; i < n; i += 32) X[(size_t)c * n + i] = xv[i];
-          __syncwarp();
-        }
+        for (int64_t e = lane; e < (int64_t)n * nrhs; e += 32) X[e] = B[e];
+        for (int c = 0; c < nrhs; ++c) band_solve_cols(b, X + (size_t)c * n, 1, ring, pring);
+        __syncwarp();
         if (!(d.flags & ASOLVE_NO_RCOND)) rc = rcond_from(sr.norm1, warp_est_inv_norm1(b, v, xi, ring, pring));
         if (d.flags & ASOLVE_BERR) {
           // FP64 backward error over the band: r = b - A x, A read in band form
