@@ -71,10 +71,10 @@ PEAK_DFMA = 1.254e12
 PEAK_DMMA = 1.095e12
 COUNT = 10000  # systems per GPU per step (--count overrides, for small profiling runs)
 # dram__bytes_read.sum + dram__bytes_write.sum of k_lu_class on the
-# 1,000-system batch of the same generator (3.421075 GB + 1.095710 GB), from
+# 1,000-system batch of the same generator (3.689203 GB + 1.292845 GB), from
 # an ncu capture of the timed step of `bench.py --count 1000 --steps 1
 # --warmup 1 --no-cpu-baseline`
-LU_CLASS_DRAM_BYTES_1000 = 3.421075e9 + 1.095710e9
+LU_CLASS_DRAM_BYTES_1000 = 3.689203e9 + 1.292845e9
 TUNING = os.path.join(ROOT, "paper_2007_11208_gb300", "tuning.json")  # autotuner output, if present
 SEED = 1
 
