@@ -839,60 +839,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_trsv_wave(const T* __restrict__
 // SM has many independent loads of A in flight: blockIdx.y takes the k
 // segment [seg * klen, (seg + 1) * klen) and writes its partial products
 // P[seg][c][r]; k_residual_sum adds the segments in order (the result does
-// not depend on scheduling) and forms R = B - sum and max |R|.
-//   nrhs <= 2: one thread per row on DFMA (A read once, eight loads ahead);
-//   nrhs <= 8: one warp per 8-row group on mma.sync f64.
+// not depend on scheduling) and forms R = B - sum and max |R|.  One thread
+// per row on DFMA with exactly NR accumulators (A read once, eight loads
+// ahead): an FP64 instruction costs its pipe time whether its lanes are on
+// or off, so a column count fixed at compile time wastes none (the 8-column
+// mma.sync f64 form spent 8 columns' work at any nrhs).
 constexpr int kResMaxSeg = 32;
+template <int NR>
 __global__ void __launch_bounds__(256) k_residual_part_fma(const double* __restrict__ A, int n,
-                                                           const double* __restrict__ X, int nrhs, int klen,
+                                                           const double* __restrict__ X, int klen,
                                                            double* __restrict__ P) {
   const int r = blockIdx.x * 256 + threadIdx.x, seg = blockIdx.y;
   const int k0 = seg * klen, k1 = min(n, k0 + klen);
   if (r >= n) return;
-  double s0 = 0.0, s1 = 0.0;
+  double s[NR];
+#pragma unroll
+  for (int c = 0; c < NR; ++c) s[c] = 0.0;
   int k = k0;
   for (; k + 8 <= k1; k += 8) {
     double a[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) a[q] = __ldg(A + (size_t)(k + q) * n + r);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      s0 = fma(a[q], __ldg(X + k + q), s0);
-      if (nrhs > 1) s1 = fma(a[q], __ldg(X + (size_t)n + k + q), s1);
-    }
+    for (int q = 0; q < 8; ++q)
+#pragma unroll
+      for (int c = 0; c < NR; ++c) s[c] = fma(a[q], __ldg(X + (size_t)c * n + k + q), s[c]);
   }
   for (; k < k1; ++k) {
     const double a = __ldg(A + (size_t)k * n + r);
-    s0 = fma(a, __ldg(X + k), s0);
-    if (nrhs > 1) s1 = fma(a, __ldg(X + (size_t)n + k), s1);
+#pragma unroll
+    for (int c = 0; c < NR; ++c) s[c] = fma(a, __ldg(X + (size_t)c * n + k), s[c]);
   }
-  P[((size_t)seg * nrhs) * n + r] = s0;
-  if (nrhs > 1) P[((size_t)seg * nrhs + 1) * n + r] = s1;
-}
-
-__global__ void __launch_bounds__(64) k_residual_part_mma(const double* __restrict__ A, int n,
-                                                          const double* __restrict__ X, int nrhs, int klen,
-                                                          double* __restrict__ P) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int g = lane >> 2, t = lane & 3, seg = blockIdx.y;
-  const int r0 = (blockIdx.x * 2 + w) * 8;
-  if (r0 >= n) return;
-  const int k0 = seg * klen, k1 = min(n, k0 + klen);  // klen is a multiple of 4
-  const int ra = r0 + g;
-  const bool xok = g < nrhs;
-  double c0 = 0.0, c1 = 0.0;
-#pragma unroll 8
-  for (int k = k0; k < k1; k += 4) {
-    const int ka = k + t;
-    const double a = (ra < n && ka < k1) ? __ldg(A + (size_t)ka * n + ra) : 0.0;
-    const double b = (xok && ka < k1) ? __ldg(X + (size_t)g * n + ka) : 0.0;
-    dmma_8x8x4(c0, c1, a, b);
-  }
-  const int r = r0 + g;
-  if (r < n) {
-    if (2 * t < nrhs) P[((size_t)seg * nrhs + 2 * t) * n + r] = c0;
-    if (2 * t + 1 < nrhs) P[((size_t)seg * nrhs + 2 * t + 1) * n + r] = c1;
-  }
+#pragma unroll
+  for (int c = 0; c < NR; ++c) P[((size_t)seg * NR + c) * n + r] = s[c];
 }
 
 __global__ void k_residual_sum(const double* __restrict__ P, int nseg, int n, int nrhs,
@@ -1054,15 +1033,23 @@ int residual_large(const double* A, int n, const double* B, const double* X, int
     LCK(cudaGetLastError());
     return ASOLVE_OK;
   }
-  const bool fma_path = nrhs <= 2;
-  const int gx = fma_path ? (n + 255) / 256 : (n + 15) / 16;
+  const int gx = (n + 255) / 256;
   int nseg = (4 * num_sms + gx - 1) / gx;  // about four CTAs of loads per SM
   nseg = nseg < 1 ? 1 : (nseg > kResMaxSeg ? kResMaxSeg : nseg);
   int klen = (n + nseg - 1) / nseg;
   klen = (klen + 7) & ~7;
   nseg = (n + klen - 1) / klen;
-  if (fma_path) k_residual_part_fma<<<dim3(gx, nseg), 256, 0, st>>>(A, n, X, nrhs, klen, P);
-  else k_residual_part_mma<<<dim3(gx, nseg), 64, 0, st>>>(A, n, X, nrhs, klen, P);
+  const dim3 grid(gx, nseg);
+  switch (nrhs) {
+    case 1: k_residual_part_fma<1><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 2: k_residual_part_fma<2><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 3: k_residual_part_fma<3><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 4: k_residual_part_fma<4><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 5: k_residual_part_fma<5><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 6: k_residual_part_fma<6><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    case 7: k_residual_part_fma<7><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+    default: k_residual_part_fma<8><<<grid, 256, 0, st>>>(A, n, X, klen, P); break;
+  }
   k_residual_sum<<<dim3((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, nrhs), 256, 0, st>>>(P, nseg, n, nrhs,
                                                                                               B, R, rmax);
   LCK(cudaGetLastError());
