@@ -608,12 +608,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_tri_class(const BatchDesc* __re
 // to kBandR registers (kl + ku < 32 kBandR); wider bands use the
 // global-memory sweep.
 constexpr int kBandR = 2;
-constexpr int kBandCols = 8;  // right-hand sides per sweep
+constexpr int kBandCols = 2;  // vectors per sweep: the estimator's first product
 constexpr int kBandRingBytes = band_ring_doubles(kBandR, kBandCols) * 8 + 64;  // ring + pivot ring, per warp
 
-// x (n x k, ld n) <- inv(A) x: all k <= kBandCols columns in one pair of
+// x (n x k, ld n, k = 1 or 2) <- inv(A) x: the k columns share one pair of
 // sweeps when the register window fits, else column by column on the
-// global-memory routine.
+// global-memory routine.  (The right-hand sides of a solve go one sweep
+// each: sweeping all of them at once measured slower, the SM's FP64 pipe
+// and issue slots being shared by every warp's sweep.)
 __device__ void band_solve_cols(const WarpBand& b, double* x, int k, double* ring, int* pring) {
   // the factor and x were written with ordinary stores; the sweeps read
   // them through cp.async
@@ -621,11 +623,13 @@ __device__ void band_solve_cols(const WarpBand& b, double* x, int k, double* rin
   __threadfence();
   const int need = (b.kv + 1 + 31) / 32;
   if (need <= kBandR) {
-    with_nr(k, [&](auto nc) {
-      constexpr int NC = decltype(nc)::value;
-      if (need <= 1) band_apply<1, NC, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
-      else band_apply<2, NC, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
-    });
+    if (k == 2) {
+      if (need <= 1) band_apply<1, 2, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+      else band_apply<2, 2, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+    } else {
+      if (need <= 1) band_apply<1, 1, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+      else band_apply<2, 1, true>(b.F, b.ldf, b.n, b.kl, b.ku, b.piv, x, ring, pring, b.n, b.rd);
+    }
   } else {
     for (int c = 0; c < k; ++c) warp_band_apply(b, x + (size_t)c * b.n, false);
   }
